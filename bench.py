@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Benchmark of the sliding-mesh DGSEM hot path on one GB300 (replicas across GPUs).
+
+A step is one low-storage RK4 step (five stages) of the interface-heavy single solve:
+two blocks of 4 x 256 x 256 hexahedra (524,288 elements, 65,536 sliding faces per side),
+N = 5 (113.2 M DOF), FP32 state with FP64 mapping and mortar matrices, moving block at
+v = 0.37, smooth random initial field of 8 seeded Fourier modes per primitive variable.
+Every stage runs the mapper/mortar-matrix kernel, the fused interface kernel and the
+element kernel (volume, surface, RK update), replayed from a CUDA graph.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload (fewer elements along z).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "interface face-updates/s & DOF-updates/s vs FP64 plain path; p50/p99 solve latency"
+UNIT = "DOF-updates/s"
+WORKLOAD = ("interface-heavy single solve: 2 blocks x 4x256x256 hexes (524,288 elements, 65,536 "
+            "sliding faces), N=5 (113.2M DOF), FP32 state, FP64 mapping and mortar matrices, "
+            "v=0.37, 8 seeded Fourier modes per primitive variable on rho=1, p=1")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--profile-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nz", type=int, default=256, help="elements along z (256 = the full workload)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower().startswith("active")})
+        loaded = [x for x in sm if mx and x > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+ELEMENT_SOURCES = ["paper_2008_04356_gb300/csrc/sm_element.cuh", "paper_2008_04356_gb300/csrc/sm_common.cuh"]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "of measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per element-kernel launch from the committed ncu summary, if it was taken
+    on the current element-kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "dg_element_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha") != source_sha(ELEMENT_SOURCES):
+        return None
+    return rec.get("dram_bytes_per_launch_full_workload")
+
+
+def cpu_baseline(seconds: float):
+    """The FP64 oracle, as it stands, on the host cores: whole RK steps of the same workload
+    with fewer elements along z (bounded sample)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2008_04356_gb300 import synth
+    nz = 4
+    p = synth.config_interface_heavy(seed=1, precision=synth.FP64, nz=nz)
+    o = O.Oracle(p)
+    U = o.init_state()
+    G = np.zeros_like(U)
+    dt = synth.cfl_dt(p)
+    t = o.step(U, G, 0.0, dt, 1)            # warm-up step
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        t = o.step(U, G, t, dt, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": p.ndof * 5 * steps / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d RK steps (5 stages each) of 2 blocks x 4x256x%d hexes, N=5 (%d DOF), FP64, %.1f s"
+                      % (steps, nz, p.ndof, el),
+            "interface_face_updates_per_s": p.n_faces * 5 * steps / el}
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2008_04356_gb300 import synth
+    # size the sample so that (warmup + steps) whole RK steps take about two minutes
+    probe = synth.config_interface_heavy(seed=1, precision=synth.FP64, nz=1)
+    o = O.Oracle(probe)
+    U = o.init_state()
+    G = np.zeros_like(U)
+    dt = synth.cfl_dt(probe)
+    t0 = time.perf_counter()
+    o.step(U, G, 0.0, dt, 1)
+    per_nz = time.perf_counter() - t0
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    nz = int(max(1, min(256, budget / max(per_nz, 1e-6))))
+    p = synth.config_interface_heavy(seed=1, precision=synth.FP64, nz=nz)
+    o = O.Oracle(p)
+    U = o.init_state()
+    G = np.zeros_like(U)
+    dt = synth.cfl_dt(p)
+    t = o.step(U, G, 0.0, dt, args.warmup) if args.warmup else 0.0
+    t0 = time.perf_counter()
+    t = o.step(U, G, t, dt, args.steps)
+    el = time.perf_counter() - t0
+    value = p.ndof * 5 * args.steps / el
+    sample = "%d RK steps of 2 blocks x 4x256x%d hexes, N=5 (%d DOF), FP64 oracle" % (args.steps, nz, p.ndof)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "interface_face_updates_per_s": p.n_faces * 5 * args.steps / el}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2008_04356_gb300 import build as B, slidemesh, synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build_library()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    p = synth.config_interface_heavy(seed=1 + rank, precision=synth.FP32, nz=args.nz)
+    sol = slidemesh.Solver(p)
+    sol.init_state()
+    dt = synth.cfl_dt(p)
+    sol.step(dt, args.warmup)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sol.step(dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    dof_updates = world * p.ndof * 5 * args.steps
+    value = dof_updates / (ms * 1e-3)
+    face_rate = world * p.n_faces * 5 * args.steps / (ms * 1e-3)
+    d = sol.diag()
+
+    # per-kernel device times of the same stage sequence (event pairs around each launch)
+    kms, kcnt = sol.step_profiled(dt, args.profile_steps)
+    nn = (p.N + 1) ** 3
+    sb = 4
+    elem_bytes = (4 * 4 * 5 * sb + 1 * 3 * 5 * sb) / 5.0 * p.nelem * nn   # U in, G in/out, U out (stage 0: no G in)
+    elem_ms = kms[2] / kcnt[2]
+    iface_bytes = 20 * (p.N + 1) ** 2 * sb * p.n_faces
+    iface_ms = kms[1] / kcnt[1]
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    achieved = elem_bytes / (elem_ms * 1e-3) / 1e9
+    traffic = ncu_traffic()
+
+    # FP64 plain path, same workload, one solve
+    p64 = synth.config_interface_heavy(seed=1 + rank, precision=synth.FP64, nz=args.nz)
+    s64 = slidemesh.Solver(p64)
+    s64.init_state()
+    s64.step(dt, 1)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    s64.step(dt, args.fp64_steps)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(f0.elapsed_time(f1))
+    value64 = world * p64.ndof * 5 * args.fp64_steps / (ms64 * 1e-3)
+    s64.close()
+    del s64
+
+    # end to end through the C-ABI with host buffers: state in (pinned), one step, state out
+    Uh, _ = sol.get_state(out=torch.empty(sol.shape(), dtype=torch.float32, pin_memory=True))
+    Uo = torch.empty_like(Uh).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        sol.set_state(Uh, d["t"])
+        sol.step(dt, 1)
+        sol.get_state(out=Uo)
+    torch.cuda.synchronize()
+    el = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * p.ndof * 5 * args.e2e_steps / el, "unit": UNIT,
+           "h2d_bytes_per_step": Uh.numel() * 4 + 8, "d2h_bytes_per_step": Uo.numel() * 4 + 8,
+           "steps": args.e2e_steps}
+
+    if rank != 0:
+        sol.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": p.nelem, "N": p.N, "dof": p.ndof,
+                   "sliding_faces_per_side": p.n_faces, "state_bytes": p.ndof * 5 * 4,
+                   "riemann": "rusanov", "l2": "inputs larger than L2 (2.26 GB state per buffer)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "dt": dt, "final_t": d["t"]},
+        "interface_face_updates_per_s": face_rate,
+        "fp64_plain": {"value": value64, "unit": UNIT, "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps,
+                       "fp32_over_fp64": value / value64},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "kernel": "dg_element_kernel<N=5, float, Rusanov, stage>",
+                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": elem_bytes,
+                     "avg_launch_ms": elem_ms},
+        "kernels": {"stage_params": {"launches": kcnt[0], "ms": kms[0]},
+                    "sliding_interface": {"launches": kcnt[1], "ms": kms[1], "avg_ms": iface_ms,
+                                          "achieved_gbs": iface_bytes / (iface_ms * 1e-3) / 1e9,
+                                          "frac_hbm": iface_bytes / (iface_ms * 1e-3) / 1e9 / hbm},
+                    "dg_element": {"launches": kcnt[2], "ms": kms[2], "avg_ms": elem_ms}},
+        "e2e": e2e,
+        "gpu_launches": 15 * args.steps,
+        "clocks": clk,
+        "diag": {"n_delta": d["n_delta"], "s_delta": d["s_delta"], "finite": d["status"] == 0},
+    }
+    if not args.no_cpu_baseline and world >= 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    sol.close()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * slidemesh — sliding-mesh DGSEM hot path for one NVIDIA GB300 (sm_103a).
+ *
+ * The operator is the per-Runge-Kutta-stage right-hand side of the compressible Euler
+ * equations in ALE form (Duerrwaechter et al., arXiv 2008.04356, Sec. 2 Eq.
+ * fluxes_written_out), discretised by weak-form DGSEM on Legendre-Gauss-Lobatto nodes
+ * (Sec. 3.1), with a plane sliding interface between a static and a moving block handled
+ * by two mortars per face (Sec. 3.2 and 3.3; displacement decomposition and index relation
+ * of Sec. 4.3, Eqs. subim and indices), advanced by the Carpenter-Kennedy low-storage RK4
+ * (Sec. 3.1).
+ *
+ * Conventions of every call:
+ *  - Every call returns an sm_status (0 = SM_OK, negative = error); no call aborts, and no
+ *    kernel traps.  CUDA errors are returned as SM_ERR_CUDA; sm_last_error() gives text.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Calls that take a stream are asynchronous on it unless stated otherwise.
+ *  - State layout (host or device): U[e][var][k][j][i], var = (rho, rho v1, rho v2, rho v3,
+ *    rho e) conservative, (i, j, k) the LGL node indices along the element's reference
+ *    axes xi^1 = y (sliding direction), xi^2 = z, xi^3 = x (interface normal).  Elements:
+ *    static block first, e = ix + nx (iy + ny iz), then the moving block likewise.
+ *    Scalars are double for SM_FP64 solvers and float for SM_FP32 solvers.
+ *  - Interface face-flux layout: F[iz][iy][var][q][p], p along y (sliding), q along z;
+ *    the outward normal flux of that side's face times its surface element.
+ *  - A solver is not thread-safe; distinct solvers may be used from distinct threads.
+ */
+#ifndef SLIDEMESH_H
+#define SLIDEMESH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SM_OK = 0,
+  SM_PENDING = 1,
+  SM_ERR_ARG = -1,
+  SM_ERR_OOM = -2,
+  SM_ERR_CUDA = -3,
+  SM_ERR_NONFINITE = -4,
+  SM_ERR_TIMEOUT = -5,
+  SM_ERR_BUSY = -6,
+  SM_ERR_UNSUPPORTED = -7
+} sm_status;
+
+enum { SM_FP64 = 0, SM_FP32 = 1 };
+enum { SM_RUSANOV = 0, SM_ROE_HH = 1 };
+enum { SM_GEOM_PLANE = 0 };
+/* Flows used as initial data (sm_init_state) and as the weak Dirichlet state at x = x0, x2:
+ *  SM_FLOW_CONSTANT      primitive (rho, v1, v2, v3, p) = fpar[0..4]
+ *  SM_FLOW_ENTROPY_WAVE  rho = fpar0 + fpar1 sin(2 pi k.(x - u t)), k = fpar2..4,
+ *                        u = fpar5..7, p = fpar8
+ *  SM_FLOW_MODES         background fpar[0..4] plus, per primitive variable, 8 modes
+ *                        modes[var][m] = (amp, ky, kz, phase): amp sin(2 pi (ky y + kz z) + phase);
+ *                        the boundary state is the background
+ *  SM_FLOW_POLY_X        rho = fpar0 + fpar1 x' + fpar2 x'^2 + fpar3 x'^3, x' = x - fpar4 t,
+ *                        velocity fpar4..6, p = fpar7 */
+enum { SM_FLOW_CONSTANT = 0, SM_FLOW_ENTROPY_WAVE = 1, SM_FLOW_MODES = 2, SM_FLOW_POLY_X = 3 };
+
+/* Two structured hexahedral blocks sharing the plane sliding interface x = x1 (Sec. 3.3,
+ * first geometry of Fig. sm_meshes_overview).  Static block x in [x0, x1], moving block
+ * x in [x1, x2]; both y in [y0, y1] and z in [z0, z1], periodic in y and z.  The faces
+ * along the interface are equispaced (Sec. 3.3): nel_static[1..2] must equal
+ * nel_moving[1..2].  interface_conforming = 1 couples the two blocks as an ordinary
+ * conforming face instead (valid only while the displacement is zero). */
+typedef struct {
+  int N;                   /* polynomial degree, 1..7 */
+  int geom;                /* SM_GEOM_PLANE */
+  int nel_static[3];       /* elements along x, y, z */
+  int nel_moving[3];
+  double x0, x1, x2, y0, y1, z0, z1;
+  double gamma;            /* ratio of specific heats */
+  int riemann;             /* SM_RUSANOV | SM_ROE_HH */
+  int precision;           /* SM_FP64 | SM_FP32 for U, G, fluxes; mapping and mortar
+                              matrices are always built in FP64 */
+  int interface_conforming;
+  int flow;                /* SM_FLOW_* */
+  double fpar[16];
+  double modes[5][8][4];
+} sm_mesh_desc;
+
+/* Motion of the moving block: displacement Delta(t) = delta0 + v t along +y (Sec. 4.3,
+ * Fig. coordinates).  omega is reserved for rotating geometries and must be 0. */
+typedef struct {
+  double v;
+  double omega;
+  double delta0;
+} sm_motion;
+
+typedef struct {
+  long long n_delta;          /* integer face offset of the last evaluated stage */
+  double s_delta;             /* sub-face fraction of the last evaluated stage, in [0, 1] */
+  double t;                   /* solver time */
+  double totals[5];           /* sum_e sum_ijk J w_i w_j w_k U (conserved totals) */
+  double iface_sum_static[5]; /* sum over static interface faces of w_p w_q F, last stage */
+  double iface_sum_moving[5]; /* same on the moving side; conservation: the two cancel */
+} sm_diag_out;
+
+typedef struct sm_solver sm_solver;
+
+/* Creates a solver: validates desc, builds the LGL basis (FP64, host), allocates the
+ * device state (two state buffers, the RK register, interface fluxes, stage parameters)
+ * on the current device.  *out is library-owned; free it with sm_destroy.
+ * Errors: SM_ERR_ARG (invalid desc), SM_ERR_UNSUPPORTED (N outside 1..7, geometry),
+ * SM_ERR_OOM, SM_ERR_CUDA. */
+int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out);
+
+/* Sets the motion (Sec. 4.3: Delta = (n + s) l).  Takes effect at the next stage. */
+int sm_set_motion(sm_solver* s, const sm_motion* motion);
+
+/* Number of scalars of the state U (elements * 5 * (N+1)^3) and bytes per scalar. */
+long long sm_state_size(const sm_solver* s);
+int sm_scalar_bytes(const sm_solver* s);
+
+/* Evaluates the desc's flow at t = 0 at every node into the solver state (on the device),
+ * sets t = 0 and clears the RK register.  Asynchronous on stream. */
+int sm_init_state(sm_solver* s, void* stream);
+
+/* Copies a state in (U: host or device pointer in the solver's precision and layout;
+ * on_device = 0 for host memory) and sets the solver time t.  Host copies go through the
+ * given stream and the call returns after the copy has been issued; the caller keeps U
+ * unchanged until the stream reaches this point (pinned host memory makes the copy
+ * asynchronous, pageable memory makes it synchronous). */
+int sm_set_state(sm_solver* s, const void* U, int on_device, double t, void* stream);
+
+/* Copies the state out (host or device pointer) and returns the solver time in *t.
+ * Synchronises the stream before returning. */
+int sm_get_state(sm_solver* s, void* U, int on_device, double* t, void* stream);
+
+/* dU/dt = R(U, t) for a caller-owned device state dU into caller-owned dUt (same layout
+ * and precision), on stream: mapper and mortar matrices at time t (Sec. 4.3, 3.2), the
+ * fused interface kernel (Sec. 3.3 steps 3-5), then volume + surface (Sec. 3.1).
+ * dU and dUt must not overlap.  The solver's own state is not touched. */
+int sm_rhs(sm_solver* s, double t, const void* dU, void* dUt, void* stream);
+
+/* The interface operator alone (Sec. 3.3 steps 1-5) for the device state dU at time t:
+ * writes both sides' face fluxes (layout above, 5 (N+1)^2 scalars per face) into the
+ * caller-owned device arrays dF_static and dF_moving. */
+int sm_interface(sm_solver* s, double t, const void* dU, void* dF_static, void* dF_moving, void* stream);
+
+/* Advances the solver state by nsteps low-storage RK4 steps of size dt (five stages each,
+ * stage time t + c_k dt computed on the device as fma(c_k, dt, t)).  Asynchronous on
+ * stream; the steps are replayed from a CUDA graph captured per (dt, buffer parity).
+ * The solver time advances by dt per step. */
+int sm_step(sm_solver* s, double dt, int nsteps, void* stream);
+
+/* The same stage sequence as sm_step, launched kernel by kernel (no graph) with a CUDA
+ * event pair around every launch on stream; synchronises.  ms_out[3] receives the summed
+ * device time of the mapper, interface and element kernels, launches_out[3] their launch
+ * counts (either may be NULL).  For measurement only: the state advances exactly as with
+ * sm_step. */
+int sm_step_profiled(sm_solver* s, double dt, int nsteps, void* stream, double* ms_out, int* launches_out);
+
+/* Diagnostics of the current state (synchronises stream).  Returns SM_ERR_NONFINITE if
+ * a total is not finite. */
+int sm_diag(sm_solver* s, sm_diag_out* out, void* stream);
+
+/* Device pointer to the solver's current state buffer (valid until the next sm_step). */
+void* sm_state_ptr(sm_solver* s);
+
+void sm_destroy(sm_solver* s);
+
+/* ---- building blocks exposed for testing ---- */
+
+/* Interface configuration for count displacements (Sec. 4.3): for each d_delta[m],
+ * q = delta / l, n = floor(q), s = q - n (IEEE FP64, no contraction), and the moving
+ * partners of every static face i of a line of n_par faces by Eq. indices,
+ * d_pairs[(m * n_par + i) * 2 + i_sub] = (i - n + i_sub - 1) mod n_par.
+ * All pointers are device pointers; d_pairs may be NULL. */
+int sm_map(const double* d_delta, int count, double l, int n_par, long long* d_n, double* d_s,
+           int* d_pairs, void* stream);
+
+/* Mortar operators for a face whose hanging node sits at sigma (Sec. 3.2, Eqs.
+ * projection_domain_mortar and projection_mortar_domain), built in FP64 on the device:
+ * d_out (device) receives P_lo, P_hi, B_lo, B_hi, each (N+1)^2 row-major, where
+ * P[j][i] maps face node i to mortar node j and B[i][j] maps mortar node j to face
+ * node i; lo is the mortar xi <= sigma (Jacobian (1+sigma)/2), hi the mortar xi > sigma. */
+int sm_mortar_matrices(int N, double sigma, double* d_out, void* stream);
+
+const char* sm_status_string(int status);
+const char* sm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,107 @@
+// Initial data and deterministic diagnostics (not on the per-stage path).
+//   - init_state: the flow's state at every node at t = 0 (moving block displaced by delta0);
+//   - totals: sum_e sum_ijk J w_i w_j w_k U (the conserved integrals of Sec. 3.1's weak form);
+//   - face sums: sum over interface faces of w_p w_q F (discrete mortar conservation).
+// Reductions are two-pass in FP64 with a fixed order, so repeated calls agree bit for bit.
+#include "sm_launch.h"
+
+namespace {
+
+template <typename T>
+__global__ void init_state_kernel(const MeshDev m, int np, T* U) {
+  const long long nn = (long long)np * np * np;
+  const long long total = m.E * nn;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total; g += (long long)gridDim.x * blockDim.x) {
+    const long long e = g / nn;
+    const int nd = (int)(g - e * nn);
+    const int i = nd % np, j = (nd / np) % np, k = nd / (np * np);
+    ElemPos p = decode_elem(m, e);
+    double X[3], u[5];
+    node_position(m, p, i, j, k, __fma_rn(m.v, 0.0, m.delta0), X);
+    flow_state(m, X[0], X[1], X[2], 0.0, 0, u);
+    for (int v = 0; v < 5; ++v) U[(e * 5 + v) * nn + nd] = (T)u[v];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) totals_kernel(const MeshDev m, int np, const T* U, double* partial) {
+  __shared__ double red[5][256];
+  const long long nn = (long long)np * np * np;
+  const long long total = m.E * nn;
+  double acc[5] = {0, 0, 0, 0, 0};
+  const double* w = m.basis->w;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total; g += (long long)gridDim.x * blockDim.x) {
+    const long long e = g / nn;
+    const int nd = (int)(g - e * nn);
+    const int i = nd % np, j = (nd / np) % np, k = nd / (np * np);
+    const double wq = elem_jacobian(m, e >= m.Es) * w[i] * w[j] * w[k];
+    for (int v = 0; v < 5; ++v) acc[v] += wq * (double)U[(e * 5 + v) * nn + nd];
+  }
+  for (int v = 0; v < 5; ++v) red[v][threadIdx.x] = acc[v];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int v = 0; v < 5; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partial[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) face_sums_kernel(const MeshDev m, int np, const T* F, double* partial) {
+  __shared__ double red[5][256];
+  const int n2 = np * np;
+  const long long total = (long long)m.ny * m.nz * n2;
+  double acc[5] = {0, 0, 0, 0, 0};
+  const double* w = m.basis->w;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total; g += (long long)gridDim.x * blockDim.x) {
+    const long long f = g / n2;
+    const int ab = (int)(g - f * n2);
+    const double wq = w[ab % np] * w[ab / np];
+    for (int v = 0; v < 5; ++v) acc[v] += wq * (double)F[(f * 5 + v) * n2 + ab];
+  }
+  for (int v = 0; v < 5; ++v) red[v][threadIdx.x] = acc[v];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int v = 0; v < 5; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partial[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void finish_sum_kernel(const double* partial, int nblk, double* out5) {
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[b * 5 + threadIdx.x];
+    out5[threadIdx.x] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_init_state(int N, int prec, const MeshDev& m, void* U, cudaStream_t st) {
+  const int np = N + 1;
+  const int blocks = 152 * 8;
+  if (prec == 0) init_state_kernel<double><<<blocks, 256, 0, st>>>(m, np, (double*)U);
+  else init_state_kernel<float><<<blocks, 256, 0, st>>>(m, np, (float*)U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_totals(int N, int prec, const MeshDev& m, const void* U, double* partial, int nblk, double* out5,
+                          cudaStream_t st) {
+  const int np = N + 1;
+  if (prec == 0) totals_kernel<double><<<nblk, 256, 0, st>>>(m, np, (const double*)U, partial);
+  else totals_kernel<float><<<nblk, 256, 0, st>>>(m, np, (const float*)U, partial);
+  finish_sum_kernel<<<1, 32, 0, st>>>(partial, nblk, out5);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_sums(int N, int prec, const MeshDev& m, const void* F, double* partial, int nblk,
+                             double* out5, cudaStream_t st) {
+  const int np = N + 1;
+  if (prec == 0) face_sums_kernel<double><<<nblk, 256, 0, st>>>(m, np, (const double*)F, partial);
+  else face_sums_kernel<float><<<nblk, 256, 0, st>>>(m, np, (const float*)F, partial);
+  finish_sum_kernel<<<1, 32, 0, st>>>(partial, nblk, out5);
+  return cudaGetLastError();
+}

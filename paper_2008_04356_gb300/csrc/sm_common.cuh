@@ -1,0 +1,259 @@
+// Device-side building blocks of the sliding-mesh DGSEM hot path (sm_103a).
+//
+// Geometry of the two-block plane interface, the ALE Euler fluxes of Sec. 2
+// (Eq. fluxes_written_out), the Rusanov and Roe/Harten-Hyman Riemann solvers named in
+// Sec. 3.1, and the flows used for initial and weak Dirichlet data.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SM_MAXNP 8
+#define SM_PI 3.14159265358979323846
+
+// Basis of degree N on Legendre-Gauss-Lobatto nodes, built in FP64 on the host once per
+// solver.  Dhat_il = -(w_l / w_i) D_li is the weak-form derivative of Sec. 3.1
+// (Eq. weak_formulation with collocated LGL quadrature).
+struct BasisDev {
+  double x[SM_MAXNP], w[SM_MAXNP], lam[SM_MAXNP];   // nodes, weights, barycentric weights
+  double M[SM_MAXNP * SM_MAXNP], Minv[SM_MAXNP * SM_MAXNP];  // exact mass matrix, inverse
+  double Dhat[SM_MAXNP * SM_MAXNP];
+  float Dhat_f[SM_MAXNP * SM_MAXNP];
+  float x_f[SM_MAXNP], w_f[SM_MAXNP];
+};
+
+// Per-stage interface configuration (Sec. 4.3) and mortar operators (Sec. 3.2), written by
+// the mapper kernel before the interface kernel runs.  Matrix order: 0 Ps_lo, 1 Ps_hi,
+// 2 Pm_lo, 3 Pm_hi (forward, [mortar node][face node]), 4 Bs_lo, 5 Bs_hi, 6 Bm_lo, 7 Bm_hi
+// (back, [face node][mortar node]); s = static face (hanging node sigma_s = 2s - 1),
+// m = moving face (sigma_m = 1 - 2s).
+struct StageParams {
+  double t;            // stage time
+  double delta;        // displacement of the moving block
+  long long n;         // integer face offset
+  double s;            // sub-face fraction
+  double sig_s, sig_m;
+  double mat[8][SM_MAXNP * SM_MAXNP];
+  float mat_f[8][SM_MAXNP * SM_MAXNP];
+};
+
+// Mesh and physics description passed to kernels by value.
+struct MeshDev {
+  int nxs, nxm, ny, nz;
+  long long Es, E;
+  double hx0, hx1, hy, hz;
+  double x0, x1, y0, z0;
+  double gamma;
+  double v, delta0;
+  int conforming;
+  int flow;
+  double fpar[16];
+  const double* modes;        // [5][8][4] device
+  const BasisDev* basis;      // device
+};
+
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+  static __device__ __forceinline__ const double* dhat(const BasisDev* b) { return b->Dhat; }
+  static __device__ __forceinline__ const double* w(const BasisDev* b) { return b->w; }
+  static __device__ __forceinline__ const double* mat(const StageParams* p, int k) { return p->mat[k]; }
+};
+template <> struct Prec<float> {
+  static __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
+  static __device__ __forceinline__ const float* dhat(const BasisDev* b) { return b->Dhat_f; }
+  static __device__ __forceinline__ const float* w(const BasisDev* b) { return b->w_f; }
+  static __device__ __forceinline__ const float* mat(const StageParams* p, int k) { return p->mat_f[k]; }
+};
+
+// ---------------------------------------------------------------------------------------
+// Element / face geometry.  Element e: static block first (e < Es), local index
+// ix + nx (iy + ny iz).  Reference axes: xi^1 -> y, xi^2 -> z, xi^3 -> x.
+// Faces of an element are f = 2 d + side, d the reference direction, side 0 = minus.
+// Face nodes a + np b:  d=0: (a,b)=(j,k);  d=1: (a,b)=(i,k);  d=2: (a,b)=(i,j).
+// ---------------------------------------------------------------------------------------
+struct ElemPos { int blk, ix, iy, iz; };
+
+__device__ __forceinline__ ElemPos decode_elem(const MeshDev& m, long long e) {
+  ElemPos p;
+  long long loc = e;
+  int nx = m.nxs;
+  p.blk = 0;
+  if (e >= m.Es) { p.blk = 1; loc = e - m.Es; nx = m.nxm; }
+  long long r = loc / nx;
+  p.ix = (int)(loc - r * nx);
+  p.iy = (int)(r % m.ny);
+  p.iz = (int)(r / m.ny);
+  return p;
+}
+
+__device__ __forceinline__ long long encode_elem(const MeshDev& m, int blk, int ix, int iy, int iz) {
+  int nx = blk ? m.nxm : m.nxs;
+  return (blk ? m.Es : 0) + ix + (long long)nx * (iy + (long long)m.ny * iz);
+}
+
+template <int NP>
+__device__ __forceinline__ int face_vol_node(int d, int side, int a, int b) {
+  const int f = side ? NP - 1 : 0;
+  return d == 0 ? f + NP * (a + NP * b) : (d == 1 ? a + NP * (f + NP * b) : a + NP * (b + NP * f));
+}
+
+// Neighbour across face (d, side): kind 0 conforming (returns element), 1 weak Dirichlet
+// boundary (x = x0 of the static block, x = x2 of the moving block), 2 sliding interface.
+__device__ __forceinline__ int face_neighbor(const MeshDev& m, const ElemPos& p, int d, int side, long long* nb) {
+  if (d == 0) {
+    int iy = p.iy + (side ? 1 : -1);
+    iy = iy < 0 ? iy + m.ny : (iy >= m.ny ? iy - m.ny : iy);
+    *nb = encode_elem(m, p.blk, p.ix, iy, p.iz);
+    return 0;
+  }
+  if (d == 1) {
+    int iz = p.iz + (side ? 1 : -1);
+    iz = iz < 0 ? iz + m.nz : (iz >= m.nz ? iz - m.nz : iz);
+    *nb = encode_elem(m, p.blk, p.ix, p.iy, iz);
+    return 0;
+  }
+  int nx = p.blk ? m.nxm : m.nxs;
+  int jx = p.ix + (side ? 1 : -1);
+  if (jx >= 0 && jx < nx) { *nb = encode_elem(m, p.blk, jx, p.iy, p.iz); return 0; }
+  if ((p.blk == 0 && side == 0) || (p.blk == 1 && side == 1)) return 1;
+  if (m.conforming) {
+    int ob = 1 - p.blk;
+    *nb = encode_elem(m, ob, ob == 0 ? m.nxs - 1 : 0, p.iy, p.iz);
+    return 0;
+  }
+  return 2;
+}
+
+// |Ja^d| (surface element of the xi^{d+1} faces) and the Jacobian of a Cartesian element.
+__device__ __forceinline__ double face_metric(const MeshDev& m, int blk, int d) {
+  double hx = blk ? m.hx1 : m.hx0;
+  return d == 0 ? m.hz * hx * 0.25 : (d == 1 ? hx * m.hy * 0.25 : m.hy * m.hz * 0.25);
+}
+__device__ __forceinline__ double elem_jacobian(const MeshDev& m, int blk) {
+  return (blk ? m.hx1 : m.hx0) * m.hy * m.hz * 0.125;
+}
+
+// ---------------------------------------------------------------------------------------
+// Physics (Sec. 2).  U = (rho, rho v, rho e); perfect gas.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T pressure(const T U[5], T gamma) {
+  T ir = T(1) / U[0];
+  return (gamma - T(1)) * (U[4] - T(0.5) * ir * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]));
+}
+
+// Flux along physical axis AX (0 = x, 1 = y, 2 = z) minus grid transport vg * U.
+template <typename T, int AX>
+__device__ __forceinline__ void axis_flux(const T U[5], T p, T vg, T F[5]) {
+  T ua = U[1 + AX] / U[0];
+  T un = ua - vg;
+  F[0] = U[0] * un;
+  F[1] = U[1] * un + (AX == 0 ? p : T(0));
+  F[2] = U[2] * un + (AX == 1 ? p : T(0));
+  F[3] = U[3] * un + (AX == 2 ? p : T(0));
+  F[4] = U[4] * un + p * ua;
+}
+
+// Riemann flux across a face with unit normal along +AX, grid normal velocity vgn.
+// RIEM 0: Rusanov (local Lax-Friedrichs); RIEM 1: Roe with the Harten-Hyman entropy fix.
+template <typename T, int AX, int RIEM>
+__device__ __forceinline__ void riemann_axis(const T UL[5], const T UR[5], T vgn, T gamma, T F[5]) {
+  T pL = pressure(UL, gamma), pR = pressure(UR, gamma);
+  T FL[5], FR[5];
+  axis_flux<T, AX>(UL, pL, vgn, FL);
+  axis_flux<T, AX>(UR, pR, vgn, FR);
+  T irL = T(1) / UL[0], irR = T(1) / UR[0];
+  T unL = UL[1 + AX] * irL, unR = UR[1 + AX] * irR;
+  T cL = Prec<T>::sqrt_(gamma * pL * irL), cR = Prec<T>::sqrt_(gamma * pR * irR);
+  if (RIEM == 0) {
+    T a = fmax(fabs(unL - vgn) + cL, fabs(unR - vgn) + cR);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * a * (UR[k] - UL[k]);
+    return;
+  }
+  // Roe-averaged state
+  T sL = Prec<T>::sqrt_(UL[0]), sR = Prec<T>::sqrt_(UR[0]);
+  T iss = T(1) / (sL + sR);
+  T uL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
+  T uR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
+  T uh[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) uh[d] = (sL * uL[d] + sR * uR[d]) * iss;
+  T HL = (UL[4] + pL) * irL, HR = (UR[4] + pR) * irR;
+  T Hh = (sL * HL + sR * HR) * iss;
+  T q2 = uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2];
+  T ch = Prec<T>::sqrt_((gamma - T(1)) * (Hh - T(0.5) * q2));
+  T rh = sL * sR;
+  T unh = uh[AX];
+  T dp = pR - pL, dr = UR[0] - UL[0], dun = unR - unL;
+  T ic2 = T(1) / (ch * ch);
+  T a1 = T(0.5) * (dp - rh * ch * dun) * ic2;   // left acoustic wave
+  T a5 = T(0.5) * (dp + rh * ch * dun) * ic2;   // right acoustic wave
+  T a2 = dr - dp * ic2;                          // entropy wave
+  T l1 = unh - ch - vgn, l2 = unh - vgn, l5 = unh + ch - vgn;
+  T al1 = fabs(l1), al2 = fabs(l2), al5 = fabs(l5);
+  // Harten-Hyman: widen |lambda| of an acoustic wave that opens across zero
+  T d1 = fmax(T(0), fmax(l1 - (unL - cL - vgn), (unR - cR - vgn) - l1));
+  if (al1 < d1) al1 = (l1 * l1 + d1 * d1) / (T(2) * d1);
+  T d5 = fmax(T(0), fmax(l5 - (unL + cL - vgn), (unR + cR - vgn) - l5));
+  if (al5 < d5) al5 = (l5 * l5 + d5 * d5) / (T(2) * d5);
+  T w1 = al1 * a1, w5 = al5 * a5, w2 = al2 * a2;
+  T du[3] = {uR[0] - uL[0], uR[1] - uL[1], uR[2] - uL[2]};
+  T D[5];
+  D[0] = w1 + w2 + w5;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T shear = du[d] - (d == AX ? dun : T(0));
+    T nd = d == AX ? ch : T(0);
+    D[1 + d] = w1 * (uh[d] - nd) + w2 * uh[d] + al2 * rh * shear + w5 * (uh[d] + nd);
+  }
+  T udu = uh[0] * du[0] + uh[1] * du[1] + uh[2] * du[2];
+  D[4] = w1 * (Hh - unh * ch) + w2 * T(0.5) * q2 + al2 * rh * (udu - unh * dun) + w5 * (Hh + unh * ch);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * D[k];
+}
+
+// ---------------------------------------------------------------------------------------
+// Flows: initial data and the weak Dirichlet boundary state (boundary = 1).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void flow_state(const MeshDev& m, double x, double y, double z, double t,
+                                           int boundary, double U[5]) {
+  double P[5];
+  const double* f = m.fpar;
+  if (m.flow == 0) {
+    for (int k = 0; k < 5; ++k) P[k] = f[k];
+  } else if (m.flow == 1) {
+    double ph = f[2] * (x - f[5] * t) + f[3] * (y - f[6] * t) + f[4] * (z - f[7] * t);
+    P[0] = f[0] + f[1] * sin(2.0 * SM_PI * ph);
+    P[1] = f[5]; P[2] = f[6]; P[3] = f[7]; P[4] = f[8];
+  } else if (m.flow == 2) {
+    for (int k = 0; k < 5; ++k) P[k] = f[k];
+    if (!boundary)
+      for (int k = 0; k < 5; ++k)
+        for (int q = 0; q < 8; ++q) {
+          const double* md = m.modes + (k * 8 + q) * 4;
+          P[k] += md[0] * sin(2.0 * SM_PI * (md[1] * y + md[2] * z) + md[3]);
+        }
+  } else {
+    double xs = x - f[4] * t;
+    P[0] = f[0] + xs * (f[1] + xs * (f[2] + xs * f[3]));
+    P[1] = f[4]; P[2] = f[5]; P[3] = f[6]; P[4] = f[7];
+  }
+  U[0] = P[0];
+  U[1] = P[0] * P[1];
+  U[2] = P[0] * P[2];
+  U[3] = P[0] * P[3];
+  U[4] = P[4] / (m.gamma - 1.0) + 0.5 * P[0] * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
+}
+
+// Physical position of node (i, j, k) of element p; the moving block is shifted by delta.
+__device__ __forceinline__ void node_position(const MeshDev& m, const ElemPos& p, int i, int j, int k,
+                                              double delta, double X[3]) {
+  const double* xi = m.basis->x;
+  double hx = p.blk ? m.hx1 : m.hx0;
+  double xlo = p.blk ? m.x1 : m.x0;
+  X[0] = xlo + p.ix * hx + (xi[k] + 1.0) * 0.5 * hx;
+  X[1] = m.y0 + p.iy * m.hy + (xi[i] + 1.0) * 0.5 * m.hy + (p.blk ? delta : 0.0);
+  X[2] = m.z0 + p.iz * m.hz + (xi[j] + 1.0) * 0.5 * m.hz;
+}

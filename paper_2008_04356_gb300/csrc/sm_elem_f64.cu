@@ -1,0 +1,8 @@
+// Element kernel instantiations, double state (N = 1..7, Rusanov / Roe, three modes).
+#include "sm_element.cuh"
+
+cudaError_t launch_element_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st) {
+  SM_ELEM_DISPATCH(double, N, riemann, mode, a, st)
+}
+
+cudaError_t prepare_element_f64(int N) { SM_ELEM_PREPARE(double, N) }

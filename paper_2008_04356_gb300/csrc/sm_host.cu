@@ -1,0 +1,559 @@
+// Host side of the C-ABI (include/slidemesh.h): solver set-up, stage sequencing and CUDA
+// graph replay of whole Runge-Kutta steps.
+//
+// Per stage k of a step (Carpenter-Kennedy five-stage RK4, Sec. 3.1):
+//   1. stage_params: t_k = fma(c_k, dt, t), Delta(t_k), (n, s), mortar operators (Sec. 4.3, 3.2)
+//   2. sliding_interface: both sides' interface face fluxes (Sec. 3.3 steps 3-5)
+//   3. dg_element: volume + surface integral and G = A_k G + dt R, U' = U + B_k G
+// U ping-pongs between two buffers because neighbour traces are read from the state of the
+// previous stage while the element kernel writes the new one.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/slidemesh.h"
+#include "sm_launch.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* what, cudaError_t e = cudaSuccess) {
+  char buf[512];
+  if (e != cudaSuccess)
+    snprintf(buf, sizeof(buf), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  else
+    snprintf(buf, sizeof(buf), "%s", what);
+  g_last_error = buf;
+  return code;
+}
+
+#define SM_CK(call, what)                                          \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return fail(SM_ERR_CUDA, what, e_);     \
+  } while (0)
+
+// Legendre polynomial P_n and derivative (three-term recurrence).
+void legendre_pd(int n, double x, double* p, double* dp) {
+  double a = 1.0, b = x, da = 0.0, db = 1.0;
+  if (n == 0) { *p = 1.0; *dp = 0.0; return; }
+  for (int k = 2; k <= n; ++k) {
+    double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+    double dc = k * b + x * db;   // P_k' = k P_{k-1} + x P_{k-1}'
+    a = b; b = c; da = db; db = dc;
+  }
+  (void)da;
+  *p = b;
+  *dp = db;
+}
+
+// LGL nodes: the N+1 roots of q(x) = P_{N+1}(x) - P_{N-1}(x) (which vanishes at +-1 and at
+// the roots of P_N'), found by Newton from Chebyshev-Gauss-Lobatto points, symmetrised.
+void lgl_basis(int N, BasisDev& b) {
+  memset(&b, 0, sizeof(b));
+  const int np = N + 1;
+  for (int j = 0; j < np; ++j) {
+    double x = -cos(M_PI * j / N);
+    for (int it = 0; it < 60; ++it) {
+      double p1, d1, p0, d0;
+      legendre_pd(N + 1, x, &p1, &d1);
+      legendre_pd(N - 1, x, &p0, &d0);
+      double dx = (p1 - p0) / (d1 - d0);
+      x -= dx;
+      if (fabs(dx) < 1e-17) break;
+    }
+    b.x[j] = x;
+  }
+  for (int j = 0; j < np / 2; ++j) {
+    double a = 0.5 * (b.x[N - j] - b.x[j]);
+    b.x[j] = -a;
+    b.x[N - j] = a;
+  }
+  b.x[0] = -1.0;
+  b.x[N] = 1.0;
+  if (np % 2 == 1) b.x[N / 2] = 0.0;
+  for (int j = 0; j < np; ++j) {
+    double p, dp;
+    legendre_pd(N, b.x[j], &p, &dp);
+    b.w[j] = 2.0 / (N * (N + 1.0) * p * p);
+  }
+  for (int i = 0; i < np; ++i) {
+    double prod = 1.0;
+    for (int k = 0; k < np; ++k)
+      if (k != i) prod *= (b.x[i] - b.x[k]);
+    b.lam[i] = 1.0 / prod;
+  }
+  // exact mass matrix of the Lagrange basis, M = V^-T diag(2/(2k+1)) V^-1 and its inverse
+  // M^-1 = V diag((2k+1)/2) V^T, with the Legendre Vandermonde V_ik = P_k(x_i)
+  double V[SM_MAXNP][SM_MAXNP], Vi[SM_MAXNP][SM_MAXNP];
+  for (int i = 0; i < np; ++i)
+    for (int k = 0; k < np; ++k) {
+      double p, dp;
+      legendre_pd(k, b.x[i], &p, &dp);
+      V[i][k] = p;
+    }
+  // invert V (Gauss-Jordan, partial pivoting)
+  double A[SM_MAXNP][2 * SM_MAXNP];
+  for (int i = 0; i < np; ++i)
+    for (int k = 0; k < 2 * np; ++k) A[i][k] = k < np ? V[i][k] : (k - np == i ? 1.0 : 0.0);
+  for (int c = 0; c < np; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < np; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    for (int k = 0; k < 2 * np; ++k) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+    double d = A[c][c];
+    for (int k = 0; k < 2 * np; ++k) A[c][k] /= d;
+    for (int r = 0; r < np; ++r)
+      if (r != c) {
+        double f = A[r][c];
+        for (int k = 0; k < 2 * np; ++k) A[r][k] -= f * A[c][k];
+      }
+  }
+  for (int i = 0; i < np; ++i)
+    for (int k = 0; k < np; ++k) Vi[i][k] = A[i][np + k];
+  for (int i = 0; i < np; ++i)
+    for (int j = 0; j < np; ++j) {
+      double m = 0.0, mi = 0.0;
+      for (int k = 0; k < np; ++k) {
+        m += Vi[k][i] * (2.0 / (2 * k + 1)) * Vi[k][j];
+        mi += V[i][k] * ((2 * k + 1) / 2.0) * V[j][k];
+      }
+      b.M[i * SM_MAXNP + j] = m;
+      b.Minv[i * SM_MAXNP + j] = mi;
+    }
+  // D_ij = ell_j'(x_i) from barycentric weights; Dhat_il = -(w_l / w_i) D_li
+  double D[SM_MAXNP][SM_MAXNP];
+  for (int i = 0; i < np; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < np; ++j)
+      if (j != i) {
+        D[i][j] = (b.lam[j] / b.lam[i]) / (b.x[i] - b.x[j]);
+        diag -= D[i][j];
+      }
+    D[i][i] = diag;
+  }
+  for (int i = 0; i < np; ++i)
+    for (int l = 0; l < np; ++l) {
+      double dh = -(b.w[l] / b.w[i]) * D[l][i];
+      b.Dhat[i * SM_MAXNP + l] = dh;
+      b.Dhat_f[i * SM_MAXNP + l] = (float)dh;
+    }
+  for (int j = 0; j < np; ++j) {
+    b.x_f[j] = (float)b.x[j];
+    b.w_f[j] = (float)b.w[j];
+  }
+}
+
+// Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage scheme.
+const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                        2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+struct GraphEntry {
+  double dt;
+  int cur;
+  cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct sm_solver {
+  sm_mesh_desc desc;
+  sm_motion motion;
+  int N, np, prec, sb;
+  long long nn, nstate, nface_vals;
+  MeshDev m;
+  BasisDev basis_h;
+  BasisDev* basis_d = nullptr;
+  double* modes_d = nullptr;
+  void* U[2] = {nullptr, nullptr};
+  void* G = nullptr;
+  void* Fs = nullptr;
+  void* Fm = nullptr;
+  StageParams* sp = nullptr;
+  double* t_d = nullptr;
+  double* red_d = nullptr;      // partial sums [nblk][5] + outputs [3][5]
+  int red_blocks = 0;
+  int cur = 0;
+  double t_host = 0.0;
+  cudaStream_t cap = nullptr;
+  std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+cudaError_t enqueue_rhs_parts(sm_solver* s, double t, const void* dU, void* Fs, void* Fm, cudaStream_t st) {
+  cudaError_t e = launch_stage_params(s->m, s->np, s->sp, s->t_d, t, 0.0, 0.0, 0, st);
+  if (e != cudaSuccess) return e;
+  if (!s->desc.interface_conforming) e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st);
+  return e;
+}
+
+cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a, cudaStream_t st) {
+  return s->prec == SM_FP64 ? launch_element_f64(s->N, s->desc.riemann, mode, a, st)
+                            : launch_element_f32(s->N, s->desc.riemann, mode, a, st);
+}
+
+cudaError_t enqueue_step(sm_solver* s, double dt, int cur, cudaStream_t st) {
+  int c = cur;
+  for (int k = 0; k < 5; ++k) {
+    cudaError_t e = launch_stage_params(s->m, s->np, s->sp, s->t_d, 0.0, RK_C[k], dt, k == 4 ? 2 : 1, st);
+    if (e != cudaSuccess) return e;
+    if (!s->desc.interface_conforming) {
+      e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, s->U[c], s->Fs, s->Fm, st);
+      if (e != cudaSuccess) return e;
+    }
+    ElemArgs a{s->m, s->sp, s->U[c], s->U[1 - c], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
+    e = launch_elem(s, k == 0 ? ELEM_STAGE_FIRST : ELEM_STAGE, a, st);
+    if (e != cudaSuccess) return e;
+    c ^= 1;
+  }
+  return cudaSuccess;
+}
+
+void clear_graphs(sm_solver* s) {
+  for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
+}
+
+int get_graph(sm_solver* s, double dt, int cur, cudaGraphExec_t* out) {
+  for (auto& g : s->graphs)
+    if (g.dt == dt && g.cur == cur) { *out = g.exec; return SM_OK; }
+  if (s->graphs.size() >= 8) clear_graphs(s);
+  SM_CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t e = enqueue_step(s, dt, cur, s->cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s->cap, &graph);
+  if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return fail(SM_ERR_CUDA, "capture step", e); }
+  if (e2 != cudaSuccess) return fail(SM_ERR_CUDA, "end capture", e2);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "instantiate step graph", e);
+  s->graphs.push_back({dt, cur, exec});
+  *out = exec;
+  return SM_OK;
+}
+
+void free_solver(sm_solver* s) {
+  if (!s) return;
+  clear_graphs(s);
+  if (s->cap) cudaStreamDestroy(s->cap);
+  void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->t_d, s->red_d};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete s;
+}
+
+int valid_desc(const sm_mesh_desc* d) {
+  if (!d) return fail(SM_ERR_ARG, "desc is NULL");
+  if (d->N < 1 || d->N > 7) return fail(SM_ERR_UNSUPPORTED, "N must be in 1..7");
+  if (d->geom != SM_GEOM_PLANE) return fail(SM_ERR_UNSUPPORTED, "only the plane interface geometry is built");
+  for (int k = 0; k < 3; ++k)
+    if (d->nel_static[k] < 1 || d->nel_moving[k] < 1) return fail(SM_ERR_ARG, "element counts must be >= 1");
+  if (d->nel_static[1] != d->nel_moving[1] || d->nel_static[2] != d->nel_moving[2])
+    return fail(SM_ERR_ARG, "interface faces must match: nel_static[1..2] == nel_moving[1..2]");
+  if (!(d->x1 > d->x0 && d->x2 > d->x1 && d->y1 > d->y0 && d->z1 > d->z0)) return fail(SM_ERR_ARG, "empty block extent");
+  if (!(d->gamma > 1.0)) return fail(SM_ERR_ARG, "gamma must exceed 1");
+  if (d->riemann != SM_RUSANOV && d->riemann != SM_ROE_HH) return fail(SM_ERR_ARG, "unknown Riemann solver");
+  if (d->precision != SM_FP64 && d->precision != SM_FP32) return fail(SM_ERR_ARG, "unknown precision");
+  if (d->flow < 0 || d->flow > 3) return fail(SM_ERR_ARG, "unknown flow");
+  long long E = (long long)(d->nel_static[0] + d->nel_moving[0]) * d->nel_static[1] * d->nel_static[2];
+  if (E > (1LL << 31)) return fail(SM_ERR_ARG, "too many elements");
+  return SM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sm_status_string(int st) {
+  switch (st) {
+    case SM_OK: return "ok";
+    case SM_PENDING: return "pending";
+    case SM_ERR_ARG: return "invalid argument";
+    case SM_ERR_OOM: return "out of device memory";
+    case SM_ERR_CUDA: return "CUDA error";
+    case SM_ERR_NONFINITE: return "non-finite state";
+    case SM_ERR_TIMEOUT: return "timeout";
+    case SM_ERR_BUSY: return "busy";
+    case SM_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* sm_last_error(void) { return g_last_error.c_str(); }
+
+int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
+  if (!out) return fail(SM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = valid_desc(desc);
+  if (rc != SM_OK) return rc;
+  sm_solver* s = new (std::nothrow) sm_solver();
+  if (!s) return fail(SM_ERR_OOM, "host allocation");
+  s->desc = *desc;
+  s->motion = {0.0, 0.0, 0.0};
+  s->N = desc->N;
+  s->np = desc->N + 1;
+  s->nn = (long long)s->np * s->np * s->np;
+  s->prec = desc->precision;
+  s->sb = s->prec == SM_FP64 ? 8 : 4;
+  lgl_basis(s->N, s->basis_h);
+  MeshDev& m = s->m;
+  memset(&m, 0, sizeof(m));
+  m.nxs = desc->nel_static[0];
+  m.nxm = desc->nel_moving[0];
+  m.ny = desc->nel_static[1];
+  m.nz = desc->nel_static[2];
+  m.Es = (long long)m.nxs * m.ny * m.nz;
+  m.E = m.Es + (long long)m.nxm * m.ny * m.nz;
+  m.hx0 = (desc->x1 - desc->x0) / m.nxs;
+  m.hx1 = (desc->x2 - desc->x1) / m.nxm;
+  m.hy = (desc->y1 - desc->y0) / m.ny;
+  m.hz = (desc->z1 - desc->z0) / m.nz;
+  m.x0 = desc->x0;
+  m.x1 = desc->x1;
+  m.y0 = desc->y0;
+  m.z0 = desc->z0;
+  m.gamma = desc->gamma;
+  m.conforming = desc->interface_conforming;
+  m.flow = desc->flow;
+  for (int k = 0; k < 16; ++k) m.fpar[k] = desc->fpar[k];
+  s->nstate = m.E * 5 * s->nn;
+  s->nface_vals = (long long)m.ny * m.nz * 5 * s->np * s->np;
+  s->red_blocks = 304;
+  const size_t sbytes = (size_t)s->nstate * s->sb, fbytes = (size_t)s->nface_vals * s->sb;
+  cudaError_t e;
+#define SM_ALLOC(ptr, bytes)                                                        \
+  e = cudaMalloc((void**)&(ptr), (bytes));                                          \
+  if (e != cudaSuccess) {                                                           \
+    cudaGetLastError();                                                             \
+    free_solver(s);                                                                 \
+    return fail(e == cudaErrorMemoryAllocation ? SM_ERR_OOM : SM_ERR_CUDA, "cudaMalloc", e); \
+  }
+  SM_ALLOC(s->basis_d, sizeof(BasisDev));
+  SM_ALLOC(s->modes_d, sizeof(double) * 160);
+  SM_ALLOC(s->U[0], sbytes);
+  SM_ALLOC(s->U[1], sbytes);
+  SM_ALLOC(s->G, sbytes);
+  SM_ALLOC(s->Fs, fbytes);
+  SM_ALLOC(s->Fm, fbytes);
+  SM_ALLOC(s->sp, sizeof(StageParams));
+  SM_ALLOC(s->t_d, sizeof(double));
+  SM_ALLOC(s->red_d, sizeof(double) * (s->red_blocks * 5 + 15));
+#undef SM_ALLOC
+  m.basis = s->basis_d;
+  m.modes = s->modes_d;
+  const char* what = nullptr;
+  if ((e = cudaMemcpy(s->basis_d, &s->basis_h, sizeof(BasisDev), cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload basis";
+  else if ((e = cudaMemcpy(s->modes_d, &desc->modes[0][0][0], sizeof(double) * 160, cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload modes";
+  else if ((e = cudaMemset(s->G, 0, sbytes)) != cudaSuccess) what = "clear G";
+  else if ((e = cudaMemset(s->U[0], 0, sbytes)) != cudaSuccess) what = "clear U";
+  else if ((e = cudaMemset(s->Fs, 0, fbytes)) != cudaSuccess || (e = cudaMemset(s->Fm, 0, fbytes)) != cudaSuccess) what = "clear F";
+  else if ((e = cudaMemset(s->t_d, 0, sizeof(double))) != cudaSuccess) what = "clear t";
+  else if ((e = cudaMemset(s->sp, 0, sizeof(StageParams))) != cudaSuccess) what = "clear stage params";
+  else if ((e = (s->prec == SM_FP64 ? prepare_element_f64(s->N) : prepare_element_f32(s->N))) != cudaSuccess) what = "element kernel attributes";
+  else if ((e = prepare_interface(s->N, s->prec)) != cudaSuccess) what = "interface kernel attributes";
+  else if ((e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking)) != cudaSuccess) what = "capture stream";
+  else if ((e = cudaDeviceSynchronize()) != cudaSuccess) what = "init sync";
+  if (what) {
+    free_solver(s);
+    return fail(SM_ERR_CUDA, what, e);
+  }
+  *out = s;
+  return SM_OK;
+}
+
+int sm_set_motion(sm_solver* s, const sm_motion* mo) {
+  if (!s || !mo) return fail(SM_ERR_ARG, "NULL argument");
+  if (mo->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");
+  if (!std::isfinite(mo->v) || !std::isfinite(mo->delta0)) return fail(SM_ERR_ARG, "non-finite motion");
+  if (s->desc.interface_conforming && (mo->v != 0.0 || mo->delta0 != 0.0))
+    return fail(SM_ERR_ARG, "a conforming interface cannot move");
+  s->motion = *mo;
+  s->m.v = mo->v;
+  s->m.delta0 = mo->delta0;
+  clear_graphs(s);
+  return SM_OK;
+}
+
+long long sm_state_size(const sm_solver* s) { return s ? s->nstate : -1; }
+int sm_scalar_bytes(const sm_solver* s) { return s ? s->sb : -1; }
+void* sm_state_ptr(sm_solver* s) { return s ? s->U[s->cur] : nullptr; }
+
+int sm_init_state(sm_solver* s, void* stream) {
+  if (!s) return fail(SM_ERR_ARG, "NULL solver");
+  cudaStream_t st = (cudaStream_t)stream;
+  SM_CK(launch_init_state(s->N, s->prec, s->m, s->U[s->cur], st), "init state");
+  SM_CK(cudaMemsetAsync(s->G, 0, (size_t)s->nstate * s->sb, st), "clear G");
+  s->t_host = 0.0;
+  SM_CK(cudaMemsetAsync(s->t_d, 0, sizeof(double), st), "clear t");
+  return SM_OK;
+}
+
+int sm_set_state(sm_solver* s, const void* U, int on_device, double t, void* stream) {
+  if (!s || !U) return fail(SM_ERR_ARG, "NULL argument");
+  if (!std::isfinite(t)) return fail(SM_ERR_ARG, "non-finite time");
+  cudaStream_t st = (cudaStream_t)stream;
+  SM_CK(cudaMemcpyAsync(s->U[s->cur], U, (size_t)s->nstate * s->sb,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "copy state in");
+  s->t_host = t;
+  SM_CK(cudaMemcpyAsync(s->t_d, &s->t_host, sizeof(double), cudaMemcpyHostToDevice, st), "copy time in");
+  SM_CK(cudaMemsetAsync(s->G, 0, (size_t)s->nstate * s->sb, st), "clear G");
+  return SM_OK;
+}
+
+int sm_get_state(sm_solver* s, void* U, int on_device, double* t, void* stream) {
+  if (!s) return fail(SM_ERR_ARG, "NULL solver");
+  cudaStream_t st = (cudaStream_t)stream;
+  double tt = 0.0;
+  if (U)
+    SM_CK(cudaMemcpyAsync(U, s->U[s->cur], (size_t)s->nstate * s->sb,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st), "copy state out");
+  SM_CK(cudaMemcpyAsync(&tt, s->t_d, sizeof(double), cudaMemcpyDeviceToHost, st), "copy time out");
+  SM_CK(cudaStreamSynchronize(st), "sync");
+  s->t_host = tt;
+  if (t) *t = tt;
+  return SM_OK;
+}
+
+int sm_rhs(sm_solver* s, double t, const void* dU, void* dUt, void* stream) {
+  if (!s || !dU || !dUt) return fail(SM_ERR_ARG, "NULL argument");
+  if (dU == dUt) return fail(SM_ERR_ARG, "dU and dUt must not overlap");
+  if (!std::isfinite(t)) return fail(SM_ERR_ARG, "non-finite time");
+  cudaStream_t st = (cudaStream_t)stream;
+  SM_CK(enqueue_rhs_parts(s, t, dU, s->Fs, s->Fm, st), "stage params / interface");
+  ElemArgs a{s->m, s->sp, dU, dUt, nullptr, s->Fs, s->Fm, 0.0, 0.0, 0.0};
+  SM_CK(launch_elem(s, ELEM_RHS, a, st), "element kernel");
+  return SM_OK;
+}
+
+int sm_interface(sm_solver* s, double t, const void* dU, void* dFs, void* dFm, void* stream) {
+  if (!s || !dU || !dFs || !dFm) return fail(SM_ERR_ARG, "NULL argument");
+  if (s->desc.interface_conforming) return fail(SM_ERR_ARG, "the interface is conforming");
+  if (!std::isfinite(t)) return fail(SM_ERR_ARG, "non-finite time");
+  SM_CK(enqueue_rhs_parts(s, t, dU, dFs, dFm, (cudaStream_t)stream), "interface");
+  return SM_OK;
+}
+
+int sm_step(sm_solver* s, double dt, int nsteps, void* stream) {
+  if (!s) return fail(SM_ERR_ARG, "NULL solver");
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(SM_ERR_ARG, "dt must be positive, nsteps >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int n = 0; n < nsteps; ++n) {
+    cudaGraphExec_t exec;
+    int rc = get_graph(s, dt, s->cur, &exec);
+    if (rc != SM_OK) return rc;
+    SM_CK(cudaGraphLaunch(exec, st), "graph launch");
+    s->cur ^= 1;
+    s->t_host += dt;
+  }
+  return SM_OK;
+}
+
+int sm_step_profiled(sm_solver* s, double dt, int nsteps, void* stream, double* ms_out, int* launches_out) {
+  if (!s) return fail(SM_ERR_ARG, "NULL solver");
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(SM_ERR_ARG, "dt must be positive, nsteps >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ev[6];
+  for (int k = 0; k < 6; ++k) SM_CK(cudaEventCreate(&ev[k]), "event create");
+  double ms[3] = {0, 0, 0};
+  int cnt[3] = {0, 0, 0};
+  int rc = SM_OK;
+  for (int n = 0; n < nsteps && rc == SM_OK; ++n) {
+    for (int k = 0; k < 5; ++k) {
+      cudaError_t e = cudaEventRecord(ev[0], st);
+      if (e == cudaSuccess) e = launch_stage_params(s->m, s->np, s->sp, s->t_d, 0.0, RK_C[k], dt, k == 4 ? 2 : 1, st);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+      if (e == cudaSuccess && !s->desc.interface_conforming)
+        e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, s->U[s->cur], s->Fs, s->Fm, st);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+      ElemArgs a{s->m, s->sp, s->U[s->cur], s->U[1 - s->cur], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
+      if (e == cudaSuccess) e = launch_elem(s, k == 0 ? ELEM_STAGE_FIRST : ELEM_STAGE, a, st);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+      float a0 = 0, a1 = 0, a2 = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&a0, ev[0], ev[1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&a1, ev[1], ev[2]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&a2, ev[2], ev[3]);
+      if (e != cudaSuccess) { rc = fail(SM_ERR_CUDA, "profiled step", e); break; }
+      ms[0] += a0; ms[1] += a1; ms[2] += a2;
+      cnt[0] += 1; cnt[1] += s->desc.interface_conforming ? 0 : 1; cnt[2] += 1;
+      s->cur ^= 1;
+    }
+    if (rc == SM_OK) s->t_host += dt;
+  }
+  for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
+  if (ms_out) for (int k = 0; k < 3; ++k) ms_out[k] = ms[k];
+  if (launches_out) for (int k = 0; k < 3; ++k) launches_out[k] = cnt[k];
+  return rc;
+}
+
+int sm_diag(sm_solver* s, sm_diag_out* out, void* stream) {
+  if (!s || !out) return fail(SM_ERR_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* part = s->red_d;
+  double* res = s->red_d + s->red_blocks * 5;
+  SM_CK(launch_totals(s->N, s->prec, s->m, s->U[s->cur], part, s->red_blocks, res, st), "totals");
+  SM_CK(launch_face_sums(s->N, s->prec, s->m, s->Fs, part, s->red_blocks, res + 5, st), "face sums static");
+  SM_CK(launch_face_sums(s->N, s->prec, s->m, s->Fm, part, s->red_blocks, res + 10, st), "face sums moving");
+  double h[15];
+  long long n = 0;
+  double sfrac = 0.0, tt = 0.0;
+  SM_CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st), "diag copy");
+  SM_CK(cudaMemcpyAsync(&n, &s->sp->n, sizeof(n), cudaMemcpyDeviceToHost, st), "diag copy n");
+  SM_CK(cudaMemcpyAsync(&sfrac, &s->sp->s, sizeof(sfrac), cudaMemcpyDeviceToHost, st), "diag copy s");
+  SM_CK(cudaMemcpyAsync(&tt, s->t_d, sizeof(tt), cudaMemcpyDeviceToHost, st), "diag copy t");
+  SM_CK(cudaStreamSynchronize(st), "diag sync");
+  out->n_delta = n;
+  out->s_delta = sfrac;
+  out->t = tt;
+  int finite = 1;
+  for (int v = 0; v < 5; ++v) {
+    out->totals[v] = h[v];
+    out->iface_sum_static[v] = h[5 + v];
+    out->iface_sum_moving[v] = h[10 + v];
+    if (!std::isfinite(h[v])) finite = 0;
+  }
+  return finite ? SM_OK : fail(SM_ERR_NONFINITE, "state totals are not finite");
+}
+
+void sm_destroy(sm_solver* s) { free_solver(s); }
+
+int sm_map(const double* d_delta, int count, double l, int n_par, long long* d_n, double* d_s, int* d_pairs,
+           void* stream) {
+  if (count < 0 || n_par < 1 || !(l > 0.0) || (count > 0 && (!d_delta || !d_n || !d_s)))
+    return fail(SM_ERR_ARG, "invalid sm_map arguments");
+  SM_CK(launch_map_batch(d_delta, count, l, n_par, d_n, d_s, d_pairs, (cudaStream_t)stream), "map kernel");
+  return SM_OK;
+}
+
+int sm_mortar_matrices(int N, double sigma, double* d_out, void* stream) {
+  static std::mutex mu;
+  static BasisDev* cache[8] = {nullptr};
+  if (N < 1 || N > 7 || !d_out || !(sigma >= -1.0 && sigma <= 1.0)) return fail(SM_ERR_ARG, "invalid sm_mortar_matrices arguments");
+  BasisDev* b;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cache[N]) {
+      BasisDev h;
+      lgl_basis(N, h);
+      SM_CK(cudaMalloc((void**)&cache[N], sizeof(BasisDev)), "basis alloc");
+      SM_CK(cudaMemcpy(cache[N], &h, sizeof(BasisDev), cudaMemcpyHostToDevice), "basis upload");
+    }
+    b = cache[N];
+  }
+  SM_CK(launch_mortar_ops(b, N + 1, sigma, d_out, (cudaStream_t)stream), "mortar kernel");
+  return SM_OK;
+}
+
+}  // extern "C"

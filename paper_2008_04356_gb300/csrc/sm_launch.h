@@ -1,0 +1,43 @@
+// Launch entry points of the kernels, shared by the translation units of the library.
+#pragma once
+
+#include "sm_common.cuh"
+
+// Per-stage mapper + mortar operators (sm_mapper.cu).
+cudaError_t launch_stage_params(const MeshDev& m, int np, StageParams* sp, double* t_dev, double t_arg,
+                                double ck, double dt, int mode, cudaStream_t st);
+cudaError_t launch_map_batch(const double* d_delta, int count, double l, int n_par, long long* d_n,
+                             double* d_s, int* d_pairs, cudaStream_t st);
+cudaError_t launch_mortar_ops(const BasisDev* b, int np, double sigma, double* d_out, cudaStream_t st);
+
+// Element kernel modes.
+enum { ELEM_RHS = 0, ELEM_STAGE = 1, ELEM_STAGE_FIRST = 2 };
+
+struct ElemArgs {
+  MeshDev m;
+  const StageParams* sp;
+  const void* U;     // state read (neighbour traces come from here too)
+  void* out;         // ELEM_RHS: dU/dt;  ELEM_STAGE*: updated state
+  void* G;           // RK register (stage modes)
+  const void* Fs;    // interface face fluxes, static side
+  const void* Fm;    // interface face fluxes, moving side
+  double rkA, rkB, dt;
+};
+
+// sm_elem_f32.cu / sm_elem_f64.cu
+cudaError_t launch_element_f32(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t launch_element_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t prepare_element_f32(int N);
+cudaError_t prepare_element_f64(int N);
+
+// sm_iface.cu
+cudaError_t launch_interface(int N, int prec, int riemann, const MeshDev& m, const StageParams* sp, const void* U,
+                             void* Fs, void* Fm, cudaStream_t st);
+cudaError_t prepare_interface(int N, int prec);
+
+// sm_aux.cu: initial data, reductions
+cudaError_t launch_init_state(int N, int prec, const MeshDev& m, void* U, cudaStream_t st);
+cudaError_t launch_totals(int N, int prec, const MeshDev& m, const void* U, double* partial, int nblk,
+                          double* out5, cudaStream_t st);
+cudaError_t launch_face_sums(int N, int prec, const MeshDev& m, const void* F, double* partial, int nblk,
+                             double* out5, cudaStream_t st);

@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libslidemesh (include/slidemesh.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; PyTorch supplies device memory and
+the current CUDA stream.  Importing this module does not load the library; the first call
+does, and raises if libslidemesh.so is missing (build it with build.build_library()).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libslidemesh.so")
+
+SM_OK, SM_PENDING = 0, 1
+SM_FP64, SM_FP32 = 0, 1
+
+
+class SmMeshDesc(C.Structure):
+    _fields_ = [("N", C.c_int), ("geom", C.c_int), ("nel_static", C.c_int * 3), ("nel_moving", C.c_int * 3),
+                ("x0", C.c_double), ("x1", C.c_double), ("x2", C.c_double), ("y0", C.c_double),
+                ("y1", C.c_double), ("z0", C.c_double), ("z1", C.c_double), ("gamma", C.c_double),
+                ("riemann", C.c_int), ("precision", C.c_int), ("interface_conforming", C.c_int),
+                ("flow", C.c_int), ("fpar", C.c_double * 16), ("modes", C.c_double * 160)]
+
+
+class SmMotion(C.Structure):
+    _fields_ = [("v", C.c_double), ("omega", C.c_double), ("delta0", C.c_double)]
+
+
+class SmDiag(C.Structure):
+    _fields_ = [("n_delta", C.c_longlong), ("s_delta", C.c_double), ("t", C.c_double),
+                ("totals", C.c_double * 5), ("iface_sum_static", C.c_double * 5),
+                ("iface_sum_moving", C.c_double * 5)]
+
+
+_vp = C.c_void_p
+_SIGS = {
+    "sm_init_mesh": (C.c_int, [C.POINTER(SmMeshDesc), C.POINTER(_vp)]),
+    "sm_set_motion": (C.c_int, [_vp, C.POINTER(SmMotion)]),
+    "sm_state_size": (C.c_longlong, [_vp]),
+    "sm_scalar_bytes": (C.c_int, [_vp]),
+    "sm_init_state": (C.c_int, [_vp, _vp]),
+    "sm_set_state": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp]),
+    "sm_get_state": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_double), _vp]),
+    "sm_rhs": (C.c_int, [_vp, C.c_double, _vp, _vp, _vp]),
+    "sm_interface": (C.c_int, [_vp, C.c_double, _vp, _vp, _vp, _vp]),
+    "sm_step": (C.c_int, [_vp, C.c_double, C.c_int, _vp]),
+    "sm_step_profiled": (C.c_int, [_vp, C.c_double, C.c_int, _vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "sm_diag": (C.c_int, [_vp, C.POINTER(SmDiag), _vp]),
+    "sm_state_ptr": (_vp, [_vp]),
+    "sm_destroy": (None, [_vp]),
+    "sm_map": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, _vp, _vp, _vp, _vp]),
+    "sm_mortar_matrices": (C.c_int, [C.c_int, C.c_double, _vp, _vp]),
+    "sm_status_string": (C.c_char_p, [C.c_int]),
+    "sm_last_error": (C.c_char_p, []),
+}
+
+_LIB = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libslidemesh.so is missing at %s: run paper_2008_04356_gb300.build.build_library()"
+                               % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class SlidemeshError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        L = lib()
+        msg = "%s failed: %s (%s)" % (where, L.sm_status_string(status).decode(), L.sm_last_error().decode())
+        super().__init__(msg)
+
+
+def check(status, where):
+    if status != SM_OK:
+        raise SlidemeshError(status, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def mesh_desc(p: synth.Problem) -> SmMeshDesc:
+    d = SmMeshDesc()
+    d.N, d.geom = p.N, 0
+    for k in range(3):
+        d.nel_static[k], d.nel_moving[k] = int(p.nel_s[k]), int(p.nel_m[k])
+    for name in ("x0", "x1", "x2", "y0", "y1", "z0", "z1", "gamma"):
+        setattr(d, name, float(getattr(p, name)))
+    d.riemann, d.precision = int(p.riemann), int(p.precision)
+    d.interface_conforming, d.flow = int(p.interface_conforming), int(p.flow)
+    for k, f in enumerate(p.fpar16()):
+        d.fpar[k] = f
+    for k, m in enumerate(p.modes_array().ravel()):
+        d.modes[k] = m
+    return d
+
+
+def sm_map(d_delta, l: float, n_par: int, with_pairs: bool = True, stream=None):
+    """Device interface configuration for a batch of displacements (torch float64 cuda)."""
+    import torch
+    count = d_delta.numel()
+    n = torch.empty(count, dtype=torch.int64, device=d_delta.device)
+    s = torch.empty(count, dtype=torch.float64, device=d_delta.device)
+    pairs = torch.empty((count, n_par, 2), dtype=torch.int32, device=d_delta.device) if with_pairs else None
+    check(lib().sm_map(d_delta.data_ptr(), count, float(l), int(n_par), n.data_ptr(), s.data_ptr(),
+                       pairs.data_ptr() if pairs is not None else None, _stream(stream)), "sm_map")
+    return n, s, pairs
+
+
+def sm_mortar_matrices(N: int, sigma: float, device="cuda", stream=None):
+    import torch
+    out = torch.empty((4, N + 1, N + 1), dtype=torch.float64, device=device)
+    check(lib().sm_mortar_matrices(int(N), float(sigma), out.data_ptr(), _stream(stream)), "sm_mortar_matrices")
+    return out  # P_lo, P_hi, B_lo, B_hi
+
+
+class Solver:
+    """One sliding-mesh solve on the current CUDA device (library-owned state)."""
+
+    def __init__(self, problem: synth.Problem):
+        self.problem = problem
+        self._desc = mesh_desc(problem)
+        h = C.c_void_p()
+        check(lib().sm_init_mesh(C.byref(self._desc), C.byref(h)), "sm_init_mesh")
+        self.h = h
+        self.set_motion(problem.v, problem.delta0)
+        self.N = problem.N
+        self.nn = (problem.N + 1) ** 3
+        self.E = problem.nelem
+        self.size = int(lib().sm_state_size(self.h))
+        self.dtype_np = np.float64 if problem.precision == SM_FP64 else np.float32
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.problem.precision == SM_FP64 else torch.float32
+
+    def shape(self):
+        return (self.E, 5, self.nn)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_motion(self, v: float, delta0: float = 0.0):
+        mo = SmMotion(float(v), 0.0, float(delta0))
+        check(lib().sm_set_motion(self.h, C.byref(mo)), "sm_set_motion")
+
+    def init_state(self, stream=None):
+        check(lib().sm_init_state(self.h, _stream(stream)), "sm_init_state")
+
+    def set_state(self, U, t: float = 0.0, stream=None):
+        """U: torch tensor (cuda or pinned/pageable cpu) or numpy array in solver precision."""
+        import torch
+        if isinstance(U, np.ndarray):
+            U = torch.from_numpy(np.ascontiguousarray(U, dtype=self.dtype_np))
+        assert U.dtype == self.torch_dtype and U.is_contiguous() and U.numel() == self.size
+        check(lib().sm_set_state(self.h, U.data_ptr(), int(U.is_cuda), float(t), _stream(stream)), "sm_set_state")
+        return U
+
+    def get_state(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape(), dtype=self.torch_dtype, device="cuda")
+        t = C.c_double()
+        check(lib().sm_get_state(self.h, out.data_ptr(), int(out.is_cuda), C.byref(t), _stream(stream)),
+              "sm_get_state")
+        return out, t.value
+
+    def rhs(self, dU, t: float, out=None, stream=None):
+        import torch
+        assert dU.is_cuda and dU.dtype == self.torch_dtype and dU.is_contiguous() and dU.numel() == self.size
+        if out is None:
+            out = torch.empty_like(dU)
+        check(lib().sm_rhs(self.h, float(t), dU.data_ptr(), out.data_ptr(), _stream(stream)), "sm_rhs")
+        return out
+
+    def interface(self, dU, t: float, stream=None):
+        import torch
+        p = self.problem
+        shp = (p.nel_s[2], p.nel_s[1], 5, p.N + 1, p.N + 1)
+        Fs = torch.empty(shp, dtype=self.torch_dtype, device=dU.device)
+        Fm = torch.empty(shp, dtype=self.torch_dtype, device=dU.device)
+        check(lib().sm_interface(self.h, float(t), dU.data_ptr(), Fs.data_ptr(), Fm.data_ptr(), _stream(stream)),
+              "sm_interface")
+        return Fs, Fm
+
+    def step(self, dt: float, nsteps: int, stream=None):
+        check(lib().sm_step(self.h, float(dt), int(nsteps), _stream(stream)), "sm_step")
+
+    def step_profiled(self, dt: float, nsteps: int, stream=None):
+        """Per-kernel device times (ms) and launch counts of nsteps steps: mapper, interface, element."""
+        ms = (C.c_double * 3)()
+        cnt = (C.c_int * 3)()
+        check(lib().sm_step_profiled(self.h, float(dt), int(nsteps), _stream(stream), ms, cnt), "sm_step_profiled")
+        return list(ms), list(cnt)
+
+    def diag(self, stream=None) -> dict:
+        d = SmDiag()
+        st = lib().sm_diag(self.h, C.byref(d), _stream(stream))
+        out = {"n_delta": d.n_delta, "s_delta": d.s_delta, "t": d.t, "totals": list(d.totals),
+               "iface_sum_static": list(d.iface_sum_static), "iface_sum_moving": list(d.iface_sum_moving),
+               "status": st}
+        if st not in (SM_OK, -4):
+            check(st, "sm_diag")
+        return out
