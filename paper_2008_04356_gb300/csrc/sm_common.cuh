@@ -37,6 +37,21 @@ struct StageParams {
   float mat_f[8][SM_MAXNP * SM_MAXNP];
 };
 
+// Per-precision constants of the discrete operator, precomputed on the host so that the
+// kernels do no FP64 arithmetic in FP32 mode.
+enum {
+  MC_METRIC = 0,      // [blk*3 + d]: |Ja^d|, surface element of the xi^{d+1} faces
+  MC_MINVJ = 6,       // [blk]: -1 / J
+  MC_VG = 8,          // grid velocity of the moving block (along y)
+  MC_GAMMA = 9,
+  MC_IW0 = 10,        // 1 / w_0 (LGL end-point weight)
+  MC_SJ_IF = 11,      // surface element of the interface faces
+  MC_BC = 12,         // [5]: constant boundary state (flows 0 and 2)
+  MC_H = 17,          // [4]: hx (static), hx (moving), hy, hz
+  MC_X = 21,          // [4]: x0, x1, y0, z0
+  MC_COUNT = 25
+};
+
 // Mesh and physics description passed to kernels by value.
 struct MeshDev {
   int nxs, nxm, ny, nz;
@@ -50,21 +65,39 @@ struct MeshDev {
   double fpar[16];
   const double* modes;        // [5][8][4] device
   const BasisDev* basis;      // device
+  float cf[MC_COUNT];
+  double cd[MC_COUNT];
+  float fparf[16];
 };
 
 template <typename T> struct Prec;
 template <> struct Prec<double> {
   static __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+  static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+  static __device__ __forceinline__ const double* c(const MeshDev& m);
+  static __device__ __forceinline__ double fpar(const MeshDev& m, int k);
   static __device__ __forceinline__ const double* dhat(const BasisDev* b) { return b->Dhat; }
   static __device__ __forceinline__ const double* w(const BasisDev* b) { return b->w; }
+  static __device__ __forceinline__ const double* x(const BasisDev* b) { return b->x; }
   static __device__ __forceinline__ const double* mat(const StageParams* p, int k) { return p->mat[k]; }
 };
+// FP32 mode uses the hardware reciprocal and reciprocal square root (about 1-2 ulp), well
+// inside the 1e-5 relative tolerance of the FP32 path; FP64 mode keeps IEEE division/sqrt.
 template <> struct Prec<float> {
-  static __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
+  static __device__ __forceinline__ float sqrt_(float a) { return a * rsqrtf(a); }
+  static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
+  static __device__ __forceinline__ const float* c(const MeshDev& m);
+  static __device__ __forceinline__ float fpar(const MeshDev& m, int k);
   static __device__ __forceinline__ const float* dhat(const BasisDev* b) { return b->Dhat_f; }
   static __device__ __forceinline__ const float* w(const BasisDev* b) { return b->w_f; }
+  static __device__ __forceinline__ const float* x(const BasisDev* b) { return b->x_f; }
   static __device__ __forceinline__ const float* mat(const StageParams* p, int k) { return p->mat_f[k]; }
 };
+
+__device__ __forceinline__ const double* Prec<double>::c(const MeshDev& m) { return m.cd; }
+__device__ __forceinline__ const float* Prec<float>::c(const MeshDev& m) { return m.cf; }
+__device__ __forceinline__ double Prec<double>::fpar(const MeshDev& m, int k) { return m.fpar[k]; }
+__device__ __forceinline__ float Prec<float>::fpar(const MeshDev& m, int k) { return m.fparf[k]; }
 
 // ---------------------------------------------------------------------------------------
 // Element / face geometry.  Element e: static block first (e < Es), local index
@@ -135,83 +168,129 @@ __device__ __forceinline__ double elem_jacobian(const MeshDev& m, int blk) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Physics (Sec. 2).  U = (rho, rho v, rho e); perfect gas.
+// Physics (Sec. 2).  U = (rho, rho v, rho e); perfect gas p = (gamma-1)(rho e - m.v/2).
 // ---------------------------------------------------------------------------------------
+template <typename T> struct Prim { T ir, u[3], p; };   // 1/rho, velocity, pressure
+
 template <typename T>
-__device__ __forceinline__ T pressure(const T U[5], T gamma) {
-  T ir = T(1) / U[0];
-  return (gamma - T(1)) * (U[4] - T(0.5) * ir * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]));
+__device__ __forceinline__ Prim<T> primitives(const T U[5], T gamma) {
+  Prim<T> q;
+  q.ir = Prec<T>::rcp(U[0]);
+  q.u[0] = U[1] * q.ir;
+  q.u[1] = U[2] * q.ir;
+  q.u[2] = U[3] * q.ir;
+  q.p = (gamma - T(1)) * (U[4] - T(0.5) * (U[1] * q.u[0] + U[2] * q.u[1] + U[3] * q.u[2]));
+  return q;
 }
+
+template <typename T>
+__device__ __forceinline__ T pressure(const T U[5], T gamma) { return primitives(U, gamma).p; }
 
 // Flux along physical axis AX (0 = x, 1 = y, 2 = z) minus grid transport vg * U.
 template <typename T, int AX>
-__device__ __forceinline__ void axis_flux(const T U[5], T p, T vg, T F[5]) {
-  T ua = U[1 + AX] / U[0];
-  T un = ua - vg;
+__device__ __forceinline__ void axis_flux(const T U[5], const Prim<T>& q, T vg, T F[5]) {
+  const T ua = q.u[AX];
+  const T un = ua - vg;
   F[0] = U[0] * un;
-  F[1] = U[1] * un + (AX == 0 ? p : T(0));
-  F[2] = U[2] * un + (AX == 1 ? p : T(0));
-  F[3] = U[3] * un + (AX == 2 ? p : T(0));
-  F[4] = U[4] * un + p * ua;
+  F[1] = U[1] * un + (AX == 0 ? q.p : T(0));
+  F[2] = U[2] * un + (AX == 1 ? q.p : T(0));
+  F[3] = U[3] * un + (AX == 2 ? q.p : T(0));
+  F[4] = U[4] * un + q.p * ua;
 }
 
 // Riemann flux across a face with unit normal along +AX, grid normal velocity vgn.
 // RIEM 0: Rusanov (local Lax-Friedrichs); RIEM 1: Roe with the Harten-Hyman entropy fix.
 template <typename T, int AX, int RIEM>
 __device__ __forceinline__ void riemann_axis(const T UL[5], const T UR[5], T vgn, T gamma, T F[5]) {
-  T pL = pressure(UL, gamma), pR = pressure(UR, gamma);
+  const Prim<T> qL = primitives(UL, gamma), qR = primitives(UR, gamma);
   T FL[5], FR[5];
-  axis_flux<T, AX>(UL, pL, vgn, FL);
-  axis_flux<T, AX>(UR, pR, vgn, FR);
-  T irL = T(1) / UL[0], irR = T(1) / UR[0];
-  T unL = UL[1 + AX] * irL, unR = UR[1 + AX] * irR;
-  T cL = Prec<T>::sqrt_(gamma * pL * irL), cR = Prec<T>::sqrt_(gamma * pR * irR);
+  axis_flux<T, AX>(UL, qL, vgn, FL);
+  axis_flux<T, AX>(UR, qR, vgn, FR);
+  const T unL = qL.u[AX], unR = qR.u[AX];
+  const T cL = Prec<T>::sqrt_(gamma * qL.p * qL.ir), cR = Prec<T>::sqrt_(gamma * qR.p * qR.ir);
   if (RIEM == 0) {
-    T a = fmax(fabs(unL - vgn) + cL, fabs(unR - vgn) + cR);
+    const T a = fmax(fabs(unL - vgn) + cL, fabs(unR - vgn) + cR);
 #pragma unroll
     for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * a * (UR[k] - UL[k]);
     return;
   }
   // Roe-averaged state
-  T sL = Prec<T>::sqrt_(UL[0]), sR = Prec<T>::sqrt_(UR[0]);
-  T iss = T(1) / (sL + sR);
-  T uL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
-  T uR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
+  const T sL = Prec<T>::sqrt_(UL[0]), sR = Prec<T>::sqrt_(UR[0]);
+  const T iss = Prec<T>::rcp(sL + sR);
   T uh[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) uh[d] = (sL * uL[d] + sR * uR[d]) * iss;
-  T HL = (UL[4] + pL) * irL, HR = (UR[4] + pR) * irR;
-  T Hh = (sL * HL + sR * HR) * iss;
-  T q2 = uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2];
-  T ch = Prec<T>::sqrt_((gamma - T(1)) * (Hh - T(0.5) * q2));
-  T rh = sL * sR;
-  T unh = uh[AX];
-  T dp = pR - pL, dr = UR[0] - UL[0], dun = unR - unL;
-  T ic2 = T(1) / (ch * ch);
-  T a1 = T(0.5) * (dp - rh * ch * dun) * ic2;   // left acoustic wave
-  T a5 = T(0.5) * (dp + rh * ch * dun) * ic2;   // right acoustic wave
-  T a2 = dr - dp * ic2;                          // entropy wave
-  T l1 = unh - ch - vgn, l2 = unh - vgn, l5 = unh + ch - vgn;
-  T al1 = fabs(l1), al2 = fabs(l2), al5 = fabs(l5);
+  for (int d = 0; d < 3; ++d) uh[d] = (sL * qL.u[d] + sR * qR.u[d]) * iss;
+  const T HL = (UL[4] + qL.p) * qL.ir, HR = (UR[4] + qR.p) * qR.ir;
+  const T Hh = (sL * HL + sR * HR) * iss;
+  const T q2 = uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2];
+  const T ch = Prec<T>::sqrt_((gamma - T(1)) * (Hh - T(0.5) * q2));
+  const T rh = sL * sR;
+  const T unh = uh[AX];
+  const T dp = qR.p - qL.p, dr = UR[0] - UL[0], dun = unR - unL;
+  const T ic2 = Prec<T>::rcp(ch * ch);
+  const T a1 = T(0.5) * (dp - rh * ch * dun) * ic2;   // left acoustic wave
+  const T a5 = T(0.5) * (dp + rh * ch * dun) * ic2;   // right acoustic wave
+  const T a2 = dr - dp * ic2;                          // entropy wave
+  const T l1 = unh - ch - vgn, l2 = unh - vgn, l5 = unh + ch - vgn;
+  T al1 = fabs(l1), al5 = fabs(l5);
+  const T al2 = fabs(l2);
   // Harten-Hyman: widen |lambda| of an acoustic wave that opens across zero
-  T d1 = fmax(T(0), fmax(l1 - (unL - cL - vgn), (unR - cR - vgn) - l1));
+  const T d1 = fmax(T(0), fmax(l1 - (unL - cL - vgn), (unR - cR - vgn) - l1));
   if (al1 < d1) al1 = (l1 * l1 + d1 * d1) / (T(2) * d1);
-  T d5 = fmax(T(0), fmax(l5 - (unL + cL - vgn), (unR + cR - vgn) - l5));
+  const T d5 = fmax(T(0), fmax(l5 - (unL + cL - vgn), (unR + cR - vgn) - l5));
   if (al5 < d5) al5 = (l5 * l5 + d5 * d5) / (T(2) * d5);
-  T w1 = al1 * a1, w5 = al5 * a5, w2 = al2 * a2;
-  T du[3] = {uR[0] - uL[0], uR[1] - uL[1], uR[2] - uL[2]};
+  const T w1 = al1 * a1, w5 = al5 * a5, w2 = al2 * a2;
+  T du[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) du[d] = qR.u[d] - qL.u[d];
   T D[5];
   D[0] = w1 + w2 + w5;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    T shear = du[d] - (d == AX ? dun : T(0));
-    T nd = d == AX ? ch : T(0);
+    const T shear = du[d] - (d == AX ? dun : T(0));
+    const T nd = d == AX ? ch : T(0);
     D[1 + d] = w1 * (uh[d] - nd) + w2 * uh[d] + al2 * rh * shear + w5 * (uh[d] + nd);
   }
-  T udu = uh[0] * du[0] + uh[1] * du[1] + uh[2] * du[2];
+  const T udu = uh[0] * du[0] + uh[1] * du[1] + uh[2] * du[2];
   D[4] = w1 * (Hh - unh * ch) + w2 * T(0.5) * q2 + al2 * rh * (udu - unh * dun) + w5 * (Hh + unh * ch);
 #pragma unroll
   for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * D[k];
+}
+
+// Exterior state of a weak Dirichlet face at physical position X and time t, in the
+// kernel's precision: the constant background (flows 0 and 2, precomputed) or the exact
+// solution (flows 1 and 3).
+__device__ __forceinline__ float sin_t(float a) { return sinf(a); }
+__device__ __forceinline__ double sin_t(double a) { return sin(a); }
+
+template <typename T>
+__device__ __forceinline__ void boundary_state(const MeshDev& m, const T X[3], T t, T U[5]) {
+  const T* c = Prec<T>::c(m);
+  if (m.flow == 0 || m.flow == 2) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) U[k] = c[MC_BC + k];
+    return;
+  }
+  T P[5];
+  if (m.flow == 1) {
+    const T ph = Prec<T>::fpar(m, 2) * (X[0] - Prec<T>::fpar(m, 5) * t) +
+                 Prec<T>::fpar(m, 3) * (X[1] - Prec<T>::fpar(m, 6) * t) +
+                 Prec<T>::fpar(m, 4) * (X[2] - Prec<T>::fpar(m, 7) * t);
+    P[0] = Prec<T>::fpar(m, 0) + Prec<T>::fpar(m, 1) * sin_t(T(2.0 * SM_PI) * ph);
+    P[1] = Prec<T>::fpar(m, 5); P[2] = Prec<T>::fpar(m, 6); P[3] = Prec<T>::fpar(m, 7);
+    P[4] = Prec<T>::fpar(m, 8);
+  } else {
+    const T xs = X[0] - Prec<T>::fpar(m, 4) * t;
+    P[0] = Prec<T>::fpar(m, 0) + xs * (Prec<T>::fpar(m, 1) + xs * (Prec<T>::fpar(m, 2) + xs * Prec<T>::fpar(m, 3)));
+    P[1] = Prec<T>::fpar(m, 4); P[2] = Prec<T>::fpar(m, 5); P[3] = Prec<T>::fpar(m, 6);
+    P[4] = Prec<T>::fpar(m, 7);
+  }
+  const T g = c[MC_GAMMA];
+  U[0] = P[0];
+  U[1] = P[0] * P[1];
+  U[2] = P[0] * P[2];
+  U[3] = P[0] * P[3];
+  U[4] = P[4] / (g - T(1)) + T(0.5) * P[0] * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -8,7 +8,8 @@
 // face fluxes from the Riemann solver (conforming neighbours and weak Dirichlet faces,
 // computed here in canonical orientation so both neighbours obtain identical values) or
 // from the interface kernel (sliding faces).  One CTA holds EPB whole elements, one
-// thread per volume node; neighbour face traces are read from the same state array.
+// thread per volume node; neighbour face traces are read from the same state array (L2
+// serves them: the DRAM traffic stays at the state's own reads and writes).
 #pragma once
 
 #include "sm_launch.h"
@@ -21,6 +22,10 @@ template <int N> struct ElemCfg {
     return sizeof(T) * (size_t)(EPB * 5 * NN + EPB * 15 * NN + EPB * 30 * NP2 + NP2 + 8);
   }
 };
+
+// Neighbour codes of the per-CTA face table: >= 0 element index, -1 weak Dirichlet face,
+// -2 sliding interface face.
+enum { NB_BOUNDARY = -1, NB_INTERFACE = -2 };
 
 template <int N, typename T, int RIEM, int MODE>
 __global__ void __launch_bounds__(ElemCfg<N>::THREADS)
@@ -35,44 +40,56 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
   T* sS = sF + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
   T* sD = sS + EPB * 30 * NP2;                   // [NP][NP] Dhat
   __shared__ int4 s_pos[EPB];
-  __shared__ double s_t, s_delta;
+  __shared__ int s_nb[EPB][6];
+  __shared__ T s_t, s_delta;
 
+  const T* c = Prec<T>::c(m);
   const int tid = threadIdx.x;
   const int le = tid / NN, nd = tid - le * NN;
   const long long e0 = (long long)blockIdx.x * EPB;
   const long long e = e0 + le;
   const bool active = e < m.E;
+  const long long base = e * 5 * NN + nd;
 
+  // ---- prologue: element positions, face-neighbour table, Dhat, state, early G fetch ----
   if (tid < NP2) sD[tid] = Prec<T>::dhat(m.basis)[(tid / NP) * SM_MAXNP + (tid % NP)];
-  if (tid < EPB && e0 + tid < m.E) {
-    ElemPos p = decode_elem(m, e0 + tid);
-    s_pos[tid] = make_int4(p.blk, p.ix, p.iy, p.iz);
-  }
-  if (tid == 0) { s_t = sp->t; s_delta = sp->delta; }
-
-  T u[5];
-  if (active) {
-    const T* Ue = U + e * 5 * NN + nd;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      u[v] = Ue[v * NN];
-      sU[(le * 5 + v) * NN + nd] = u[v];
+  if (tid < 6 * EPB) {
+    const int l2 = tid / 6, fc = tid - l2 * 6;
+    if (e0 + l2 < m.E) {
+      const ElemPos p = decode_elem(m, e0 + l2);
+      if (fc == 0) s_pos[l2] = make_int4(p.blk, p.ix, p.iy, p.iz);
+      long long nb = 0;
+      const int kind = face_neighbor(m, p, fc >> 1, fc & 1, &nb);
+      s_nb[l2][fc] = kind == 0 ? (int)nb : (kind == 1 ? NB_BOUNDARY : NB_INTERFACE);
     }
   }
+  if (tid == THREADS - 1) { s_t = (T)sp->t; s_delta = (T)sp->delta; }
+  T u[5], g[5];
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = U[base + v * NN];
+    if (MODE == ELEM_STAGE) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) g[v] = G[base + v * NN];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sU[(le * 5 + v) * NN + nd] = u[v];
+  }
   __syncthreads();
+  const T gamma = c[MC_GAMMA];
   if (active) {
     const int blk = s_pos[le].x;
-    const T p = pressure(u, (T)m.gamma);
-    const T a0 = (T)face_metric(m, blk, 0), a1 = (T)face_metric(m, blk, 1), a2 = (T)face_metric(m, blk, 2);
+    const Prim<T> q = primitives(u, gamma);
     T f[5];
     T* Fe = sF + le * 15 * NN + nd;
-    axis_flux<T, 1>(u, p, blk ? (T)m.v : T(0), f);          // xi^1 -> y (grid velocity)
+    const T a0 = c[MC_METRIC + 3 * blk], a1 = c[MC_METRIC + 3 * blk + 1], a2 = c[MC_METRIC + 3 * blk + 2];
+    axis_flux<T, 1>(u, q, blk ? c[MC_VG] : T(0), f);          // xi^1 -> y (grid velocity)
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fe[v * NN] = a0 * f[v];
-    axis_flux<T, 2>(u, p, T(0), f);                          // xi^2 -> z
+    axis_flux<T, 2>(u, q, T(0), f);                             // xi^2 -> z
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN] = a1 * f[v];
-    axis_flux<T, 0>(u, p, T(0), f);                          // xi^3 -> x
+    axis_flux<T, 0>(u, q, T(0), f);                             // xi^3 -> x
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN] = a2 * f[v];
   }
@@ -83,41 +100,42 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
     const int r = w - l2 * 6 * NP2;
     const int fc = r / NP2, ab = r - fc * NP2;
     if (e0 + l2 >= m.E) continue;
-    const int4 q4 = s_pos[l2];
-    ElemPos ps{q4.x, q4.y, q4.z, q4.w};
     const int d = fc >> 1, side = fc & 1;
     const int a = ab % NP, b = ab / NP;
     const int vn = face_vol_node<NP>(d, side, a, b);
+    const int nb = s_nb[l2][fc];
+    const int4 q4 = s_pos[l2];
     T Fo[5];
-    long long nb = 0;
-    const int kind = face_neighbor(m, ps, d, side, &nb);
-    if (kind == 2) {
-      const T* src = (ps.blk ? Fm : Fs) + ((long long)ps.iz * m.ny + ps.iy) * 5 * NP2 + ab;
+    if (nb == NB_INTERFACE) {
+      const T* src = (q4.x ? Fm : Fs) + ((long long)q4.w * m.ny + q4.z) * 5 * NP2 + ab;
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fo[v] = src[v * NP2];
     } else {
       T uin[5], uout[5], fs[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) uin[v] = sU[(l2 * 5 + v) * NN + vn];
-      if (kind == 0) {
-        const T* Un = U + nb * 5 * NN + face_vol_node<NP>(d, 1 - side, a, b);
+      if (nb >= 0) {
+        const T* Un = U + (long long)nb * 5 * NN + face_vol_node<NP>(d, 1 - side, a, b);
 #pragma unroll
         for (int v = 0; v < 5; ++v) uout[v] = Un[v * NN];
       } else {
+        // weak Dirichlet face (x = x0 or x = x2): node position at the stage time
+        const T* xi = Prec<T>::x(m.basis);
         const int i = vn % NP, j = (vn / NP) % NP, k = vn / NP2;
-        double X[3], ub[5];
-        node_position(m, ps, i, j, k, s_delta, X);
-        flow_state(m, X[0], X[1], X[2], s_t, 1, ub);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) uout[v] = (T)ub[v];
+        const T hx = c[MC_H + q4.x];
+        T X[3];
+        X[0] = c[MC_X + q4.x] + (T)q4.y * hx + (xi[k] + T(1)) * T(0.5) * hx;
+        X[1] = c[MC_X + 2] + (T)q4.z * c[MC_H + 2] + (xi[i] + T(1)) * T(0.5) * c[MC_H + 2] + (q4.x ? s_delta : T(0));
+        X[2] = c[MC_X + 3] + (T)q4.w * c[MC_H + 3] + (xi[j] + T(1)) * T(0.5) * c[MC_H + 3];
+        boundary_state<T>(m, X, s_t, uout);
       }
-      const T vgn = (d == 0 && ps.blk) ? (T)m.v : T(0);
+      const T vgn = (d == 0 && q4.x) ? c[MC_VG] : T(0);
       const T* L = side ? uin : uout;
       const T* R = side ? uout : uin;
-      if (d == 0) riemann_axis<T, 1, RIEM>(L, R, vgn, (T)m.gamma, fs);
-      else if (d == 1) riemann_axis<T, 2, RIEM>(L, R, vgn, (T)m.gamma, fs);
-      else riemann_axis<T, 0, RIEM>(L, R, vgn, (T)m.gamma, fs);
-      const T sJ = (T)face_metric(m, ps.blk, d);
+      if (d == 0) riemann_axis<T, 1, RIEM>(L, R, vgn, gamma, fs);
+      else if (d == 1) riemann_axis<T, 2, RIEM>(L, R, vgn, gamma, fs);
+      else riemann_axis<T, 0, RIEM>(L, R, vgn, gamma, fs);
+      const T sJ = c[MC_METRIC + 3 * q4.x + d];
       const T sg = side ? sJ : -sJ;
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fo[v] = sg * fs[v];
@@ -141,7 +159,7 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] += d1 * F1[v * NN + n1] + d2 * F2[v * NN + n2] + d3 * F3[v * NN + n3];
   }
-  const T iw0 = T(1) / Prec<T>::w(m.basis)[0];
+  const T iw0 = c[MC_IW0];
   const T* Se = sS + le * 30 * NP2;
   if (i == 0 || i == N) {
     const T* s = Se + (i == 0 ? 0 : 1) * 5 * NP2 + j + NP * k;
@@ -158,8 +176,7 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] += iw0 * s[v * NP2];
   }
-  const T mInvJ = T(-1) / (T)elem_jacobian(m, s_pos[le].x);
-  const long long base = e * 5 * NN + nd;
+  const T mInvJ = c[MC_MINVJ + s_pos[le].x];
   if (MODE == ELEM_RHS) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) out[base + v * NN] = acc[v] * mInvJ;
@@ -167,9 +184,9 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const T ut = acc[v] * mInvJ;
-      T g = (MODE == ELEM_STAGE_FIRST) ? dt * ut : rkA * G[base + v * NN] + dt * ut;
-      G[base + v * NN] = g;
-      out[base + v * NN] = u[v] + rkB * g;
+      const T gn = (MODE == ELEM_STAGE_FIRST) ? dt * ut : rkA * g[v] + dt * ut;
+      G[base + v * NN] = gn;
+      out[base + v * NN] = u[v] + rkB * gn;
     }
   }
 }
@@ -188,8 +205,11 @@ static cudaError_t launch_elem_t(const ElemArgs& a, cudaStream_t st) {
 template <int N, typename T, int RIEM, int MODE>
 static cudaError_t prepare_elem_t() {
   using C = ElemCfg<N>;
-  return cudaFuncSetAttribute(dg_element_kernel<N, T, RIEM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)C::template smem_bytes<T>());
+  cudaError_t e = cudaFuncSetAttribute(dg_element_kernel<N, T, RIEM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::template smem_bytes<T>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(dg_element_kernel<N, T, RIEM, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
 }
 
 template <int N, typename T>

@@ -158,6 +158,41 @@ const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 136
 const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
                         2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
 
+// Fills the per-precision constant block of the kernels (FP64 values, rounded once for FP32).
+void fill_constants(MeshDev& m, const BasisDev& b, const double* fpar) {
+  double c[MC_COUNT] = {0};
+  const double hx[2] = {m.hx0, m.hx1};
+  for (int blk = 0; blk < 2; ++blk) {
+    c[MC_METRIC + 3 * blk + 0] = m.hz * hx[blk] * 0.25;
+    c[MC_METRIC + 3 * blk + 1] = hx[blk] * m.hy * 0.25;
+    c[MC_METRIC + 3 * blk + 2] = m.hy * m.hz * 0.25;
+    c[MC_MINVJ + blk] = -1.0 / (hx[blk] * m.hy * m.hz * 0.125);
+  }
+  c[MC_VG] = m.v;
+  c[MC_GAMMA] = m.gamma;
+  c[MC_IW0] = 1.0 / b.w[0];
+  c[MC_SJ_IF] = m.hy * m.hz * 0.25;
+  const double* P = fpar;   // background primitive state of flows 0 and 2
+  c[MC_BC + 0] = P[0];
+  c[MC_BC + 1] = P[0] * P[1];
+  c[MC_BC + 2] = P[0] * P[2];
+  c[MC_BC + 3] = P[0] * P[3];
+  c[MC_BC + 4] = P[4] / (m.gamma - 1.0) + 0.5 * P[0] * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
+  c[MC_H + 0] = m.hx0;
+  c[MC_H + 1] = m.hx1;
+  c[MC_H + 2] = m.hy;
+  c[MC_H + 3] = m.hz;
+  c[MC_X + 0] = m.x0;
+  c[MC_X + 1] = m.x1;
+  c[MC_X + 2] = m.y0;
+  c[MC_X + 3] = m.z0;
+  for (int k = 0; k < MC_COUNT; ++k) {
+    m.cd[k] = c[k];
+    m.cf[k] = (float)c[k];
+  }
+  for (int k = 0; k < 16; ++k) m.fparf[k] = (float)fpar[k];
+}
+
 struct GraphEntry {
   double dt;
   int cur;
@@ -353,6 +388,7 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
 #undef SM_ALLOC
   m.basis = s->basis_d;
   m.modes = s->modes_d;
+  fill_constants(m, s->basis_h, desc->fpar);
   const char* what = nullptr;
   if ((e = cudaMemcpy(s->basis_d, &s->basis_h, sizeof(BasisDev), cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload basis";
   else if ((e = cudaMemcpy(s->modes_d, &desc->modes[0][0][0], sizeof(double) * 160, cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload modes";
@@ -382,6 +418,8 @@ int sm_set_motion(sm_solver* s, const sm_motion* mo) {
   s->motion = *mo;
   s->m.v = mo->v;
   s->m.delta0 = mo->delta0;
+  s->m.cd[MC_VG] = mo->v;
+  s->m.cf[MC_VG] = (float)mo->v;
   clear_graphs(s);
   return SM_OK;
 }

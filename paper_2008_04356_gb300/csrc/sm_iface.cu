@@ -67,7 +67,8 @@ sliding_interface_kernel(const MeshDev m, const StageParams* __restrict__ sp, co
   __syncthreads();
 
   // mortars mi = 2 r + i_sub for r < TFe, plus mi = 2 TFe (the halo mortar (i0+TFe, 0))
-  const T sJ = (T)(m.hy * m.hz * 0.25);
+  const T sJ = Prec<T>::c(m)[MC_SJ_IF];
+  const T gamma = Prec<T>::c(m)[MC_GAMMA];
   for (int w = tid; w < (2 * TFe + 1) * NP2; w += THREADS) {
     const int mi = w / NP2, ab = w - mi * NP2;
     const int r = mi >> 1, isub = mi & 1;
@@ -89,7 +90,7 @@ sliding_interface_kernel(const MeshDev m, const StageParams* __restrict__ sp, co
       QL[v] = al;
       QR[v] = ar;
     }
-    riemann_axis<T, 0, RIEM>(QL, QR, T(0), (T)m.gamma, F);
+    riemann_axis<T, 0, RIEM>(QL, QR, T(0), gamma, F);
 #pragma unroll
     for (int v = 0; v < 5; ++v) sFm[(mi * 5 + v) * NP2 + ab] = F[v] * sJ;
   }
