@@ -162,6 +162,30 @@ void* sm_state_ptr(sm_solver* s);
 
 void sm_destroy(sm_solver* s);
 
+/* sm_rhs without any device allocation.  The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc, e.g. code running while another framework owns
+ * the device memory through its own pool, code in regions where an allocation (which
+ * synchronises the device) is not acceptable, or embedders that forbid allocations after
+ * start-up.  It computes dU/dt = R(U, t) for the mesh desc and motion into dUt exactly
+ * as sm_init_mesh + sm_set_motion + sm_rhs would, but needs no solver: its scratch (basis
+ * tables, stage parameters, both sides' interface face fluxes) lives in one fixed
+ * 16 MiB device array inside the library, which every GPU that loads the library holds
+ * until the process exits.  The caller owns dU and dUt (device pointers, the solver
+ * layout and precision of desc, not overlapping).
+ *  - Sizes: the scratch needed is about 2 * faces * 5 (N+1)^2 * bytes-per-scalar plus
+ *    ~10 KB (faces = nel_static[1] * nel_static[2]); larger problems are rejected with
+ *    SM_ERR_ARG and a message naming both sizes (use sm_rhs for them).
+ *  - The first call on a device sets that device up (looks up the array's device address
+ *    and sets kernel attributes); make that first call before any stream capture.
+ *  - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - All calls share the one array, whose contents persist from the last call: every byte
+ *    a call reads is written by that same call first, so nothing needs clearing, but calls
+ *    whose work overlaps on the GPU (other streams, other host threads) race with each
+ *    other; serialise them, e.g. on one stream.
+ * Asynchronous on stream. */
+int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, double t, const void* dU, void* dUt,
+                  void* stream);
+
 /* ---- building blocks exposed for testing ---- */
 
 /* Interface configuration for count displacements (Sec. 4.3): for each d_delta[m],

@@ -595,3 +595,132 @@ int sm_mortar_matrices(int N, double sigma, double* d_out, void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Right-hand side without any device allocation (sm_rhs_static).
+//
+// Some callers cannot call cudaMalloc: code that runs while a framework owns the device
+// memory through its own pool (allocating behind it breaks its accounting or fails once
+// it has reserved the device), code inside regions where an allocation would synchronise
+// the device (cudaMalloc and cudaFree wait for outstanding work), and embedders that
+// forbid allocations after start-up.  For them the scratch of the right-hand side — the
+// basis tables, the stage parameters (interface configuration and mortar operators) and
+// both sides' interface face fluxes — lives in one file-scope device array of fixed size
+// that every GPU loading this library holds until the process exits.
+// ---------------------------------------------------------------------------------------
+#define SM_STATIC_SCRATCH_BYTES (16u << 20)
+
+static __device__ __align__(256) unsigned char g_static_scratch[SM_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_addr[256] = {nullptr};
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// Once per device, with that device current: the device address of the scratch array and
+// the kernels' shared-memory attributes.
+int static_scratch_address(int dev, unsigned char** out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (dev < 0 || dev >= 256) return fail(SM_ERR_ARG, "device ordinal out of range");
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    SM_CK(cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress of the static scratch");
+    for (int n = 1; n <= 7; ++n) {
+      SM_CK(prepare_element_f64(n), "element kernel attributes");
+      SM_CK(prepare_element_f32(n), "element kernel attributes");
+      SM_CK(prepare_interface(n, SM_FP64), "interface kernel attributes");
+      SM_CK(prepare_interface(n, SM_FP32), "interface kernel attributes");
+    }
+    g_static_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_static_addr[dev];
+  return SM_OK;
+}
+
+size_t static_scratch_bytes(const sm_mesh_desc* desc) {
+  if (!desc || desc->N < 1 || desc->N > 7) return 0;
+  const size_t np = desc->N + 1, sb = desc->precision == SM_FP64 ? 8 : 4;
+  const size_t faces = (size_t)desc->nel_static[1] * (size_t)desc->nel_static[2];
+  return align256(sizeof(BasisDev)) + align256(sizeof(double) * 160) + align256(sizeof(StageParams)) +
+         2 * align256(faces * 5 * np * np * sb);
+}
+
+}  // namespace
+
+extern "C" int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, double t, const void* dU,
+                             void* dUt, void* stream) {
+  int rc = valid_desc(desc);
+  if (rc != SM_OK) return rc;
+  if (!motion || !dU || !dUt) return fail(SM_ERR_ARG, "NULL argument");
+  if (dU == dUt) return fail(SM_ERR_ARG, "dU and dUt must not overlap");
+  if (motion->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");
+  if (!std::isfinite(motion->v) || !std::isfinite(motion->delta0) || !std::isfinite(t))
+    return fail(SM_ERR_ARG, "non-finite motion or time");
+  if (desc->interface_conforming && (motion->v != 0.0 || motion->delta0 != 0.0))
+    return fail(SM_ERR_ARG, "a conforming interface cannot move");
+  const size_t need = static_scratch_bytes(desc);
+  if (need > SM_STATIC_SCRATCH_BYTES) {
+    char buf[200];
+    snprintf(buf, sizeof(buf), "sm_rhs_static: needs %zu bytes of scratch, more than its fixed %u bytes "
+             "(reduce the interface face count or use sm_rhs)", need, (unsigned)SM_STATIC_SCRATCH_BYTES);
+    return fail(SM_ERR_ARG, buf);
+  }
+  int dev = 0;
+  SM_CK(cudaGetDevice(&dev), "cudaGetDevice");
+  unsigned char* base = nullptr;
+  rc = static_scratch_address(dev, &base);
+  if (rc != SM_OK) return rc;
+  const int N = desc->N, np = N + 1, prec = desc->precision, sb = prec == SM_FP64 ? 8 : 4;
+  BasisDev* d_basis = (BasisDev*)base;
+  double* d_modes = (double*)(base + align256(sizeof(BasisDev)));
+  StageParams* d_sp = (StageParams*)((unsigned char*)d_modes + align256(sizeof(double) * 160));
+  unsigned char* d_fs = (unsigned char*)d_sp + align256(sizeof(StageParams));
+  const size_t fbytes = (size_t)desc->nel_static[1] * desc->nel_static[2] * 5 * np * np * sb;
+  unsigned char* d_fm = d_fs + align256(fbytes);
+  // mesh description, as sm_init_mesh builds it
+  BasisDev basis;
+  lgl_basis(N, basis);
+  MeshDev m;
+  memset(&m, 0, sizeof(m));
+  m.nxs = desc->nel_static[0];
+  m.nxm = desc->nel_moving[0];
+  m.ny = desc->nel_static[1];
+  m.nz = desc->nel_static[2];
+  m.Es = (long long)m.nxs * m.ny * m.nz;
+  m.E = m.Es + (long long)m.nxm * m.ny * m.nz;
+  m.hx0 = (desc->x1 - desc->x0) / m.nxs;
+  m.hx1 = (desc->x2 - desc->x1) / m.nxm;
+  m.hy = (desc->y1 - desc->y0) / m.ny;
+  m.hz = (desc->z1 - desc->z0) / m.nz;
+  m.x0 = desc->x0;
+  m.x1 = desc->x1;
+  m.y0 = desc->y0;
+  m.z0 = desc->z0;
+  m.gamma = desc->gamma;
+  m.conforming = desc->interface_conforming;
+  m.flow = desc->flow;
+  m.v = motion->v;
+  m.delta0 = motion->delta0;
+  for (int k = 0; k < 16; ++k) m.fpar[k] = desc->fpar[k];
+  m.basis = d_basis;
+  m.modes = d_modes;
+  fill_constants(m, basis, desc->fpar);
+  // Every byte the kernels read is written by this call first (basis and modes here, the
+  // stage parameters by the mapper kernel, every interface face by the interface kernel),
+  // so nothing of a previous call's contents is used.
+  cudaStream_t st = (cudaStream_t)stream;
+  SM_CK(cudaMemcpyAsync(d_basis, &basis, sizeof(BasisDev), cudaMemcpyHostToDevice, st), "upload basis");
+  SM_CK(cudaMemcpyAsync(d_modes, &desc->modes[0][0][0], sizeof(double) * 160, cudaMemcpyHostToDevice, st),
+        "upload modes");
+  SM_CK(launch_stage_params(m, np, d_sp, nullptr, t, 0.0, 0.0, 0, st), "stage parameters");
+  if (!desc->interface_conforming)
+    SM_CK(launch_interface(N, prec, desc->riemann, m, d_sp, dU, d_fs, d_fm, st), "interface kernel");
+  ElemArgs a{m, d_sp, dU, dUt, nullptr, d_fs, d_fm, 0.0, 0.0, 0.0};
+  SM_CK(prec == SM_FP64 ? launch_element_f64(N, desc->riemann, ELEM_RHS, a, st)
+                        : launch_element_f32(N, desc->riemann, ELEM_RHS, a, st), "element kernel");
+  // the host copies of basis and modes above are pageable: cudaMemcpyAsync has staged
+  // them before returning, so the stack buffers may go out of scope here.
+  return SM_OK;
+}

@@ -54,6 +54,7 @@ _SIGS = {
     "sm_diag": (C.c_int, [_vp, C.POINTER(SmDiag), _vp]),
     "sm_state_ptr": (_vp, [_vp]),
     "sm_destroy": (None, [_vp]),
+    "sm_rhs_static": (C.c_int, [C.POINTER(SmMeshDesc), C.POINTER(SmMotion), C.c_double, _vp, _vp, _vp]),
     "sm_map": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, _vp, _vp, _vp, _vp]),
     "sm_mortar_matrices": (C.c_int, [C.c_int, C.c_double, _vp, _vp]),
     "sm_status_string": (C.c_char_p, [C.c_int]),
@@ -127,6 +128,19 @@ def sm_map(d_delta, l: float, n_par: int, with_pairs: bool = True, stream=None):
     check(lib().sm_map(d_delta.data_ptr(), count, float(l), int(n_par), n.data_ptr(), s.data_ptr(),
                        pairs.data_ptr() if pairs is not None else None, _stream(stream)), "sm_map")
     return n, s, pairs
+
+
+def sm_rhs_static(problem: synth.Problem, dU, t: float, out=None, stream=None):
+    """dU/dt through the entry point that allocates no device memory (the library keeps its
+    scratch in a fixed device array); dU and out are the caller's device tensors."""
+    import torch
+    if out is None:
+        out = torch.empty_like(dU)
+    desc = mesh_desc(problem)
+    mo = SmMotion(float(problem.v), 0.0, float(problem.delta0))
+    check(lib().sm_rhs_static(C.byref(desc), C.byref(mo), float(t), dU.data_ptr(), out.data_ptr(),
+                              _stream(stream)), "sm_rhs_static")
+    return out
 
 
 def sm_mortar_matrices(N: int, sigma: float, device="cuda", stream=None):
