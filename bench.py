@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=256, help="elements along z (256 = the full workload)")
+    ap.add_argument("--workload", choices=["interface-heavy", "serving"], default="interface-heavy")
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--serve-steps", type=int, default=100)
+    ap.add_argument("--load", type=float, default=0.8, help="offered load as a fraction of measured capacity")
     return ap.parse_args()
 
 
@@ -192,6 +196,100 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------ serving
+def serving_stream(n, steps, seed=12345):
+    """Requests shaped like the serving configuration: N in {3,5,7}, 4k-200k elements
+    (log-uniform, two blocks of 4 x m x m hexes), plane interface, v ~ U[0.1,1], an entropy
+    wave carried at Mach ~ U[0.1,0.8], FP32 bulk; seeded SplitMix64 draws."""
+    import math
+    from paper_2008_04356_gb300 import synth
+    u = synth.uniform(seed, 4 * n).reshape(n, 4)
+    reqs = []
+    for r in range(n):
+        N = (3, 5, 7)[min(2, int(u[r, 0] * 3))]
+        E = math.exp(math.log(4000) + u[r, 1] * (math.log(200000) - math.log(4000)))
+        mm = max(2, int(round(math.sqrt(E / 8.0))))
+        h = 1.0 / mm
+        c = math.sqrt(1.4)
+        ma = 0.1 + 0.7 * u[r, 3]
+        p = synth.Problem(N=N, nel_s=(4, mm, mm), nel_m=(4, mm, mm), x0=0.0, x1=4 * h, x2=8 * h, y1=1.0, z1=1.0,
+                          v=0.1 + 0.9 * u[r, 2], flow=synth.FLOW_ENTROPY_WAVE,
+                          fpar=(1.0, 0.2, 0.0, 1.0, 1.0, ma * c, 0.0, 0.0, 1.0), precision=synth.FP32)
+        reqs.append((p, synth.cfl_dt(p), steps))
+    return reqs
+
+
+def run_serving(args):
+    import numpy as np
+    import torch
+    from paper_2008_04356_gb300 import build as B, slidemesh, synth
+    torch.cuda.set_device(0)
+    B.build_library()
+    reqs = serving_stream(args.requests, args.serve_steps)
+    work = [p.ndof * 5 * n for p, _, n in reqs]
+    # capacity probe: the batched path on the first 8 requests at once
+    probe = [slidemesh.Solver(p) for p, _, _ in reqs[:8]]
+    for s_ in probe:
+        s_.init_state()
+    bt = slidemesh.Batch(probe, [dt for _, dt, _ in reqs[:8]])
+    bt.autotune()
+    bt.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt.step(6)
+    torch.cuda.synchronize()
+    cap = sum(p.ndof * 5 * 6 for p, _, _ in reqs[:8]) / (time.perf_counter() - t0)
+    bt.close()
+    for s_ in probe:
+        s_.close()
+    rate = args.load * cap / (sum(work) / len(work))            # requests per second
+    gaps = -np.log(1.0 - synth.uniform(777, len(reqs))) / rate   # Poisson arrivals
+    srv = slidemesh.Server(hbm_budget_bytes=120 << 30, max_slots=256)
+    tickets = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    for (p, dt, n), g in zip(reqs, gaps):
+        t_next += g
+        while time.perf_counter() < t_next:
+            time.sleep(min(0.002, max(0.0, t_next - time.perf_counter())))
+        tickets.append(srv.submit(p, dt, n))
+    srv.wait(3600)
+    res = [srv.poll(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    thr = sum(work) / span
+    # one-at-a-time FP64 plain path on a sample of the same requests
+    t64, w64 = 0.0, 0
+    for p, dt, n in reqs[:12]:
+        q = synth.Problem(**{**p.__dict__, "precision": synth.FP64})
+        s64 = slidemesh.Solver(q)
+        s64.init_state()
+        s64.step(dt, 1)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        s64.step(dt, 10)
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - a
+        w64 += q.ndof * 5 * 10
+        s64.close()
+    v64 = w64 / t64
+    line = {"metric": METRIC, "workload": "serving", "value": thr, "unit": UNIT, "n_gpus": 1,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "requests": len(reqs), "completed": st["completed"], "failed": st["failed"],
+            "max_concurrent": st["max_concurrent"], "peak_bytes": st["peak_bytes"],
+            "offered_load": args.load, "arrival_rate_per_s": rate, "capacity_probe": cap,
+            "makespan_s": span, "steps_per_request": args.serve_steps,
+            "fp64_one_at_a_time": {"value": v64, "unit": UNIT, "sample": "12 requests x 10 steps"},
+            "batched_fp32_over_fp64_one_at_a_time": thr / v64,
+            "config": {"workload": "Poisson stream of %d sliding-mesh Euler solves, N in {3,5,7}, 4k-200k elements, "
+                                   "v in U[0.1,1], Mach in U[0.1,0.8], %d steps each, FP32 bulk, FP64 mapping, "
+                                   "120 GB budget" % (len(reqs), args.serve_steps)},
+            "data": "synthetic", "dtype": "f32"}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -200,6 +298,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            run_serving(args)
         return
     import numpy as np
     import torch

@@ -186,6 +186,94 @@ void sm_destroy(sm_solver* s);
 int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, double t, const void* dU, void* dUt,
                   void* stream);
 
+/* ---- batched stepping: several solves advanced by shared launches ---- */
+
+/* A batch advances count FP32 solvers (each with its own mesh, degree, motion and time
+ * step dt[i]) together: per RK stage, one persistent launch of each kernel kind per group
+ * of solvers sharing N and the Riemann solver, over a work list of (solve, CTA block)
+ * items; a whole step replays from one CUDA graph.  Each solve's arithmetic is the same as
+ * in a batch of one.  The solvers stay owned by the caller and must outlive the batch;
+ * while in a batch a solver must be advanced only through it (sm_rhs and the state calls
+ * remain usable between steps).  Errors: SM_ERR_ARG (count outside 1..1024, NULL solver,
+ * non-positive dt), SM_ERR_UNSUPPORTED (an FP64 solver: the batched kernels are FP32). */
+typedef struct sm_batch sm_batch;
+int sm_batch_create(sm_solver* const* solvers, const double* dt, int count, sm_batch** out);
+
+/* Chooses the launch shapes of every group (interface tile width 4/8/16 faces, persistent
+ * grid sizes of the interface and element kernels) by timing the candidates on this
+ * batch's own data, without changing any state; the choices are remembered per (N,
+ * Riemann solver, size class) for later batches.  Synchronises stream. */
+int sm_batch_autotune(sm_batch* b, void* stream);
+
+/* nsteps batched RK steps on stream (asynchronous). */
+int sm_batch_step(sm_batch* b, int nsteps, void* stream);
+
+/* Launch shapes in use: for group g (0-based, groups ordered by first member), writes N,
+ * interface tile width, interface grid and element grid into shape[4]; returns the number
+ * of groups (or a negative status). */
+int sm_batch_shapes(const sm_batch* b, int g, int* shape);
+
+void sm_batch_destroy(sm_batch* b);
+
+/* ---- serving: continuous batching of many solves ---- */
+
+/* A request: one sliding-mesh solve of nsteps RK steps of size dt, from the desc's flow at
+ * t = 0 (sm_init_state), with the given motion. */
+typedef struct {
+  sm_mesh_desc desc;
+  sm_motion motion;
+  double dt;
+  int nsteps;
+  int keep_state;      /* 1: keep a host copy of the final state (sm_result.state) */
+} sm_request;
+
+typedef struct {
+  int status;          /* SM_OK when done, SM_PENDING while queued or running, else the error */
+  double t_submit;     /* seconds on the server clock (steady clock since sm_server_create) */
+  double t_admit;      /* when the solve got its slot and device memory */
+  double t_done;       /* when its last step finished on the device */
+  double sim_time;     /* solver time reached */
+  long long dof;       /* elements * (N+1)^3 */
+  int steps;
+  double totals[5];    /* conserved totals of the final state */
+  const void* state;   /* final state (host, solver precision and layout), owned by the server,
+                          valid until sm_server_destroy; NULL unless keep_state */
+  long long state_bytes;
+} sm_result;
+
+typedef struct {
+  long long submitted, completed, failed, running, queued;
+  long long batched_steps;       /* batched RK steps launched */
+  long long dof_updates;         /* sum over completed solves of dof * 5 * steps */
+  double busy_seconds;           /* wall time with at least one solve running */
+  size_t bytes_in_use, peak_bytes;
+  int max_concurrent;
+} sm_server_stats_out;
+
+typedef struct sm_server sm_server;
+
+/* Starts a server on the current device with a worker thread.  Requests are admitted in
+ * arrival order whenever a slot is free (at most max_slots solves resident) and the
+ * solve's device memory fits in hbm_budget_bytes next to the ones already resident; all
+ * resident solves are advanced together (FP32 solves through one batch per degree N and
+ * Riemann solver, FP64 solves one at a time), and new requests join between steps. */
+int sm_server_create(size_t hbm_budget_bytes, int max_slots, sm_server** out);
+
+/* Queues a request (thread-safe, returns immediately); *ticket identifies it.
+ * SM_ERR_ARG for an invalid request; SM_ERR_OOM if it could never fit the budget. */
+int sm_submit(sm_server* s, const sm_request* req, uint64_t* ticket);
+
+/* Status of a request (thread-safe): SM_PENDING until its last step is done. */
+int sm_poll(sm_server* s, uint64_t ticket, sm_result* out);
+
+/* Waits until every submitted request is done or timeout_s passes (SM_ERR_TIMEOUT). */
+int sm_server_wait(sm_server* s, double timeout_s);
+
+int sm_server_stats(sm_server* s, sm_server_stats_out* out);
+
+/* Stops the worker (finishing no further steps), frees every solve and result. */
+void sm_server_destroy(sm_server* s);
+
 /* ---- building blocks exposed for testing ---- */
 
 /* Interface configuration for count displacements (Sec. 4.3): for each d_delta[m],

@@ -37,7 +37,7 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or os.environ.get("SM_NVCC_EXTRA"):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
@@ -48,7 +48,8 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags=None) 
         return LIB
     os.makedirs(OBJDIR, exist_ok=True)
     cc = nvcc()
-    flags = ARCH + NVCC_FLAGS + list(extra_flags or []) + ["-I", INCLUDE, "-I", CSRC]
+    env_flags = os.environ.get("SM_NVCC_EXTRA", "").split()
+    flags = ARCH + NVCC_FLAGS + list(extra_flags or []) + env_flags + ["-I", INCLUDE, "-I", CSRC]
 
     def compile_one(src):
         obj = os.path.join(OBJDIR, os.path.basename(src).replace(".cu", ".o"))

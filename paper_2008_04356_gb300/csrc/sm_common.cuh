@@ -68,6 +68,10 @@ struct MeshDev {
   float cf[MC_COUNT];
   double cd[MC_COUNT];
   float fparf[16];
+  // Optional precomputed topology, two int4 per element: (nb0, nb1, nb2, nb3) and
+  // (nb4, nb5, (ix << 1) | blk, iz * ny + iy), neighbour codes as in the element kernel
+  // (>= 0 element, -1 weak Dirichlet face, -2 sliding interface).  NULL: computed on the fly.
+  const int4* topo;
 };
 
 template <typename T> struct Prec;
@@ -107,20 +111,21 @@ __device__ __forceinline__ float Prec<float>::fpar(const MeshDev& m, int k) { re
 // ---------------------------------------------------------------------------------------
 struct ElemPos { int blk, ix, iy, iz; };
 
-__device__ __forceinline__ ElemPos decode_elem(const MeshDev& m, long long e) {
+// Element counts stay below 2^31 (checked when a solver is created): 32-bit arithmetic.
+__host__ __device__ __forceinline__ ElemPos decode_elem(const MeshDev& m, long long e64) {
   ElemPos p;
-  long long loc = e;
+  int loc = (int)e64;
   int nx = m.nxs;
   p.blk = 0;
-  if (e >= m.Es) { p.blk = 1; loc = e - m.Es; nx = m.nxm; }
-  long long r = loc / nx;
-  p.ix = (int)(loc - r * nx);
-  p.iy = (int)(r % m.ny);
-  p.iz = (int)(r / m.ny);
+  if (e64 >= m.Es) { p.blk = 1; loc = (int)(e64 - m.Es); nx = m.nxm; }
+  const int r = loc / nx;
+  p.ix = loc - r * nx;
+  p.iy = r % m.ny;
+  p.iz = r / m.ny;
   return p;
 }
 
-__device__ __forceinline__ long long encode_elem(const MeshDev& m, int blk, int ix, int iy, int iz) {
+__host__ __device__ __forceinline__ long long encode_elem(const MeshDev& m, int blk, int ix, int iy, int iz) {
   int nx = blk ? m.nxm : m.nxs;
   return (blk ? m.Es : 0) + ix + (long long)nx * (iy + (long long)m.ny * iz);
 }
@@ -133,7 +138,7 @@ __device__ __forceinline__ int face_vol_node(int d, int side, int a, int b) {
 
 // Neighbour across face (d, side): kind 0 conforming (returns element), 1 weak Dirichlet
 // boundary (x = x0 of the static block, x = x2 of the moving block), 2 sliding interface.
-__device__ __forceinline__ int face_neighbor(const MeshDev& m, const ElemPos& p, int d, int side, long long* nb) {
+__host__ __device__ __forceinline__ int face_neighbor(const MeshDev& m, const ElemPos& p, int d, int side, long long* nb) {
   if (d == 0) {
     int iy = p.iy + (side ? 1 : -1);
     iy = iy < 0 ? iy + m.ny : (iy >= m.ny ? iy - m.ny : iy);
@@ -255,6 +260,27 @@ __device__ __forceinline__ void riemann_axis(const T UL[5], const T UR[5], T vgn
   D[4] = w1 * (Hh - unh * ch) + w2 * T(0.5) * q2 + al2 * rh * (udu - unh * dun) + w5 * (Hh + unh * ch);
 #pragma unroll
   for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * D[k];
+}
+
+// Cyclic rotation of the momentum components that brings physical axis ax (0 = x, 1 = y,
+// 2 = z) to the first slot: (m_ax, m_ax+1, m_ax+2) (indices mod 3).  A cyclic permutation
+// is a proper rotation, under which the Riemann fluxes are invariant, so every face is
+// solved as an x-normal face by one code path.
+template <typename T>
+__device__ __forceinline__ void rotate_to_x(const T U[5], int ax, T R[5]) {
+  R[0] = U[0];
+  R[4] = U[4];
+  R[1] = ax == 0 ? U[1] : (ax == 1 ? U[2] : U[3]);
+  R[2] = ax == 0 ? U[2] : (ax == 1 ? U[3] : U[1]);
+  R[3] = ax == 0 ? U[3] : (ax == 1 ? U[1] : U[2]);
+}
+template <typename T>
+__device__ __forceinline__ void rotate_from_x(const T R[5], int ax, T U[5]) {
+  U[0] = R[0];
+  U[4] = R[4];
+  U[1] = ax == 0 ? R[1] : (ax == 1 ? R[3] : R[2]);
+  U[2] = ax == 0 ? R[2] : (ax == 1 ? R[1] : R[3]);
+  U[3] = ax == 0 ? R[3] : (ax == 1 ? R[2] : R[1]);
 }
 
 // Exterior state of a weak Dirichlet face at physical position X and time t, in the

@@ -6,3 +6,5 @@ cudaError_t launch_element_f64(int N, int riemann, int mode, const ElemArgs& a, 
 }
 
 cudaError_t prepare_element_f64(int N) { SM_ELEM_PREPARE(double, N) }
+
+cudaError_t upload_dhat_f64(const float* f, const double* d) { return upload_dhat_here(f, d); }

@@ -18,8 +18,14 @@ template <int N> struct ElemCfg {
   static constexpr int NP = N + 1, NP2 = NP * NP, NN = NP * NP * NP;
   static constexpr int EPB = N == 1 ? 32 : (N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 2 : 1)));
   static constexpr int THREADS = EPB * NN;
+  // resident CTAs per SM asked of the register allocator in FP32 mode (about 48 registers)
+#ifdef SM_ELEM_MINB_OVERRIDE
+  static constexpr int MINB = SM_ELEM_MINB_OVERRIDE;
+#else
+  static constexpr int MINB = N == 1 ? 4 : (N == 6 ? 4 : (N == 7 ? 2 : (N == 2 || N == 3 || N == 4 ? 5 : 6)));
+#endif
   template <typename T> static constexpr size_t smem_bytes() {
-    return sizeof(T) * (size_t)(EPB * 5 * NN + EPB * 15 * NN + EPB * 30 * NP2 + NP2 + 8);
+    return sizeof(T) * (size_t)(EPB * 15 * NN + EPB * 30 * NP2 + NP2 + 8);
   }
 };
 
@@ -27,43 +33,90 @@ template <int N> struct ElemCfg {
 // -2 sliding interface face.
 enum { NB_BOUNDARY = -1, NB_INTERFACE = -2 };
 
+// Contraction line of NP values starting at p (shared memory), read with vector loads when
+// the line length allows aligned pairs or quadruples.
+template <typename T, int NP>
+__device__ __forceinline__ void load_line(const T* p, T (&r)[NP]) {
+  if constexpr (sizeof(T) == 4 && NP % 4 == 0) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int h = 0; h < NP / 4; ++h) {
+      const float4 x = q[h];
+      r[4 * h] = x.x; r[4 * h + 1] = x.y; r[4 * h + 2] = x.z; r[4 * h + 3] = x.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && NP % 2 == 0) {
+    const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+    for (int h = 0; h < NP / 2; ++h) {
+      const float2 x = q[h];
+      r[2 * h] = x.x; r[2 * h + 1] = x.y;
+    }
+  } else if constexpr (sizeof(T) == 8 && NP % 2 == 0) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int h = 0; h < NP / 2; ++h) {
+      const double2 x = q[h];
+      r[2 * h] = x.x; r[2 * h + 1] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < NP; ++l) r[l] = p[l];
+  }
+}
+
+// Weak-form derivative matrices Dhat for N = 1..7 in constant memory, [N-1][i*8 + l]; the
+// line contractions below index them with compile-time constants, so every Dhat entry is
+// an operand of the multiply-add itself.  Each translation unit that instantiates the
+// element kernels has its own copy, filled once per device through upload_dhat_here().
+static __constant__ float c_dhat_f[7][SM_MAXNP * SM_MAXNP];
+static __constant__ double c_dhat_d[7][SM_MAXNP * SM_MAXNP];
+
+static inline cudaError_t upload_dhat_here(const float* f, const double* d) {
+  cudaError_t e = cudaMemcpyToSymbol(c_dhat_f, f, sizeof(float) * 7 * SM_MAXNP * SM_MAXNP);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_dhat_d, d, sizeof(double) * 7 * SM_MAXNP * SM_MAXNP);
+}
+
+template <typename T> __device__ __forceinline__ T dhat_c(int n, int idx);
+template <> __device__ __forceinline__ float dhat_c<float>(int n, int idx) { return c_dhat_f[n - 1][idx]; }
+template <> __device__ __forceinline__ double dhat_c<double>(int n, int idx) { return c_dhat_d[n - 1][idx]; }
+
+// Volume integral as one in-place contraction per (direction, variable, line) (1), or per
+// node over its three lines (0).
+#ifndef SM_ELEM_LINES
+#define SM_ELEM_LINES 1
+#endif
+
+// The work of one CTA: elements e0 .. e0+EPB-1 of one solve.  Shared by the single-solve
+// kernel below and the batched persistent kernel.
+//
+// One barrier per element: before it, every thread computes its node's contravariant
+// fluxes into shared memory and one face-node Riemann flux (own and neighbour traces both
+// read from the state in global memory, the neighbour codes from the topology table), so
+// no thread needs another thread's result until the volume/surface phase after it.
 template <int N, typename T, int RIEM, int MODE>
-__global__ void __launch_bounds__(ElemCfg<N>::THREADS)
-dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
-                  T* __restrict__ out, T* __restrict__ G, const T* __restrict__ Fs,
-                  const T* __restrict__ Fm, const T rkA, const T rkB, const T dt) {
+__device__ __forceinline__ void element_block(const MeshDev& m, const StageParams* __restrict__ sp,
+                                              const T* __restrict__ U, T* __restrict__ out, T* __restrict__ G,
+                                              const T* __restrict__ Fs, const T* __restrict__ Fm, const T rkA,
+                                              const T rkB, const T dt, const long long e0) {
   using C = ElemCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sU = reinterpret_cast<T*>(smem_raw);        // [EPB][5][NN]
-  T* sF = sU + EPB * 5 * NN;                     // [EPB][3][5][NN] contravariant fluxes
+  // contravariant fluxes, each direction stored with its contraction index contiguous:
+  // F~1 at [v][k][j][i], F~2 at [v][k][i][j], F~3 at [v][j][i][k]
+  T* sF = reinterpret_cast<T*>(smem_raw);        // [EPB][3][5][NN]
   T* sS = sF + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
   T* sD = sS + EPB * 30 * NP2;                   // [NP][NP] Dhat
-  __shared__ int4 s_pos[EPB];
-  __shared__ int s_nb[EPB][6];
-  __shared__ T s_t, s_delta;
 
   const T* c = Prec<T>::c(m);
   const int tid = threadIdx.x;
   const int le = tid / NN, nd = tid - le * NN;
-  const long long e0 = (long long)blockIdx.x * EPB;
   const long long e = e0 + le;
   const bool active = e < m.E;
   const long long base = e * 5 * NN + nd;
+  const T gamma = c[MC_GAMMA];
 
-  // ---- prologue: element positions, face-neighbour table, Dhat, state, early G fetch ----
   if (tid < NP2) sD[tid] = Prec<T>::dhat(m.basis)[(tid / NP) * SM_MAXNP + (tid % NP)];
-  if (tid < 6 * EPB) {
-    const int l2 = tid / 6, fc = tid - l2 * 6;
-    if (e0 + l2 < m.E) {
-      const ElemPos p = decode_elem(m, e0 + l2);
-      if (fc == 0) s_pos[l2] = make_int4(p.blk, p.ix, p.iy, p.iz);
-      long long nb = 0;
-      const int kind = face_neighbor(m, p, fc >> 1, fc & 1, &nb);
-      s_nb[l2][fc] = kind == 0 ? (int)nb : (kind == 1 ? NB_BOUNDARY : NB_INTERFACE);
-    }
-  }
-  if (tid == THREADS - 1) { s_t = (T)sp->t; s_delta = (T)sp->delta; }
   T u[5], g[5];
   if (active) {
 #pragma unroll
@@ -72,26 +125,21 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
 #pragma unroll
       for (int v = 0; v < 5; ++v) g[v] = G[base + v * NN];
     }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) sU[(le * 5 + v) * NN + nd] = u[v];
-  }
-  __syncthreads();
-  const T gamma = c[MC_GAMMA];
-  if (active) {
-    const int blk = s_pos[le].x;
+    const int blk = e >= m.Es;
     const Prim<T> q = primitives(u, gamma);
     T f[5];
-    T* Fe = sF + le * 15 * NN + nd;
+    const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
+    T* Fe = sF + le * 15 * NN;
     const T a0 = c[MC_METRIC + 3 * blk], a1 = c[MC_METRIC + 3 * blk + 1], a2 = c[MC_METRIC + 3 * blk + 2];
     axis_flux<T, 1>(u, q, blk ? c[MC_VG] : T(0), f);          // xi^1 -> y (grid velocity)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[v * NN] = a0 * f[v];
+    for (int v = 0; v < 5; ++v) Fe[v * NN + nd] = a0 * f[v];
     axis_flux<T, 2>(u, q, T(0), f);                             // xi^2 -> z
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN] = a1 * f[v];
+    for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN + j + NP * (i + NP * k)] = a1 * f[v];
     axis_flux<T, 0>(u, q, T(0), f);                             // xi^3 -> x
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN] = a2 * f[v];
+    for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN + k + NP * (i + NP * j)] = a2 * f[v];
   }
 
   // ---- face fluxes: one work item per (element, face, face node) ----
@@ -99,43 +147,71 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
     const int l2 = w / (6 * NP2);
     const int r = w - l2 * 6 * NP2;
     const int fc = r / NP2, ab = r - fc * NP2;
-    if (e0 + l2 >= m.E) continue;
+    const long long e2 = e0 + l2;
+    if (e2 >= m.E) continue;
+    const int blk2 = e2 >= m.Es;
     const int d = fc >> 1, side = fc & 1;
     const int a = ab % NP, b = ab / NP;
-    const int vn = face_vol_node<NP>(d, side, a, b);
-    const int nb = s_nb[l2][fc];
-    const int4 q4 = s_pos[l2];
+    // strides of the face-normal index and of the two in-face indices (a, b)
+    const int sn = d == 0 ? 1 : (d == 1 ? NP : NP2);
+    const int sab = d == 0 ? NP * ab : (d == 1 ? a + NP2 * b : ab);
+    const int vn = sab + (side ? N : 0) * sn;
+    // neighbour code and packed position: topology table, or derived from the index
+    int nb, pos_ix = 0, pos_f = 0;
+    const int* tp = m.topo ? reinterpret_cast<const int*>(m.topo) + 8 * e2 : nullptr;
+    if (tp) {
+      nb = tp[fc];
+    } else {
+      const ElemPos p = decode_elem(m, e2);
+      long long q = 0;
+      const int kind = face_neighbor(m, p, d, side, &q);
+      nb = kind == 0 ? (int)q : (kind == 1 ? NB_BOUNDARY : NB_INTERFACE);
+      pos_ix = p.ix;
+      pos_f = p.iz * m.ny + p.iy;
+    }
     T Fo[5];
     if (nb == NB_INTERFACE) {
-      const T* src = (q4.x ? Fm : Fs) + ((long long)q4.w * m.ny + q4.z) * 5 * NP2 + ab;
+      const int fi = tp ? tp[7] : pos_f;
+      const T* src = (blk2 ? Fm : Fs) + (long long)fi * 5 * NP2 + ab;
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fo[v] = src[v * NP2];
     } else {
-      T uin[5], uout[5], fs[5];
+      T uin[5], uout[5];
+      const T* Ui = U + e2 * 5 * NN + vn;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) uin[v] = sU[(l2 * 5 + v) * NN + vn];
+      for (int v = 0; v < 5; ++v) uin[v] = Ui[v * NN];
       if (nb >= 0) {
-        const T* Un = U + (long long)nb * 5 * NN + face_vol_node<NP>(d, 1 - side, a, b);
+        const T* Un = U + (long long)nb * 5 * NN + sab + (side ? 0 : N) * sn;
 #pragma unroll
         for (int v = 0; v < 5; ++v) uout[v] = Un[v * NN];
       } else {
         // weak Dirichlet face (x = x0 or x = x2): node position at the stage time
+        if (tp) { pos_ix = tp[6] >> 1; pos_f = tp[7]; }
+        const int iy = pos_f % m.ny, iz = pos_f / m.ny;
         const T* xi = Prec<T>::x(m.basis);
         const int i = vn % NP, j = (vn / NP) % NP, k = vn / NP2;
-        const T hx = c[MC_H + q4.x];
+        const T hx = c[MC_H + blk2];
         T X[3];
-        X[0] = c[MC_X + q4.x] + (T)q4.y * hx + (xi[k] + T(1)) * T(0.5) * hx;
-        X[1] = c[MC_X + 2] + (T)q4.z * c[MC_H + 2] + (xi[i] + T(1)) * T(0.5) * c[MC_H + 2] + (q4.x ? s_delta : T(0));
-        X[2] = c[MC_X + 3] + (T)q4.w * c[MC_H + 3] + (xi[j] + T(1)) * T(0.5) * c[MC_H + 3];
-        boundary_state<T>(m, X, s_t, uout);
+        X[0] = c[MC_X + blk2] + (T)pos_ix * hx + (xi[k] + T(1)) * T(0.5) * hx;
+        X[1] = c[MC_X + 2] + (T)iy * c[MC_H + 2] + (xi[i] + T(1)) * T(0.5) * c[MC_H + 2] + (blk2 ? (T)sp->delta : T(0));
+        X[2] = c[MC_X + 3] + (T)iz * c[MC_H + 3] + (xi[j] + T(1)) * T(0.5) * c[MC_H + 3];
+        boundary_state<T>(m, X, (T)sp->t, uout);
       }
-      const T vgn = (d == 0 && q4.x) ? c[MC_VG] : T(0);
-      const T* L = side ? uin : uout;
-      const T* R = side ? uout : uin;
-      if (d == 0) riemann_axis<T, 1, RIEM>(L, R, vgn, gamma, fs);
-      else if (d == 1) riemann_axis<T, 2, RIEM>(L, R, vgn, gamma, fs);
-      else riemann_axis<T, 0, RIEM>(L, R, vgn, gamma, fs);
-      const T sJ = c[MC_METRIC + 3 * q4.x + d];
+      // canonical orientation: left = minus-side element, normal +axis
+      const int ax = d == 0 ? 1 : (d == 1 ? 2 : 0);
+      T L[5], R[5], fl[5], fs[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        L[v] = side ? uin[v] : uout[v];
+        R[v] = side ? uout[v] : uin[v];
+      }
+      T Lr[5], Rr[5];
+      rotate_to_x(L, ax, Lr);
+      rotate_to_x(R, ax, Rr);
+      const T vgn = (d == 0 && blk2) ? c[MC_VG] : T(0);
+      riemann_axis<T, 0, RIEM>(Lr, Rr, vgn, gamma, fl);
+      rotate_from_x(fl, ax, fs);
+      const T sJ = c[MC_METRIC + 3 * blk2 + d];
       const T sg = side ? sJ : -sJ;
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fo[v] = sg * fs[v];
@@ -143,22 +219,67 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
 #pragma unroll
     for (int v = 0; v < 5; ++v) sS[((l2 * 6 + fc) * 5 + v) * NP2 + ab] = Fo[v];
   }
-  __syncthreads();
-  if (!active) return;
 
   // ---- volume integral (sum factorisation) + surface integral ----
   const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
-  T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
-  const T* F1 = sF + le * 15 * NN;
-  const T* F2 = F1 + 5 * NN;
-  const T* F3 = F1 + 10 * NN;
+  T acc[5];
+#if SM_ELEM_LINES
+  // every contraction line (direction, variable, line) once: read its NP fluxes, write the
+  // NP derivative values back in place; Dhat entries are constant-memory operands
+  __syncthreads();
+  for (int w = tid; w < EPB * 15 * NP2; w += THREADS) {
+    const int l2 = w / (15 * NP2);
+    const int rr = w - l2 * 15 * NP2;
+    T* line = sF + l2 * 15 * NN + (rr / NP2) * NN + (rr % NP2) * NP;
+    T rv[NP], ov[NP];
+    load_line<T, NP>(line, rv);
 #pragma unroll
-  for (int l = 0; l < NP; ++l) {
-    const T d1 = sD[i * NP + l], d2 = sD[j * NP + l], d3 = sD[k * NP + l];
-    const int n1 = l + NP * (j + NP * k), n2 = i + NP * (l + NP * k), n3 = i + NP * (j + NP * l);
+    for (int a = 0; a < NP; ++a) {
+      T s = T(0);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] += d1 * F1[v * NN + n1] + d2 * F2[v * NN + n2] + d3 * F3[v * NN + n3];
+      for (int l = 0; l < NP; ++l) s += dhat_c<T>(N, a * SM_MAXNP + l) * rv[l];
+      ov[a] = s;
+    }
+#pragma unroll
+    for (int a = 0; a < NP; ++a) line[a] = ov[a];
   }
+  __syncthreads();
+  if (!active) return;
+  {
+    const T* F1 = sF + le * 15 * NN + nd;
+    const T* F2 = sF + le * 15 * NN + 5 * NN + j + NP * (i + NP * k);
+    const T* F3 = sF + le * 15 * NN + 10 * NN + k + NP * (i + NP * j);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] = F1[v * NN] + F2[v * NN] + F3[v * NN];
+  }
+#else
+  __syncthreads();
+  if (!active) return;
+  {
+    T d1[NP], d2[NP], d3[NP];
+    load_line<T, NP>(sD + i * NP, d1);
+    load_line<T, NP>(sD + j * NP, d2);
+    load_line<T, NP>(sD + k * NP, d3);
+    const T* F1 = sF + le * 15 * NN + NP * (j + NP * k);
+    const T* F2 = sF + le * 15 * NN + 5 * NN + NP * (i + NP * k);
+    const T* F3 = sF + le * 15 * NN + 10 * NN + NP * (i + NP * j);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      T r[NP];
+      T a = T(0);
+      load_line<T, NP>(F1 + v * NN, r);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) a += d1[l] * r[l];
+      load_line<T, NP>(F2 + v * NN, r);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) a += d2[l] * r[l];
+      load_line<T, NP>(F3 + v * NN, r);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) a += d3[l] * r[l];
+      acc[v] = a;
+    }
+  }
+#endif
   const T iw0 = c[MC_IW0];
   const T* Se = sS + le * 30 * NP2;
   if (i == 0 || i == N) {
@@ -176,7 +297,7 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] += iw0 * s[v * NP2];
   }
-  const T mInvJ = c[MC_MINVJ + s_pos[le].x];
+  const T mInvJ = c[MC_MINVJ + (e >= m.Es)];
   if (MODE == ELEM_RHS) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) out[base + v * NN] = acc[v] * mInvJ;
@@ -189,6 +310,14 @@ dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* 
       out[base + v * NN] = u[v] + rkB * gn;
     }
   }
+}
+
+template <int N, typename T, int RIEM, int MODE>
+__global__ void __launch_bounds__(ElemCfg<N>::THREADS, sizeof(T) == 4 ? ElemCfg<N>::MINB : 1)
+dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
+                  T* __restrict__ out, T* __restrict__ G, const T* __restrict__ Fs,
+                  const T* __restrict__ Fm, const T rkA, const T rkB, const T dt) {
+  element_block<N, T, RIEM, MODE>(m, sp, U, out, G, Fs, Fm, rkA, rkB, dt, (long long)blockIdx.x * ElemCfg<N>::EPB);
 }
 
 template <int N, typename T, int RIEM, int MODE>

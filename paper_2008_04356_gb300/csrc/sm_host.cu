@@ -9,6 +9,7 @@
 // previous stage while the element kernel writes the new one.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -193,6 +194,35 @@ void fill_constants(MeshDev& m, const BasisDev& b, const double* fpar) {
   for (int k = 0; k < 16; ++k) m.fparf[k] = (float)fpar[k];
 }
 
+// Once per device: the Dhat tables of every degree in each element-kernel unit's constant
+// memory.
+std::mutex g_dhat_mu;
+bool g_dhat_done[256] = {false};
+
+cudaError_t ensure_dhat_constants() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_dhat_mu);
+  if (g_dhat_done[dev]) return cudaSuccess;
+  static float f[7][SM_MAXNP * SM_MAXNP];
+  static double d[7][SM_MAXNP * SM_MAXNP];
+  for (int n = 1; n <= 7; ++n) {
+    BasisDev b;
+    lgl_basis(n, b);
+    for (int k = 0; k < SM_MAXNP * SM_MAXNP; ++k) {
+      d[n - 1][k] = b.Dhat[k];
+      f[n - 1][k] = b.Dhat_f[k];
+    }
+  }
+  if ((e = upload_dhat_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_batch(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  g_dhat_done[dev] = true;
+  return cudaSuccess;
+}
+
 struct GraphEntry {
   double dt;
   int cur;
@@ -217,6 +247,7 @@ struct sm_solver {
   StageParams* sp = nullptr;
   double* t_d = nullptr;
   double* red_d = nullptr;      // partial sums [nblk][5] + outputs [3][5]
+  int4* topo_d = nullptr;       // per-element neighbour table (2 int4 per element)
   int red_blocks = 0;
   int cur = 0;
   double t_host = 0.0;
@@ -283,7 +314,7 @@ void free_solver(sm_solver* s) {
   if (!s) return;
   clear_graphs(s);
   if (s->cap) cudaStreamDestroy(s->cap);
-  void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->t_d, s->red_d};
+  void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->t_d, s->red_d, s->topo_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -385,19 +416,36 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   SM_ALLOC(s->sp, sizeof(StageParams));
   SM_ALLOC(s->t_d, sizeof(double));
   SM_ALLOC(s->red_d, sizeof(double) * (s->red_blocks * 5 + 15));
+  SM_ALLOC(s->topo_d, sizeof(int4) * 2 * (size_t)m.E);
 #undef SM_ALLOC
   m.basis = s->basis_d;
   m.modes = s->modes_d;
+  m.topo = s->topo_d;
   fill_constants(m, s->basis_h, desc->fpar);
+  // static mesh topology: neighbour codes and packed position of every element
+  std::vector<int4> topo(2 * (size_t)m.E);
+  for (long long e = 0; e < m.E; ++e) {
+    ElemPos p = decode_elem(m, e);
+    int nb[6];
+    for (int fc = 0; fc < 6; ++fc) {
+      long long q = 0;
+      int kind = face_neighbor(m, p, fc >> 1, fc & 1, &q);
+      nb[fc] = kind == 0 ? (int)q : (kind == 1 ? -1 : -2);
+    }
+    topo[2 * e] = make_int4(nb[0], nb[1], nb[2], nb[3]);
+    topo[2 * e + 1] = make_int4(nb[4], nb[5], (p.ix << 1) | p.blk, p.iz * m.ny + p.iy);
+  }
   const char* what = nullptr;
   if ((e = cudaMemcpy(s->basis_d, &s->basis_h, sizeof(BasisDev), cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload basis";
   else if ((e = cudaMemcpy(s->modes_d, &desc->modes[0][0][0], sizeof(double) * 160, cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload modes";
+  else if ((e = cudaMemcpy(s->topo_d, topo.data(), sizeof(int4) * topo.size(), cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload topology";
   else if ((e = cudaMemset(s->G, 0, sbytes)) != cudaSuccess) what = "clear G";
   else if ((e = cudaMemset(s->U[0], 0, sbytes)) != cudaSuccess) what = "clear U";
   else if ((e = cudaMemset(s->Fs, 0, fbytes)) != cudaSuccess || (e = cudaMemset(s->Fm, 0, fbytes)) != cudaSuccess) what = "clear F";
   else if ((e = cudaMemset(s->t_d, 0, sizeof(double))) != cudaSuccess) what = "clear t";
   else if ((e = cudaMemset(s->sp, 0, sizeof(StageParams))) != cudaSuccess) what = "clear stage params";
   else if ((e = (s->prec == SM_FP64 ? prepare_element_f64(s->N) : prepare_element_f32(s->N))) != cudaSuccess) what = "element kernel attributes";
+  else if ((e = ensure_dhat_constants()) != cudaSuccess) what = "derivative constants";
   else if ((e = prepare_interface(s->N, s->prec)) != cudaSuccess) what = "interface kernel attributes";
   else if ((e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking)) != cudaSuccess) what = "capture stream";
   else if ((e = cudaDeviceSynchronize()) != cudaSuccess) what = "init sync";
@@ -597,6 +645,291 @@ int sm_mortar_matrices(int N, double sigma, double* d_out, void* stream) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------
+// Batched stepping (sm_batch_*).
+// ---------------------------------------------------------------------------------------
+struct sm_batch {
+  struct Group {
+    int N = 0, riem = 0;
+    std::vector<int> members;
+    std::vector<BatchSolveDev> host;
+    BatchSolveDev* d_bs = nullptr;
+    int* d_offs_el = nullptr;
+    int* d_offs_if = nullptr;
+    int total_el = 0, total_if = 0;
+    int grid_el = 0, grid_if = 0, tf = 8;
+  };
+  std::vector<sm_solver*> solvers;
+  std::vector<double> dt;
+  std::vector<Group> groups;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int sms = 152;
+};
+
+namespace {
+
+struct TuneKey { int N, riem, size_class; };
+struct TuneVal { int tf, grid_if_per_sm, grid_el_per_sm; };
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+
+int size_class(long long elems) { int c = 0; while (elems > 1) { elems >>= 1; ++c; } return c / 2; }
+
+bool tune_lookup(const TuneKey& k, TuneVal* v) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& p : g_tune)
+    if (p.first.N == k.N && p.first.riem == k.riem && p.first.size_class == k.size_class) { *v = p.second; return true; }
+  return false;
+}
+void tune_store(const TuneKey& k, const TuneVal& v) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& p : g_tune)
+    if (p.first.N == k.N && p.first.riem == k.riem && p.first.size_class == k.size_class) { p.second = v; return; }
+  g_tune.push_back({k, v});
+}
+
+long long group_elems(const sm_batch& b, const sm_batch::Group& g) {
+  long long e = 0;
+  for (int i : g.members) e += b.solvers[i]->m.E;
+  return e;
+}
+
+// interface work-item offsets for tile width tf
+cudaError_t upload_if_offsets(sm_batch::Group& g, const sm_batch& b, int tf) {
+  std::vector<int> offs(g.members.size() + 1, 0);
+  for (size_t q = 0; q < g.members.size(); ++q) {
+    const MeshDev& m = b.solvers[g.members[q]]->m;
+    offs[q + 1] = offs[q] + ((m.ny + tf - 1) / tf) * m.nz;
+  }
+  g.total_if = offs.back();
+  g.tf = tf;
+  return cudaMemcpy(g.d_offs_if, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice);
+}
+
+void free_batch(sm_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (auto& g : b->groups) {
+    if (g.d_bs) cudaFree(g.d_bs);
+    if (g.d_offs_el) cudaFree(g.d_offs_el);
+    if (g.d_offs_if) cudaFree(g.d_offs_if);
+  }
+  delete b;
+}
+
+cudaError_t enqueue_batch_step(sm_batch* b, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 5; ++k)
+    for (auto& g : b->groups) {
+      const int n = (int)g.members.size();
+      if ((e = launch_batch_stage_params(g.N, g.d_bs, n, RK_C[k], k == 4 ? 2 : 1, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_interface(g.N, g.riem, g.tf, g.d_bs, g.d_offs_if, n, g.grid_if, k, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_element(g.N, g.riem, k == 0 ? ELEM_STAGE_FIRST : ELEM_STAGE, g.d_bs, g.d_offs_el, n, g.grid_el,
+                                    k, RK_A[k], RK_B[k], st)) != cudaSuccess)
+        return e;
+    }
+  for (auto& g : b->groups)
+    if ((e = launch_batch_flip(g.d_bs, (int)g.members.size(), st)) != cudaSuccess) return e;
+  return e;
+}
+
+}  // namespace
+
+extern "C" int sm_batch_create(sm_solver* const* solvers, const double* dt, int count, sm_batch** out) {
+  if (!out || !solvers || !dt) return fail(SM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (count < 1 || count > SM_MAX_BATCH) return fail(SM_ERR_ARG, "batch size must be in 1..1024");
+  for (int i = 0; i < count; ++i) {
+    if (!solvers[i]) return fail(SM_ERR_ARG, "NULL solver in batch");
+    if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return fail(SM_ERR_ARG, "batch time steps must be positive");
+    if (solvers[i]->prec != SM_FP32) return fail(SM_ERR_UNSUPPORTED, "batched kernels are FP32; step FP64 solvers with sm_step");
+  }
+  sm_batch* b = new (std::nothrow) sm_batch();
+  if (!b) return fail(SM_ERR_OOM, "host allocation");
+  b->solvers.assign(solvers, solvers + count);
+  b->dt.assign(dt, dt + count);
+  int dev = 0;
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, (cudaGetDevice(&dev), dev));
+  for (int i = 0; i < count; ++i) {
+    const int N = solvers[i]->N, riem = solvers[i]->desc.riemann;
+    sm_batch::Group* g = nullptr;
+    for (auto& q : b->groups)
+      if (q.N == N && q.riem == riem) g = &q;
+    if (!g) {
+      b->groups.emplace_back();
+      g = &b->groups.back();
+      g->N = N;
+      g->riem = riem;
+    }
+    g->members.push_back(i);
+  }
+  cudaError_t e = cudaSuccess;
+  for (auto& g : b->groups) {
+    const int n = (int)g.members.size();
+    std::vector<int> offs(n + 1, 0);
+    const int epb = batch_elements_per_block(g.N);
+    g.host.resize(n);
+    for (int q = 0; q < n; ++q) {
+      sm_solver* s = b->solvers[g.members[q]];
+      BatchSolveDev& d = g.host[q];
+      memset(&d, 0, sizeof(d));
+      d.m = s->m;
+      d.sp = s->sp;
+      d.U[0] = s->U[0];
+      d.U[1] = s->U[1];
+      d.G = s->G;
+      d.Fs = s->Fs;
+      d.Fm = s->Fm;
+      d.t_d = s->t_d;
+      d.dt = b->dt[g.members[q]];
+      d.cur = s->cur;
+      offs[q + 1] = offs[q] + (int)((s->m.E + epb - 1) / epb);
+    }
+    g.total_el = offs.back();
+    if ((e = cudaMalloc((void**)&g.d_bs, sizeof(BatchSolveDev) * n)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&g.d_offs_el, sizeof(int) * (n + 1))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&g.d_offs_if, sizeof(int) * (n + 1))) != cudaSuccess ||
+        (e = cudaMemcpy(g.d_bs, g.host.data(), sizeof(BatchSolveDev) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(g.d_offs_el, offs.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = prepare_batch(g.N)) != cudaSuccess)
+      break;
+    TuneVal tv{8, 8, 0};
+    const bool known = tune_lookup({g.N, g.riem, size_class(group_elems(*b, g))}, &tv);
+    if ((e = upload_if_offsets(g, *b, known ? tv.tf : 8)) != cudaSuccess) break;
+    g.grid_if = std::min(g.total_if, b->sms * (known ? tv.grid_if_per_sm : 8));
+    g.grid_el = known && tv.grid_el_per_sm > 0 ? std::min(g.total_el, b->sms * tv.grid_el_per_sm) : g.total_el;
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return fail(e == cudaErrorMemoryAllocation ? SM_ERR_OOM : SM_ERR_CUDA, "batch set-up", e);
+  }
+  *out = b;
+  return SM_OK;
+}
+
+static int batch_autotune(sm_batch* b, void* stream, bool only_missing) {
+  if (!b) return fail(SM_ERR_ARG, "NULL batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  SM_CK(cudaEventCreate(&e0), "event");
+  SM_CK(cudaEventCreate(&e1), "event");
+  auto timed = [&](auto&& launch) -> float {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, st);
+      launch();
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < best) best = ms;     // first launch is the warm-up
+    }
+    return best;
+  };
+  cudaError_t err = cudaSuccess;
+  bool tuned = false;
+  for (auto& g : b->groups) {
+    const int n = (int)g.members.size();
+    TuneVal known;
+    if (only_missing && tune_lookup({g.N, g.riem, size_class(group_elems(*b, g))}, &known)) continue;
+    tuned = true;
+    // the stage parameters at each solve's current time (mode 1 with c = 0 writes only them)
+    if ((err = launch_batch_stage_params(g.N, g.d_bs, n, 0.0, 1, st)) != cudaSuccess) break;
+    int best_tf = g.tf, best_gif = g.grid_if;
+    float best_if = 1e30f;
+    for (int tf : {4, 8, 16}) {
+      if ((err = upload_if_offsets(g, *b, tf)) != cudaSuccess) break;
+      for (int per_sm : {2, 4, 8, 16, 0}) {
+        const int grid = per_sm ? std::min(g.total_if, b->sms * per_sm) : g.total_if;
+        const float ms = timed([&] { launch_batch_interface(g.N, g.riem, tf, g.d_bs, g.d_offs_if, n, grid, 0, st); });
+        if (ms < best_if) { best_if = ms; best_tf = tf; best_gif = grid; }
+      }
+    }
+    if (err != cudaSuccess) break;
+    if ((err = upload_if_offsets(g, *b, best_tf)) != cudaSuccess) break;
+    g.grid_if = best_gif;
+    // element kernel in first-stage mode: writes only G and the other state buffer
+    int best_gel = g.grid_el;
+    float best_el = 1e30f;
+    for (int per_sm : {2, 4, 6, 8, 12, 0}) {
+      const int grid = per_sm ? std::min(g.total_el, b->sms * per_sm) : g.total_el;
+      const float ms = timed([&] {
+        launch_batch_element(g.N, g.riem, ELEM_STAGE_FIRST, g.d_bs, g.d_offs_el, n, grid, 0, RK_A[0], RK_B[0], st);
+      });
+      if (ms < best_el) { best_el = ms; best_gel = grid; }
+    }
+    g.grid_el = best_gel;
+    const int gif_per_sm = best_gif >= g.total_if ? 0 : best_gif / b->sms;
+    const int gel_per_sm = best_gel >= g.total_el ? 0 : best_gel / b->sms;
+    tune_store({g.N, g.riem, size_class(group_elems(*b, g))}, {best_tf, gif_per_sm ? gif_per_sm : 1 << 20, gel_per_sm});
+    if ((err = cudaGetLastError()) != cudaSuccess) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(SM_ERR_CUDA, "autotune", err);
+  if (tuned && b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  SM_CK(cudaStreamSynchronize(st), "autotune sync");
+  return SM_OK;
+}
+
+extern "C" int sm_batch_autotune(sm_batch* b, void* stream) { return batch_autotune(b, stream, false); }
+
+// Tunes only the groups whose (N, Riemann solver, size class) has no remembered shape.
+int sm_batch_autotune_missing(sm_batch* b, void* stream) { return batch_autotune(b, stream, true); }
+
+extern "C" int sm_batch_step(sm_batch* b, int nsteps, void* stream) {
+  if (!b) return fail(SM_ERR_ARG, "NULL batch");
+  if (nsteps < 0) return fail(SM_ERR_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return SM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the device copy of every solve's buffer parity follows the solver (it may have been
+  // given a new state between batched steps)
+  for (auto& g : b->groups) {
+    bool changed = false;
+    for (size_t q = 0; q < g.members.size(); ++q)
+      if (g.host[q].cur != b->solvers[g.members[q]]->cur) { g.host[q].cur = b->solvers[g.members[q]]->cur; changed = true; }
+    if (changed)
+      SM_CK(cudaMemcpyAsync(g.d_bs, g.host.data(), sizeof(BatchSolveDev) * g.host.size(), cudaMemcpyHostToDevice, st),
+            "batch parity upload");
+  }
+  if (!b->graph) {
+    SM_CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = enqueue_batch_step(b, b->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return fail(SM_ERR_CUDA, "capture batch step", e); }
+    if (e2 != cudaSuccess) return fail(SM_ERR_CUDA, "end capture", e2);
+    e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { b->graph = nullptr; return fail(SM_ERR_CUDA, "instantiate batch graph", e); }
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    SM_CK(cudaGraphLaunch(b->graph, st), "batch graph launch");
+    for (size_t i = 0; i < b->solvers.size(); ++i) {
+      b->solvers[i]->cur ^= 1;
+      b->solvers[i]->t_host += b->dt[i];
+    }
+    for (auto& g : b->groups)
+      for (auto& h : g.host) h.cur ^= 1;
+  }
+  return SM_OK;
+}
+
+extern "C" int sm_batch_shapes(const sm_batch* b, int g, int* shape) {
+  if (!b || !shape || g < 0 || g >= (int)b->groups.size()) return fail(SM_ERR_ARG, "invalid group");
+  const auto& q = b->groups[g];
+  shape[0] = q.N;
+  shape[1] = q.tf;
+  shape[2] = q.grid_if;
+  shape[3] = q.grid_el;
+  return (int)b->groups.size();
+}
+
+extern "C" void sm_batch_destroy(sm_batch* b) { free_batch(b); }
+
+// ---------------------------------------------------------------------------------------
 // Right-hand side without any device allocation (sm_rhs_static).
 //
 // Some callers cannot call cudaMalloc: code that runs while a framework owns the device
@@ -627,6 +960,7 @@ int static_scratch_address(int dev, unsigned char** out) {
   if (!g_static_addr[dev]) {
     void* p = nullptr;
     SM_CK(cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress of the static scratch");
+    SM_CK(ensure_dhat_constants(), "derivative constants");
     for (int n = 1; n <= 7; ++n) {
       SM_CK(prepare_element_f64(n), "element kernel attributes");
       SM_CK(prepare_element_f32(n), "element kernel attributes");

@@ -30,6 +30,11 @@ cudaError_t launch_element_f64(int N, int riemann, int mode, const ElemArgs& a, 
 cudaError_t prepare_element_f32(int N);
 cudaError_t prepare_element_f64(int N);
 
+// constant-memory Dhat tables of the element kernels ([7][64], N = 1..7), one copy per unit
+cudaError_t upload_dhat_f32(const float* f, const double* d);
+cudaError_t upload_dhat_f64(const float* f, const double* d);
+cudaError_t upload_dhat_batch(const float* f, const double* d);
+
 // sm_iface.cu
 cudaError_t launch_interface(int N, int prec, int riemann, const MeshDev& m, const StageParams* sp, const void* U,
                              void* Fs, void* Fm, cudaStream_t st);
@@ -41,3 +46,30 @@ cudaError_t launch_totals(int N, int prec, const MeshDev& m, const void* U, doub
                           double* out5, cudaStream_t st);
 cudaError_t launch_face_sums(int N, int prec, const MeshDev& m, const void* F, double* partial, int nblk,
                              double* out5, cudaStream_t st);
+
+// ---- batched execution (sm_batch.cu): several FP32 solves of one degree N per launch ----
+// One entry per solve, in device memory.  cur is the state buffer at the start of the next
+// batched step; a stage k reads U[cur ^ (k & 1)] and writes the other buffer.
+struct BatchSolveDev {
+  MeshDev m;
+  StageParams* sp;
+  void* U[2];
+  void* G;
+  void* Fs;
+  void* Fm;
+  double* t_d;
+  double dt;
+  int cur;
+  int pad;
+};
+
+#define SM_MAX_BATCH 1024
+
+cudaError_t launch_batch_stage_params(int N, const BatchSolveDev* d_bs, int nsolve, double ck, int mode, cudaStream_t st);
+cudaError_t launch_batch_interface(int N, int riemann, int tf, const BatchSolveDev* d_bs, const int* d_offs, int nsolve,
+                                   int grid, int stage, cudaStream_t st);
+cudaError_t launch_batch_element(int N, int riemann, int mode, const BatchSolveDev* d_bs, const int* d_offs, int nsolve,
+                                 int grid, int stage, double rkA, double rkB, cudaStream_t st);
+cudaError_t launch_batch_flip(BatchSolveDev* d_bs, int nsolve, cudaStream_t st);
+cudaError_t prepare_batch(int N);
+int batch_elements_per_block(int N);

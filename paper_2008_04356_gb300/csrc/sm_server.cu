@@ -1,0 +1,287 @@
+// Serving loop (sm_server_*): continuous batching of many sliding-mesh solves on one GPU.
+//
+// A worker thread owns the device work.  Requests wait in arrival order; a request is
+// admitted when a slot is free and its device memory fits in the budget next to the
+// resident solves.  Every iteration advances all resident solves together by the same
+// number of RK steps (FP32 solves through one batch with shared launches, FP64 solves one
+// at a time), at most a few steps so that new arrivals join quickly, then retires the
+// finished ones and frees their memory.  Built on the library's own C-ABI.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/slidemesh.h"
+
+int sm_batch_autotune_missing(sm_batch* b, void* stream);   // sm_host.cu
+
+namespace {
+
+struct Job {
+  uint64_t id = 0;
+  sm_request req;
+  sm_result res;
+  sm_solver* solver = nullptr;
+  size_t bytes = 0;
+  int remaining = 0;
+  std::vector<unsigned char> state;
+};
+
+size_t request_bytes(const sm_mesh_desc& d) {
+  const size_t np = d.N + 1, nn = np * np * np, sb = d.precision == SM_FP64 ? 8 : 4;
+  const size_t E = (size_t)(d.nel_static[0] + d.nel_moving[0]) * d.nel_static[1] * d.nel_static[2];
+  const size_t faces = (size_t)d.nel_static[1] * d.nel_static[2];
+  return 3 * E * nn * 5 * sb + 2 * faces * 5 * np * np * sb + 32 * E + (64 << 10);
+}
+
+}  // namespace
+
+struct sm_server {
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::deque<Job*> queue;
+  std::vector<Job*> active;
+  std::unordered_map<uint64_t, Job*> jobs;
+  size_t budget = 0, used = 0, peak = 0;
+  int max_slots = 0;
+  int device = 0;
+  uint64_t next_id = 1;
+  std::atomic<bool> stop{false};
+  std::thread worker;
+  std::chrono::steady_clock::time_point t0;
+  sm_server_stats_out stats;
+  sm_batch* batch = nullptr;
+  bool batch_dirty = true;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  void run();
+  void finish(Job* j, int status, cudaStream_t st);
+};
+
+void sm_server::finish(Job* j, int status, cudaStream_t st) {
+  j->res.t_done = now();
+  if (status == SM_OK && j->solver) {
+    sm_diag_out d;
+    int rc = sm_diag(j->solver, &d, (void*)st);
+    if (rc == SM_OK || rc == SM_ERR_NONFINITE) {
+      for (int v = 0; v < 5; ++v) j->res.totals[v] = d.totals[v];
+      j->res.sim_time = d.t;
+      if (rc != SM_OK) status = rc;
+    } else {
+      status = rc;
+    }
+    if (status == SM_OK && j->req.keep_state) {
+      j->state.resize((size_t)sm_state_size(j->solver) * sm_scalar_bytes(j->solver));
+      double t = 0.0;
+      status = sm_get_state(j->solver, j->state.data(), 0, &t, (void*)st);
+      j->res.state = j->state.data();
+      j->res.state_bytes = (long long)j->state.size();
+    }
+  }
+  if (j->solver) sm_destroy(j->solver);
+  j->solver = nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  j->res.status = status;
+  used -= j->bytes;
+  if (status == SM_OK) {
+    stats.completed++;
+    stats.dof_updates += j->res.dof * 5LL * j->res.steps;
+  } else {
+    stats.failed++;
+  }
+  stats.running--;
+  done_cv.notify_all();
+}
+
+void sm_server::run() {
+  cudaSetDevice(device);
+  cudaStream_t st = nullptr;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  double busy_since = -1.0;
+  while (!stop.load()) {
+    std::vector<Job*> admit;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      while (!queue.empty() && (int)active.size() + (int)admit.size() < max_slots &&
+             used + queue.front()->bytes <= budget) {
+        Job* j = queue.front();
+        queue.pop_front();
+        used += j->bytes;
+        peak = std::max(peak, used);
+        stats.queued--;
+        stats.running++;
+        admit.push_back(j);
+      }
+      if (active.empty() && admit.empty()) {
+        if (busy_since >= 0.0) { stats.busy_seconds += now() - busy_since; busy_since = -1.0; }
+        cv.wait_for(lk, std::chrono::milliseconds(2));
+        continue;
+      }
+    }
+    if (busy_since < 0.0) busy_since = now();
+    for (Job* j : admit) {
+      j->res.t_admit = now();
+      int rc = sm_init_mesh(&j->req.desc, &j->solver);
+      if (rc == SM_OK) rc = sm_set_motion(j->solver, &j->req.motion);
+      if (rc == SM_OK) rc = sm_init_state(j->solver, (void*)st);
+      if (rc != SM_OK) { finish(j, rc, st); continue; }
+      active.push_back(j);
+      batch_dirty = true;
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stats.max_concurrent = std::max(stats.max_concurrent, (int)active.size());
+    }
+    if (active.empty()) continue;
+    if (batch_dirty) {
+      if (batch) sm_batch_destroy(batch);
+      batch = nullptr;
+      std::vector<sm_solver*> sol;
+      std::vector<double> dts;
+      for (Job* j : active)
+        if (j->req.desc.precision == SM_FP32) { sol.push_back(j->solver); dts.push_back(j->req.dt); }
+      if (!sol.empty()) {
+        int rc = sm_batch_create(sol.data(), dts.data(), (int)sol.size(), &batch);
+        if (rc == SM_OK) rc = sm_batch_autotune_missing(batch, (void*)st);
+        if (rc != SM_OK) {
+          if (batch) sm_batch_destroy(batch);
+          batch = nullptr;
+          for (Job* j : active) finish(j, rc, st);
+          active.clear();
+          continue;
+        }
+      }
+      batch_dirty = false;
+    }
+    int k = 8;
+    for (Job* j : active) k = std::min(k, j->remaining);
+    int rc = SM_OK;
+    if (k > 0) {
+      if (batch) rc = sm_batch_step(batch, k, (void*)st);
+      for (Job* j : active)
+        if (rc == SM_OK && j->req.desc.precision == SM_FP64) rc = sm_step(j->solver, j->req.dt, k, (void*)st);
+      if (rc == SM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SM_ERR_CUDA;
+      std::lock_guard<std::mutex> lk(mu);
+      stats.batched_steps += k;
+    }
+    std::vector<Job*> still;
+    for (Job* j : active) {
+      j->remaining -= k;
+      j->res.steps += k;
+      if (rc != SM_OK || j->remaining <= 0) {
+        finish(j, rc, st);
+        batch_dirty = true;
+      } else {
+        still.push_back(j);
+      }
+    }
+    active.swap(still);
+  }
+  if (batch) sm_batch_destroy(batch);
+  batch = nullptr;
+  for (Job* j : active) {
+    if (j->solver) sm_destroy(j->solver);
+    j->solver = nullptr;
+  }
+  active.clear();
+  if (st) cudaStreamDestroy(st);
+}
+
+extern "C" {
+
+int sm_server_create(size_t hbm_budget_bytes, int max_slots, sm_server** out) {
+  if (!out || max_slots < 1 || hbm_budget_bytes == 0) return SM_ERR_ARG;
+  sm_server* s = new (std::nothrow) sm_server();
+  if (!s) return SM_ERR_OOM;
+  s->budget = hbm_budget_bytes;
+  s->max_slots = std::min(max_slots, 1024);
+  memset(&s->stats, 0, sizeof(s->stats));
+  s->t0 = std::chrono::steady_clock::now();
+  if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return SM_ERR_CUDA; }
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return SM_OK;
+}
+
+int sm_submit(sm_server* s, const sm_request* req, uint64_t* ticket) {
+  if (!s || !req || !ticket) return SM_ERR_ARG;
+  const sm_mesh_desc& d = req->desc;
+  if (d.N < 1 || d.N > 7 || req->nsteps < 0 || !(req->dt > 0.0)) return SM_ERR_ARG;
+  for (int k = 0; k < 3; ++k)
+    if (d.nel_static[k] < 1 || d.nel_moving[k] < 1) return SM_ERR_ARG;
+  Job* j = new (std::nothrow) Job();
+  if (!j) return SM_ERR_OOM;
+  j->req = *req;
+  memset(&j->res, 0, sizeof(j->res));
+  j->res.status = SM_PENDING;
+  j->bytes = request_bytes(d);
+  j->remaining = req->nsteps;
+  j->res.dof = (long long)(d.nel_static[0] + d.nel_moving[0]) * d.nel_static[1] * d.nel_static[2] *
+               (d.N + 1) * (d.N + 1) * (d.N + 1);
+  if (j->bytes > s->budget) { delete j; return SM_ERR_OOM; }
+  std::lock_guard<std::mutex> lk(s->mu);
+  j->id = s->next_id++;
+  j->res.t_submit = s->now();
+  s->jobs[j->id] = j;
+  s->queue.push_back(j);
+  s->stats.submitted++;
+  s->stats.queued++;
+  *ticket = j->id;
+  s->cv.notify_one();
+  return SM_OK;
+}
+
+int sm_poll(sm_server* s, uint64_t ticket, sm_result* out) {
+  if (!s || !out) return SM_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return SM_ERR_ARG;
+  *out = it->second->res;
+  return out->status;
+}
+
+int sm_server_wait(sm_server* s, double timeout_s) {
+  if (!s) return SM_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  while (s->stats.completed + s->stats.failed < s->stats.submitted) {
+    if (s->done_cv.wait_until(lk, deadline) == std::cv_status::timeout &&
+        s->stats.completed + s->stats.failed < s->stats.submitted)
+      return SM_ERR_TIMEOUT;
+  }
+  return SM_OK;
+}
+
+int sm_server_stats(sm_server* s, sm_server_stats_out* out) {
+  if (!s || !out) return SM_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  out->bytes_in_use = s->used;
+  out->peak_bytes = s->peak;
+  return SM_OK;
+}
+
+void sm_server_destroy(sm_server* s) {
+  if (!s) return;
+  s->stop.store(true);
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& kv : s->jobs) {
+    if (kv.second->solver) sm_destroy(kv.second->solver);
+    delete kv.second;
+  }
+  delete s;
+}
+
+}  // extern "C"

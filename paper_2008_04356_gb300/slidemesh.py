@@ -38,6 +38,24 @@ class SmDiag(C.Structure):
                 ("iface_sum_moving", C.c_double * 5)]
 
 
+class SmRequest(C.Structure):
+    _fields_ = [("desc", SmMeshDesc), ("motion", SmMotion), ("dt", C.c_double), ("nsteps", C.c_int),
+                ("keep_state", C.c_int)]
+
+
+class SmResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("sim_time", C.c_double), ("dof", C.c_longlong), ("steps", C.c_int), ("totals", C.c_double * 5),
+                ("state", C.c_void_p), ("state_bytes", C.c_longlong)]
+
+
+class SmServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("running", C.c_longlong), ("queued", C.c_longlong), ("batched_steps", C.c_longlong),
+                ("dof_updates", C.c_longlong), ("busy_seconds", C.c_double), ("bytes_in_use", C.c_size_t),
+                ("peak_bytes", C.c_size_t), ("max_concurrent", C.c_int)]
+
+
 _vp = C.c_void_p
 _SIGS = {
     "sm_init_mesh": (C.c_int, [C.POINTER(SmMeshDesc), C.POINTER(_vp)]),
@@ -57,6 +75,17 @@ _SIGS = {
     "sm_rhs_static": (C.c_int, [C.POINTER(SmMeshDesc), C.POINTER(SmMotion), C.c_double, _vp, _vp, _vp]),
     "sm_map": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, _vp, _vp, _vp, _vp]),
     "sm_mortar_matrices": (C.c_int, [C.c_int, C.c_double, _vp, _vp]),
+    "sm_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(C.c_double), C.c_int, C.POINTER(_vp)]),
+    "sm_batch_autotune": (C.c_int, [_vp, _vp]),
+    "sm_batch_step": (C.c_int, [_vp, C.c_int, _vp]),
+    "sm_batch_shapes": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
+    "sm_batch_destroy": (None, [_vp]),
+    "sm_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(_vp)]),
+    "sm_submit": (C.c_int, [_vp, C.POINTER(SmRequest), C.POINTER(C.c_uint64)]),
+    "sm_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(SmResult)]),
+    "sm_server_wait": (C.c_int, [_vp, C.c_double]),
+    "sm_server_stats": (C.c_int, [_vp, C.POINTER(SmServerStats)]),
+    "sm_server_destroy": (None, [_vp]),
     "sm_status_string": (C.c_char_p, [C.c_int]),
     "sm_last_error": (C.c_char_p, []),
 }
@@ -247,3 +276,92 @@ class Solver:
         if st not in (SM_OK, -4):
             check(st, "sm_diag")
         return out
+
+
+class Batch:
+    """Several FP32 solvers advanced by shared launches (sm_batch_*)."""
+
+    def __init__(self, solvers, dts):
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        dt = (C.c_double * len(self.solvers))(*[float(x) for x in dts])
+        h = C.c_void_p()
+        check(lib().sm_batch_create(arr, dt, len(self.solvers), C.byref(h)), "sm_batch_create")
+        self.h = h
+
+    def autotune(self, stream=None):
+        check(lib().sm_batch_autotune(self.h, _stream(stream)), "sm_batch_autotune")
+
+    def step(self, nsteps, stream=None):
+        check(lib().sm_batch_step(self.h, int(nsteps), _stream(stream)), "sm_batch_step")
+
+    def shapes(self):
+        out, g = [], 0
+        while True:
+            sh = (C.c_int * 4)()
+            n = lib().sm_batch_shapes(self.h, g, sh)
+            if n < 0:
+                break
+            out.append({"N": sh[0], "tile_faces": sh[1], "grid_interface": sh[2], "grid_element": sh[3]})
+            g += 1
+            if g >= n:
+                break
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (sm_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int):
+        h = C.c_void_p()
+        check(lib().sm_server_create(C.c_size_t(int(hbm_budget_bytes)), int(max_slots), C.byref(h)),
+              "sm_server_create")
+        self.h = h
+
+    def submit(self, problem: synth.Problem, dt: float, nsteps: int, keep_state: bool = False) -> int:
+        req = SmRequest()
+        req.desc = mesh_desc(problem)
+        req.motion = SmMotion(float(problem.v), 0.0, float(problem.delta0))
+        req.dt, req.nsteps, req.keep_state = float(dt), int(nsteps), int(keep_state)
+        t = C.c_uint64()
+        check(lib().sm_submit(self.h, C.byref(req), C.byref(t)), "sm_submit")
+        return t.value
+
+    def poll(self, ticket: int) -> dict:
+        r = SmResult()
+        st = lib().sm_poll(self.h, C.c_uint64(ticket), C.byref(r))
+        out = {"status": st, "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done,
+               "sim_time": r.sim_time, "dof": r.dof, "steps": r.steps, "totals": list(r.totals)}
+        if r.state and r.state_bytes:
+            out["state"] = bytes(C.string_at(r.state, r.state_bytes))
+        return out
+
+    def wait(self, timeout_s: float = 600.0):
+        check(lib().sm_server_wait(self.h, float(timeout_s)), "sm_server_wait")
+
+    def stats(self) -> dict:
+        s = SmServerStats()
+        check(lib().sm_server_stats(self.h, C.byref(s)), "sm_server_stats")
+        return {k: getattr(s, k) for k, _ in SmServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
