@@ -18,7 +18,11 @@
 
 template <int N> struct IfCfg {
   static constexpr int NP = N + 1, NP2 = NP * NP, NN = NP * NP * NP;
+#ifdef SM_IF_TF_OVERRIDE
+  static constexpr int TF = SM_IF_TF_OVERRIDE;
+#else
   static constexpr int TF = N == 1 ? 32 : (N == 2 ? 16 : 8);   // default tile: static faces per CTA
+#endif
   static constexpr int THREADS = 256;
   template <typename T, int TFV = TF> static constexpr size_t smem_bytes() {
     return sizeof(T) * (size_t)(8 * NP2 + 2 * (TFV + 1) * 5 * NP2 + (2 * TFV + 1) * 5 * NP2);
@@ -50,20 +54,40 @@ __device__ __forceinline__ void interface_tile(const MeshDev& m, const StagePara
     const int k = w / NP2, r = w - k * NP2;
     sMat[w] = Prec<T>::mat(sp, k)[r];
   }
-  // traces: static faces i0+r (r = 0..TFe) and moving faces i0-n-1+r (r = 0..TFe)
-  const int ntr = (TFe + 1) * 5 * NP2;
-  for (int w = tid; w < 2 * ntr; w += THREADS) {
-    const int side = w >= ntr;
-    const int ww = w - side * ntr;
-    const int r = ww / (5 * NP2);
-    const int rem = ww - r * 5 * NP2;
-    const int v = rem / NP2, ab = rem - v * NP2;
+  // traces: static faces i0+r (r = 0..TFe) and moving faces i0-n-1+r (r = 0..TFe); the
+  // trace of a face is its element's xi^3 = +1 (static) or -1 (moving) node layer, (N+1)^2
+  // contiguous values per variable
+  __shared__ long long s_base[2][TF + 1];
+  if (tid < 2 * (TFe + 1)) {
+    const int side = tid / (TFe + 1), r = tid - side * (TFe + 1);
     int f = side ? i0 - nmod - 1 + r : i0 + r;
     f %= ny;
     if (f < 0) f += ny;
-    const long long e = encode_elem(m, side, side ? 0 : m.nxs - 1, f, iz);
-    const T val = U[(e * 5 + v) * NN + (side ? 0 : NP2 * N) + ab];
-    (side ? sTm : sTs)[ww] = val;
+    s_base[side][r] = encode_elem(m, side, side ? 0 : m.nxs - 1, f, iz) * 5 * NN + (side ? 0 : NP2 * N);
+  }
+  __syncthreads();
+  const int ntr = (TFe + 1) * 5 * NP2;
+  if constexpr (sizeof(T) == 4 && NP2 % 4 == 0) {
+    // 16-byte loads: the layer offsets and (N+1)^3 are multiples of 4 values
+    constexpr int Q4 = NP2 / 4;
+    const int nv = 2 * (TFe + 1) * 5 * Q4;
+    for (int w = tid; w < nv; w += THREADS) {
+      const int q4 = w % Q4;
+      const int rest = w / Q4;
+      const int v = rest % 5;
+      const int sr = rest / 5;                   // side * (TFe+1) + r
+      const int side = sr >= TFe + 1, r = sr - side * (TFe + 1);
+      const float4 val = *reinterpret_cast<const float4*>(U + s_base[side][r] + v * NN + 4 * q4);
+      *reinterpret_cast<float4*>((side ? sTm : sTs) + (r * 5 + v) * NP2 + 4 * q4) = val;
+    }
+  } else {
+    for (int w = tid; w < 2 * ntr; w += THREADS) {
+      const int side = w >= ntr;
+      const int ww = w - side * ntr;
+      const int r = ww / (5 * NP2);
+      const int rem = ww - r * 5 * NP2;
+      (side ? sTm : sTs)[ww] = U[s_base[side][r] + rem / NP2 * NN + rem % NP2];
+    }
   }
   __syncthreads();
 
