@@ -387,6 +387,33 @@ void orc_riemann(int kind, const double* UL, const double* UR, const double* n, 
   for (int k = 0; k < 5; ++k) F[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * D[k];
 }
 
+/* Viscous fluxes (Sec. 2, Eqs. fluxes_written_out, stress_tensor, heat_flux): columns
+ * i = x, y, z of F^v = (0, tau_1i, tau_2i, tau_3i, tau_ij v_j - q_i), Stokes' hypothesis
+ * lambda = -2/3 mu, q = -k grad T with k = mu c_p / Pr, c_p = gamma R / (gamma - 1),
+ * T = p / (rho R).  grad15[d*5 + c] is the derivative along x_d of primitive c of
+ * (rho, v1, v2, v3, p); Fv15[i*5 + c] is component c of column i. */
+void orc_viscous_flux(const double* U, const double* g, double mu, double Pr, double Rgas, double gamma,
+                      double* Fv) {
+  double rho = U[0], v[3] = {U[1] / rho, U[2] / rho, U[3] / rho};
+  double p = (gamma - 1.0) * (U[4] - 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+  double T = p / (rho * Rgas);
+  double k = mu * gamma * Rgas / ((gamma - 1.0) * Pr);
+  double dv[3][3], dT[3];            /* dv[a][d] = d v_a / d x_d */
+  for (int d = 0; d < 3; ++d) {
+    for (int a = 0; a < 3; ++a) dv[a][d] = g[d * 5 + 1 + a];
+    /* grad T = (grad p - T R grad rho) / (rho R) */
+    dT[d] = (g[d * 5 + 4] - T * Rgas * g[d * 5 + 0]) / (rho * Rgas);
+  }
+  double div = dv[0][0] + dv[1][1] + dv[2][2];
+  for (int i = 0; i < 3; ++i) {
+    double tau[3];
+    for (int a = 0; a < 3; ++a) tau[a] = mu * (dv[a][i] + dv[i][a]) + (a == i ? -2.0 / 3.0 * mu * div : 0.0);
+    Fv[i * 5 + 0] = 0.0;
+    for (int a = 0; a < 3; ++a) Fv[i * 5 + 1 + a] = tau[a];
+    Fv[i * 5 + 4] = tau[0] * v[0] + tau[1] * v[1] + tau[2] * v[2] + k * dT[i];
+  }
+}
+
 /* Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients, the scheme
  * Sec. 3.1 names for time integration (values are not printed in the paper):
  *   G = A_k G + dt R(U, t + c_k dt);  U = U + B_k G. */
@@ -429,6 +456,7 @@ struct Oracle {
   double hy, hz, hx[2];
   std::vector<double> x, w, D, Dhat;
   double A[5], B[5], c[5];
+  bool ns;   /* Navier-Stokes with BR1 lifting */
 };
 
 struct ElemId { int blk, ix, iy, iz; };
@@ -472,6 +500,14 @@ void prim_to_cons(const double* P, double gamma, double* U) {
   U[4] = P[4] / (gamma - 1.0) + 0.5 * P[0] * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
 }
 
+void cons_to_prim(const double* U, double gamma, double* Q) {
+  Q[0] = U[0];
+  Q[1] = U[1] / U[0];
+  Q[2] = U[2] / U[0];
+  Q[3] = U[3] / U[0];
+  Q[4] = (gamma - 1.0) * (U[4] - 0.5 * U[0] * (Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3]));
+}
+
 /* The flows used as initial data and as Dirichlet boundary states.
  *  0: constant primitive state fpar[0..4].
  *  1: entropy wave rho = fpar0 + fpar1 sin(2 pi k.(x - u t)), k = fpar2..4, u = fpar5..7,
@@ -501,10 +537,18 @@ void flow_state(const orc_problem& p, const double* X, double t, int boundary, d
           }
       break;
     }
-    default: {
+    case 3: {
       double xs = X[0] - f[4] * t;
       P[0] = f[0] + xs * (f[1] + xs * (f[2] + xs * f[3]));
       P[1] = f[4]; P[2] = f[5]; P[3] = f[6]; P[4] = f[7];
+      break;
+    }
+    default: {
+      /* 4: rho = fpar0, p = fpar1, velocity (0, 0, w(x)) with w = fpar2 + fpar3 x + fpar4 x^2 */
+      P[0] = f[0];
+      P[1] = 0.0; P[2] = 0.0;
+      P[3] = f[2] + X[0] * (f[3] + X[0] * f[4]);
+      P[4] = f[1];
       break;
     }
   }
@@ -575,10 +619,29 @@ void interface_trace(const Oracle& o, const double* U, int blk, int ipar, int ip
         tr[(v * o.np + q) * o.np + p] = U[(e * 5 + v) * o.nn + face_node_to_vol(o, 2, side, p, q)];
 }
 
+/* Trace of the lifted gradients on the interface: grad[((e*3 + d)*5 + c)*nn + node],
+ * tr[(k*np + q)*np + p] with k = 5 d + c (15 components). */
+void interface_grad_trace(const Oracle& o, const double* grad, int blk, int ipar, int iperp, double* tr) {
+  int ix = blk == 0 ? o.p.nel_s[0] - 1 : 0;
+  int side = blk == 0 ? 1 : 0;
+  long long e = elem_index(o, blk, ix, ipar, iperp);
+  for (int k = 0; k < 15; ++k)
+    for (int q = 0; q < o.np; ++q)
+      for (int p = 0; p < o.np; ++p)
+        tr[(k * o.np + q) * o.np + p] = grad[(e * 15 + k) * o.nn + face_node_to_vol(o, 2, side, p, q)];
+}
+
+/* Normal viscous flux (F^v . e_axis) at a point from state U and the 15 gradients. */
+void viscous_normal(const Oracle& o, const double* U, const double* g15, int axis, double* Fn) {
+  double Fv[15];
+  orc_viscous_flux(U, g15, o.p.mu, o.p.Pr, o.p.Rgas, o.p.gamma, Fv);
+  for (int c = 0; c < 5; ++c) Fn[c] = Fv[axis * 5 + c];
+}
+
 /* Step 3: L2 projection of a face trace onto a mortar, along the sliding direction only
  * (the mortar and face nodes line up along the perpendicular lines, Sec. 3.2). */
-void project_to_mortar(const Oracle& o, const double* P, const double* tr, double* Q) {
-  for (int v = 0; v < 5; ++v)
+void project_to_mortar(const Oracle& o, const double* P, const double* tr, double* Q, int ncomp = 5) {
+  for (int v = 0; v < ncomp; ++v)
     for (int q = 0; q < o.np; ++q)
       for (int j = 0; j < o.np; ++j) {
         double acc = 0.0;
@@ -590,24 +653,61 @@ void project_to_mortar(const Oracle& o, const double* P, const double* tr, doubl
 /* Steps 2-4 for one mortar (ipar, iperp, isub) (mortar index triple of Sec. 4.3):
  * primary (static) and replica (moving) states on the mortar, then the Riemann flux with
  * the static face's outward normal (+x), scaled by the static face's surface element. */
-void mortar_flux(const Oracle& o, const Interface& I, const double* U, int ipar, int iperp, int isub,
-                 double* Fm) {
+void mortar_flux(const Oracle& o, const Interface& I, const double* U, const double* grad, int ipar, int iperp,
+                 int isub, double* Fm) {
   int nq = o.np * o.np;
-  std::vector<double> tr(5 * nq), QL(5 * nq), QR(5 * nq);
-  interface_trace(o, U, 0, ipar, iperp, tr.data());
-  project_to_mortar(o, isub == 0 ? I.Ps_lo.data() : I.Ps_hi.data(), tr.data(), QL.data());
-  int it = wrap((long long)ipar - I.n + isub - 1, o.ny);          /* Eq. indices */
-  interface_trace(o, U, 1, it, iperp, tr.data());
+  std::vector<double> tr(15 * nq), QL(5 * nq), QR(5 * nq), GL(15 * nq), GR(15 * nq);
+  const double* Ps = isub == 0 ? I.Ps_lo.data() : I.Ps_hi.data();
   /* the static lower mortar is the upper part of the moving face, and vice versa */
-  project_to_mortar(o, isub == 0 ? I.Pm_hi.data() : I.Pm_lo.data(), tr.data(), QR.data());
+  const double* Pm = isub == 0 ? I.Pm_hi.data() : I.Pm_lo.data();
+  int it = wrap((long long)ipar - I.n + isub - 1, o.ny);          /* Eq. indices */
+  interface_trace(o, U, 0, ipar, iperp, tr.data());
+  project_to_mortar(o, Ps, tr.data(), QL.data());
+  interface_trace(o, U, 1, it, iperp, tr.data());
+  project_to_mortar(o, Pm, tr.data(), QR.data());
+  if (grad) {   /* gradients projected onto the mortars like the solution (Sec. 3.2) */
+    interface_grad_trace(o, grad, 0, ipar, iperp, tr.data());
+    project_to_mortar(o, Ps, tr.data(), GL.data(), 15);
+    interface_grad_trace(o, grad, 1, it, iperp, tr.data());
+    project_to_mortar(o, Pm, tr.data(), GR.data(), 15);
+  }
   double n[3] = {1.0, 0.0, 0.0}, sJ = metric(o, 0, 2);
   for (int q = 0; q < o.np; ++q)
     for (int j = 0; j < o.np; ++j) {
       double ul[5], ur[5], f[5];
       for (int v = 0; v < 5; ++v) { ul[v] = QL[(v * o.np + q) * o.np + j]; ur[v] = QR[(v * o.np + q) * o.np + j]; }
       orc_riemann(o.p.riemann, ul, ur, n, 0.0, o.p.gamma, f);
+      if (grad) {   /* BR1: mean of both sides' viscous fluxes */
+        double gl[15], gr[15], fl[5], fr[5];
+        for (int k = 0; k < 15; ++k) { gl[k] = GL[(k * o.np + q) * o.np + j]; gr[k] = GR[(k * o.np + q) * o.np + j]; }
+        viscous_normal(o, ul, gl, 0, fl);
+        viscous_normal(o, ur, gr, 0, fr);
+        for (int v = 0; v < 5; ++v) f[v] -= 0.5 * (fl[v] + fr[v]);
+      }
       for (int v = 0; v < 5; ++v) Fm[(v * o.np + q) * o.np + j] = f[v] * sJ;
     }
+}
+
+/* BR1 lifting on one mortar: mean of both sides' projected primitive traces, times the
+ * static face's surface element (its outward normal is +x). */
+void mortar_lift(const Oracle& o, const Interface& I, const double* U, int ipar, int iperp, int isub, double* Lm) {
+  int nq = o.np * o.np;
+  std::vector<double> tr(5 * nq), pr(5 * nq), QL(5 * nq), QR(5 * nq);
+  auto prim_trace = [&](int blk, int i) {
+    interface_trace(o, U, blk, i, iperp, tr.data());
+    for (int ab = 0; ab < nq; ++ab) {
+      double u[5], q[5];
+      for (int v = 0; v < 5; ++v) u[v] = tr[v * nq + ab];
+      cons_to_prim(u, o.p.gamma, q);
+      for (int v = 0; v < 5; ++v) pr[v * nq + ab] = q[v];
+    }
+  };
+  prim_trace(0, ipar);
+  project_to_mortar(o, isub == 0 ? I.Ps_lo.data() : I.Ps_hi.data(), pr.data(), QL.data());
+  prim_trace(1, wrap((long long)ipar - I.n + isub - 1, o.ny));
+  project_to_mortar(o, isub == 0 ? I.Pm_hi.data() : I.Pm_lo.data(), pr.data(), QR.data());
+  double sJ = metric(o, 0, 2);
+  for (int k = 0; k < 5 * nq; ++k) Lm[k] = sJ * 0.5 * (QL[k] + QR[k]);
 }
 
 /* Step 5: projection of the mortar fluxes back onto a face, F = B_lo F_lo + B_hi F_hi. */
@@ -624,22 +724,24 @@ void project_to_face(const Oracle& o, const double* B_lo, const double* F_lo, co
 }
 
 /* Outward flux (times surface element) on static face (ipar, iperp). */
-void static_face_flux(const Oracle& o, const Interface& I, const double* U, int ipar, int iperp, double* F) {
+void static_face_flux(const Oracle& o, const Interface& I, const double* U, const double* grad, int ipar, int iperp,
+                      double* F) {
   int nq = o.np * o.np;
   std::vector<double> F0(5 * nq), F1(5 * nq);
-  mortar_flux(o, I, U, ipar, iperp, 0, F0.data());
-  mortar_flux(o, I, U, ipar, iperp, 1, F1.data());
+  mortar_flux(o, I, U, grad, ipar, iperp, 0, F0.data());
+  mortar_flux(o, I, U, grad, ipar, iperp, 1, F1.data());
   project_to_face(o, I.Bs_lo.data(), F0.data(), I.Bs_hi.data(), F1.data(), 1.0, F);
 }
 
 /* Outward flux on moving face (it, iperp): its lower part (xi~ <= sigma~) is mortar
  * (it + n, 1), its upper part mortar (it + n + 1, 0); the moving side's outward normal
  * is -x, hence the sign. */
-void moving_face_flux(const Oracle& o, const Interface& I, const double* U, int it, int iperp, double* F) {
+void moving_face_flux(const Oracle& o, const Interface& I, const double* U, const double* grad, int it, int iperp,
+                      double* F) {
   int nq = o.np * o.np;
   std::vector<double> Flo(5 * nq), Fhi(5 * nq);
-  mortar_flux(o, I, U, wrap((long long)it + I.n, o.ny), iperp, 1, Flo.data());
-  mortar_flux(o, I, U, wrap((long long)it + I.n + 1, o.ny), iperp, 0, Fhi.data());
+  mortar_flux(o, I, U, grad, wrap((long long)it + I.n, o.ny), iperp, 1, Flo.data());
+  mortar_flux(o, I, U, grad, wrap((long long)it + I.n + 1, o.ny), iperp, 0, Fhi.data());
   project_to_face(o, I.Bm_lo.data(), Flo.data(), I.Bm_hi.data(), Fhi.data(), -1.0, F);
 }
 
@@ -649,8 +751,9 @@ void moving_face_flux(const Oracle& o, const Interface& I, const double* U, int 
  * Conforming faces use the flux in canonical orientation (minus element left, normal
  * +axis) so that both neighbours see the same number; Dirichlet faces use the exact flow
  * state outside (weak boundary condition); interface faces come from the mortars. */
-void face_flux_out(const Oracle& o, const Interface* I, const double* U, double t, long long e, int d, int side,
-                   const std::vector<double>* Fsl_static, const std::vector<double>* Fsl_moving, double* Fout) {
+void face_flux_out(const Oracle& o, const Interface* I, const double* U, const double* grad, double t, long long e,
+                   int d, int side, const std::vector<double>* Fsl_static, const std::vector<double>* Fsl_moving,
+                   double* Fout) {
   ElemId id = elem_id(o, e);
   int np = o.np, nq = np * np;
   int nx = id.blk == 0 ? o.p.nel_s[0] : o.p.nel_m[0];
@@ -676,8 +779,8 @@ void face_flux_out(const Oracle& o, const Interface* I, const double* U, double 
       const double* F = src->data() + ((long long)id.iz * o.ny + id.iy) * 5 * nq;
       for (int v = 0; v < 5; ++v)
         for (int ab = 0; ab < nq; ++ab) Fout[v * nq + ab] = F[v * nq + ab];
-    } else if (id.blk == 0) static_face_flux(o, *I, U, id.iy, id.iz, Fout);
-    else moving_face_flux(o, *I, U, id.iy, id.iz, Fout);
+    } else if (id.blk == 0) static_face_flux(o, *I, U, grad, id.iy, id.iz, Fout);
+    else moving_face_flux(o, *I, U, grad, id.iy, id.iz, Fout);
     return;
   }
   for (int b = 0; b < np; ++b)
@@ -696,6 +799,18 @@ void face_flux_out(const Oracle& o, const Interface* I, const double* U, double 
       }
       if (side == 1) orc_riemann(o.p.riemann, uin, uout, n, vgn, o.p.gamma, f);
       else orc_riemann(o.p.riemann, uout, uin, n, vgn, o.p.gamma, f);
+      if (grad) {
+        /* BR1 viscous face flux: mean of both sides' viscous fluxes; at a weak Dirichlet
+         * face the exterior flux takes the exterior state with the interior gradients */
+        double gin[15], gout[15], fi[5], fo[5];
+        for (int k = 0; k < 15; ++k) {
+          gin[k] = grad[(e * 15 + k) * o.nn + vn];
+          gout[k] = kind == 1 ? gin[k] : grad[(nb * 15 + k) * o.nn + face_node_to_vol(o, d, 1 - side, a, b)];
+        }
+        viscous_normal(o, uin, gin, phys_axis(d), fi);
+        viscous_normal(o, uout, gout, phys_axis(d), fo);
+        for (int v = 0; v < 5; ++v) f[v] -= 0.5 * (fi[v] + fo[v]);
+      }
       double sg = side == 1 ? 1.0 : -1.0;
       for (int v = 0; v < 5; ++v) Fout[v * nq + a + np * b] = sg * sJ * f[v];
     }
@@ -705,7 +820,7 @@ void face_flux_out(const Oracle& o, const Interface* I, const double* U, double 
  *   J dU/dt = - [ sum_l Dhat_il F~1_ljk + sum_l Dhat_jl F~2_ilk + sum_l Dhat_kl F~3_ijl ]
  *             - sum_faces ell(+-1)/w * (F* . N) sJ ,
  * with Dhat_il = -(w_l / w_i) D_li and contravariant fluxes F~d = |Ja^d| (F - v^g U) . e. */
-void element_residual(const Oracle& o, const Interface* I, const double* U, double t, long long e,
+void element_residual(const Oracle& o, const Interface* I, const double* U, const double* grad, double t, long long e,
                       const std::vector<double>* Fs, const std::vector<double>* Fm, double* Ut_e) {
   ElemId id = elem_id(o, e);
   int np = o.np, nn = o.nn, nq = np * np;
@@ -713,9 +828,17 @@ void element_residual(const Oracle& o, const Interface* I, const double* U, doub
   for (int node = 0; node < nn; ++node) {
     double u[5], f[5], n[3];
     for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * nn + node];
+    double Fv[15];
+    if (grad) {
+      double g15[15];
+      for (int k = 0; k < 15; ++k) g15[k] = grad[(e * 15 + k) * nn + node];
+      orc_viscous_flux(u, g15, o.p.mu, o.p.Pr, o.p.Rgas, o.p.gamma, Fv);
+    }
     for (int d = 0; d < 3; ++d) {
       unit_normal(d, n);
       orc_euler_flux(u, n, grid_vel(o, id.blk, d), o.p.gamma, f);
+      if (grad)   /* total flux F^c - F^v (Sec. 2, Eq. navier_stokes) */
+        for (int v = 0; v < 5; ++v) f[v] -= Fv[phys_axis(d) * 5 + v];
       for (int v = 0; v < 5; ++v) Ft[(d * 5 + v) * nn + node] = metric(o, id.blk, d) * f[v];
     }
   }
@@ -735,7 +858,7 @@ void element_residual(const Oracle& o, const Interface* I, const double* U, doub
   std::vector<double> Fout(5 * nq);
   for (int d = 0; d < 3; ++d)
     for (int side = 0; side < 2; ++side) {
-      face_flux_out(o, I, U, t, e, d, side, Fs, Fm, Fout.data());
+      face_flux_out(o, I, U, grad, t, e, d, side, Fs, Fm, Fout.data());
       double wend = o.w[side == 0 ? 0 : o.N];
       for (int v = 0; v < 5; ++v)
         for (int b = 0; b < np; ++b)
@@ -747,7 +870,7 @@ void element_residual(const Oracle& o, const Interface* I, const double* U, doub
 
 /* All interface face fluxes, via the mortar arrays of Sec. 4.2: first every mortar flux
  * (indexed by (i_par, i_perp, i_sub)), then the projections onto both sides' faces. */
-void all_interface_fluxes(const Oracle& o, const Interface& I, const double* U,
+void all_interface_fluxes(const Oracle& o, const Interface& I, const double* U, const double* grad,
                           std::vector<double>& Fs, std::vector<double>& Fm) {
   int nq = o.np * o.np;
   long long nf = (long long)o.ny * o.nz;
@@ -756,7 +879,7 @@ void all_interface_fluxes(const Oracle& o, const Interface& I, const double* U,
   for (long long f = 0; f < nf; ++f) {
     int ipar = (int)(f % o.ny), iperp = (int)(f / o.ny);
     for (int isub = 0; isub < 2; ++isub)
-      mortar_flux(o, I, U, ipar, iperp, isub, Fsm.data() + (f * 2 + isub) * 5 * nq);
+      mortar_flux(o, I, U, grad, ipar, iperp, isub, Fsm.data() + (f * 2 + isub) * 5 * nq);
   }
   Fs.assign(nf * 5 * nq, 0.0);
   Fm.assign(nf * 5 * nq, 0.0);
@@ -772,6 +895,107 @@ void all_interface_fluxes(const Oracle& o, const Interface& I, const double* U,
   }
 }
 
+
+/* BR1 lifting ("first method" of Bassi and Rebay, Sec. 3.1): the gradient of each primitive
+ * variable (rho, v1, v2, v3, p) along each physical axis by the same weak DG operator as the
+ * flux divergence, applied to the "flux" Q e_axis with face value the mean of both sides'
+ * traces; on the sliding interface the mean is taken on the mortars between the projected
+ * primitive traces and projected back (Sec. 3.2).  grad[((e*3 + a)*5 + c)*nn + node]. */
+void compute_lifting(const Oracle& o, const Interface& I, const double* U, double t, double* grad) {
+  int np = o.np, nn = o.nn, nq = np * np;
+  long long nf = (long long)o.ny * o.nz;
+  std::vector<double> Ls, Lm;
+  if (!o.p.interface_conforming) {
+    std::vector<double> Lsm(nf * 2 * 5 * nq);
+    for (long long f = 0; f < nf; ++f)
+      for (int isub = 0; isub < 2; ++isub)
+        mortar_lift(o, I, U, (int)(f % o.ny), (int)(f / o.ny), isub, Lsm.data() + (f * 2 + isub) * 5 * nq);
+    Ls.assign(nf * 5 * nq, 0.0);
+    Lm.assign(nf * 5 * nq, 0.0);
+    for (long long f = 0; f < nf; ++f) {
+      int ipar = (int)(f % o.ny);
+      long long row = (f / o.ny) * o.ny;
+      project_to_face(o, I.Bs_lo.data(), Lsm.data() + (f * 2 + 0) * 5 * nq, I.Bs_hi.data(),
+                      Lsm.data() + (f * 2 + 1) * 5 * nq, 1.0, Ls.data() + f * 5 * nq);
+      long long flo = row + wrap((long long)ipar + I.n, o.ny), fhi = row + wrap((long long)ipar + I.n + 1, o.ny);
+      project_to_face(o, I.Bm_lo.data(), Lsm.data() + (flo * 2 + 1) * 5 * nq, I.Bm_hi.data(),
+                      Lsm.data() + (fhi * 2 + 0) * 5 * nq, -1.0, Lm.data() + f * 5 * nq);
+    }
+  }
+  #pragma omp parallel for schedule(static)
+  for (long long e = 0; e < o.E; ++e) {
+    ElemId id = elem_id(o, e);
+    std::vector<double> Q(5 * nn);
+    for (int node = 0; node < nn; ++node) {
+      double u[5], q[5];
+      for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * nn + node];
+      cons_to_prim(u, o.p.gamma, q);
+      for (int v = 0; v < 5; ++v) Q[v * nn + node] = q[v];
+    }
+    double invJ = 1.0 / jacobian(o, id.blk);
+    int nx = id.blk == 0 ? o.p.nel_s[0] : o.p.nel_m[0];
+    for (int d = 0; d < 3; ++d) {
+      int a = phys_axis(d);
+      double sJ = metric(o, id.blk, d);
+      double* g = grad + (e * 15 + a * 5) * nn;
+      /* volume: sum_l Dhat_il |Ja^d| Q along direction d */
+      for (int v = 0; v < 5; ++v)
+        for (int k = 0; k < np; ++k)
+          for (int j = 0; j < np; ++j)
+            for (int i = 0; i < np; ++i) {
+              double acc = 0.0;
+              for (int l = 0; l < np; ++l) {
+                int nl = d == 0 ? l + np * (j + np * k) : (d == 1 ? i + np * (l + np * k) : i + np * (j + np * l));
+                int il = d == 0 ? i : (d == 1 ? j : k);
+                acc += o.Dhat[il * np + l] * sJ * Q[v * nn + nl];
+              }
+              g[v * nn + i + np * (j + np * k)] = acc;
+            }
+      /* surface: the two faces of direction d */
+      for (int side = 0; side < 2; ++side) {
+        long long nb = -1; int kind = 0, nb_blk = id.blk;
+        if (d == 0) nb = elem_index(o, id.blk, id.ix, wrap(id.iy + (side ? 1 : -1), o.ny), id.iz);
+        else if (d == 1) nb = elem_index(o, id.blk, id.ix, id.iy, wrap(id.iz + (side ? 1 : -1), o.nz));
+        else {
+          int jx = id.ix + (side ? 1 : -1);
+          if (jx >= 0 && jx < nx) nb = elem_index(o, id.blk, jx, id.iy, id.iz);
+          else if ((id.blk == 0 && side == 0) || (id.blk == 1 && side == 1)) kind = 1;
+          else if (o.p.interface_conforming) {
+            nb_blk = 1 - id.blk;
+            nb = elem_index(o, nb_blk, nb_blk == 0 ? o.p.nel_s[0] - 1 : 0, id.iy, id.iz);
+          } else kind = 2;
+        }
+        double wend = o.w[side == 0 ? 0 : o.N];
+        for (int b = 0; b < np; ++b)
+          for (int aa = 0; aa < np; ++aa) {
+            int vn = face_node_to_vol(o, d, side, aa, b);
+            double Fo[5];
+            if (kind == 2) {
+              const std::vector<double>& L = id.blk == 0 ? Ls : Lm;
+              long long f = (long long)id.iz * o.ny + id.iy;
+              for (int v = 0; v < 5; ++v) Fo[v] = L[(f * 5 + v) * nq + aa + np * b];
+            } else {
+              double qo[5], uo[5];
+              if (kind == 1) {
+                int i = vn % np, j = (vn / np) % np, k = vn / nq;
+                double X[3];
+                node_xyz(o, id, i, j, k, t, X);
+                flow_state(o.p, X, t, 1, uo);
+              } else {
+                int vnn = face_node_to_vol(o, d, 1 - side, aa, b);
+                for (int v = 0; v < 5; ++v) uo[v] = U[(nb * 5 + v) * nn + vnn];
+              }
+              cons_to_prim(uo, o.p.gamma, qo);
+              double sg = side == 1 ? 1.0 : -1.0;
+              for (int v = 0; v < 5; ++v) Fo[v] = sg * sJ * 0.5 * (Q[v * nn + vn] + qo[v]);
+            }
+            for (int v = 0; v < 5; ++v) g[v * nn + vn] += Fo[v] / wend;
+          }
+      }
+      for (int k = 0; k < 5 * nn; ++k) g[k] *= invJ;
+    }
+  }
+}
 }  // namespace
 
 extern "C" {
@@ -797,6 +1021,7 @@ void* orc_create(const orc_problem* p) {
   for (int i = 0; i < o->np; ++i)
     for (int l = 0; l < o->np; ++l) o->Dhat[i * o->np + l] = -(o->w[l] / o->w[i]) * o->D[l * o->np + i];
   orc_lsrk_coeffs(o->A, o->B, o->c);
+  o->ns = p->physics == 1;
   return o;
 }
 
@@ -841,27 +1066,42 @@ void orc_rhs(void* h, const double* U, double t, double* Ut) {
   Oracle& o = *(Oracle*)h;
   Interface I;
   interface_config(o, t, I);
+  std::vector<double> grad;
+  if (o.ns) { grad.assign(o.E * 15 * o.nn, 0.0); compute_lifting(o, I, U, t, grad.data()); }
+  const double* g = o.ns ? grad.data() : nullptr;
   std::vector<double> Fs, Fm;
   const std::vector<double>* ps = nullptr, *pm = nullptr;
-  if (!o.p.interface_conforming) { all_interface_fluxes(o, I, U, Fs, Fm); ps = &Fs; pm = &Fm; }
+  if (!o.p.interface_conforming) { all_interface_fluxes(o, I, U, g, Fs, Fm); ps = &Fs; pm = &Fm; }
   #pragma omp parallel for schedule(static)
-  for (long long e = 0; e < o.E; ++e) element_residual(o, &I, U, t, e, ps, pm, Ut + e * 5 * o.nn);
+  for (long long e = 0; e < o.E; ++e) element_residual(o, &I, U, g, t, e, ps, pm, Ut + e * 5 * o.nn);
 }
 
 void orc_rhs_elements(void* h, const double* U, double t, const long long* elems, int count, double* Ut) {
   Oracle& o = *(Oracle*)h;
   Interface I;
   interface_config(o, t, I);
+  std::vector<double> grad;
+  if (o.ns) { grad.assign(o.E * 15 * o.nn, 0.0); compute_lifting(o, I, U, t, grad.data()); }
+  const double* g = o.ns ? grad.data() : nullptr;
   #pragma omp parallel for schedule(dynamic)
-  for (int m = 0; m < count; ++m) element_residual(o, &I, U, t, elems[m], nullptr, nullptr, Ut + (long long)m * 5 * o.nn);
+  for (int m = 0; m < count; ++m) element_residual(o, &I, U, g, t, elems[m], nullptr, nullptr, Ut + (long long)m * 5 * o.nn);
+}
+
+void orc_lifting(void* h, const double* U, double t, double* grad) {
+  Oracle& o = *(Oracle*)h;
+  Interface I;
+  interface_config(o, t, I);
+  compute_lifting(o, I, U, t, grad);
 }
 
 void orc_interface_fluxes(void* h, const double* U, double t, double* F_static, double* F_moving) {
   Oracle& o = *(Oracle*)h;
   Interface I;
   interface_config(o, t, I);
+  std::vector<double> grad;
+  if (o.ns) { grad.assign(o.E * 15 * o.nn, 0.0); compute_lifting(o, I, U, t, grad.data()); }
   std::vector<double> Fs, Fm;
-  all_interface_fluxes(o, I, U, Fs, Fm);
+  all_interface_fluxes(o, I, U, o.ns ? grad.data() : nullptr, Fs, Fm);
   std::memcpy(F_static, Fs.data(), sizeof(double) * Fs.size());
   std::memcpy(F_moving, Fm.data(), sizeof(double) * Fm.size());
 }

@@ -36,6 +36,8 @@ typedef struct {
   int flow;              /* 0 constant state, 1 entropy wave, 2 Fourier modes (see fpar) */
   double fpar[16];
   double modes[5][8][4]; /* flow 2: per primitive variable, 8 modes of (amp, ky, kz, phase) */
+  int physics;           /* 0 Euler, 1 Navier-Stokes with BR1 lifting */
+  double mu, Pr, Rgas;   /* viscosity, Prandtl number, gas constant (Navier-Stokes) */
 } orc_problem;
 
 /* ---- 1-D basis (Sec. 3.1) ---- */
@@ -75,6 +77,9 @@ void      orc_rhs_elements(void* h, const double* U, double t, const long long* 
 void      orc_interface_fluxes(void* h, const double* U, double t, double* F_static,
                                double* F_moving);                  /* [nz][ny][5][np][np] */
 void      orc_step(void* h, double* U, double* G, double* t, double dt, int nsteps);
+void      orc_lifting(void* h, const double* U, double t, double* grad);  /* [E][3][5][np^3] */
+void      orc_viscous_flux(const double* U, const double* grad15, double mu, double Pr, double Rgas,
+                           double gamma, double* Fv15);                    /* [3][5] at one point */
 void      orc_totals(void* h, const double* U, double* tot5);      /* sum J w w w U */
 void      orc_face_flux_sums(const orc_problem* p, const double* F_static, const double* F_moving,
                              double* sum_static5, double* sum_moving5);

@@ -28,7 +28,8 @@ class OrcProblem(C.Structure):
                 ("y0", C.c_double), ("y1", C.c_double), ("z0", C.c_double), ("z1", C.c_double),
                 ("v", C.c_double), ("delta0", C.c_double), ("gamma", C.c_double),
                 ("riemann", C.c_int), ("interface_conforming", C.c_int), ("flow", C.c_int),
-                ("fpar", C.c_double * 16), ("modes", C.c_double * 160)]
+                ("fpar", C.c_double * 16), ("modes", C.c_double * 160),
+                ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double)]
 
 
 _LIB = None
@@ -64,6 +65,8 @@ def lib():
         L.orc_interface_fluxes.argtypes = [C.c_void_p, _dp, C.c_double, _dp, _dp]
         L.orc_step.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double, C.c_int]
         L.orc_totals.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_lifting.argtypes = [C.c_void_p, _dp, C.c_double, _dp]
+        L.orc_viscous_flux.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double, C.c_double, _dp]
         L.orc_face_flux_sums.argtypes = [C.POINTER(OrcProblem), _dp, _dp, _dp, _dp]
         L.orc_l2_error_rho.argtypes = [C.c_void_p, _dp, C.c_double]
         L.orc_l2_error_rho.restype = C.c_double
@@ -152,6 +155,14 @@ def riemann(kind, UL, UR, n, vgn=0.0, gamma=1.4):
     return F
 
 
+def viscous_flux(U, grad15, mu, Pr, Rgas, gamma=1.4):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    g = np.ascontiguousarray(grad15, dtype=np.float64)
+    F = np.zeros(15)
+    lib().orc_viscous_flux(_p(U), _p(g), float(mu), float(Pr), float(Rgas), float(gamma), _p(F))
+    return F.reshape(3, 5)
+
+
 def lsrk_coeffs():
     A, B, c = np.zeros(5), np.zeros(5), np.zeros(5)
     lib().orc_lsrk_coeffs(_p(A), _p(B), _p(c))
@@ -177,6 +188,8 @@ def to_orc_problem(p) -> OrcProblem:
         s.fpar[k] = f
     for k, m in enumerate(p.modes_array().ravel()):
         s.modes[k] = m
+    s.physics = int(p.physics)
+    s.mu, s.Pr, s.Rgas = float(p.mu), float(p.Pr), float(p.Rgas)
     return s
 
 
@@ -248,6 +261,13 @@ class Oracle:
         tt = C.c_double(t)
         lib().orc_step(self.h, _p(U), _p(G), C.byref(tt), float(dt), int(nsteps))
         return tt.value
+
+    def lifting(self, U, t):
+        """BR1 gradients of the primitive variables, shape (E, 3, 5, np^3)."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        g = np.zeros((self.E, 3, 5, self.nn))
+        lib().orc_lifting(self.h, _p(U), float(t), _p(g))
+        return g
 
     def totals(self, U):
         U = np.ascontiguousarray(U, dtype=np.float64)

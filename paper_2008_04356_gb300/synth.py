@@ -20,7 +20,8 @@ GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 M1 = np.uint64(0xBF58476D1CE4E5B9)
 M2 = np.uint64(0x94D049BB133111EB)
 
-FLOW_CONSTANT, FLOW_ENTROPY_WAVE, FLOW_MODES, FLOW_POLY_X = 0, 1, 2, 3
+FLOW_CONSTANT, FLOW_ENTROPY_WAVE, FLOW_MODES, FLOW_POLY_X, FLOW_SHEAR_X = 0, 1, 2, 3, 4
+EULER, NAVIER_STOKES = 0, 1
 RUSANOV, ROE_HH = 0, 1
 FP64, FP32 = 0, 1
 
@@ -69,6 +70,10 @@ class Problem:
     fpar: tuple = (1.0, 0.2, 1.0, 1.0, 1.0, 0.3, 0.0, 0.0, 1.0)
     modes: Optional[np.ndarray] = None          # (5, 8, 4): amp, ky, kz, phase
     precision: int = FP64
+    physics: int = EULER
+    mu: float = 0.0
+    Pr: float = 0.72
+    Rgas: float = 1.0
 
     @property
     def np_(self) -> int:
@@ -146,6 +151,13 @@ def config_interface_heavy(seed: int = 1, precision: int = FP32, nz: int = 256, 
                    modes=fourier_modes(seed), precision=precision)
 
 
+def config_shear_x(N: int = 3, v: float = 0.5, mu: float = 0.01, w=(0.1, 0.3, -0.2),
+                   rho: float = 1.0, p: float = 1.0) -> Problem:
+    """Navier-Stokes, rho and p constant, velocity (0, 0, w(x)) with w quadratic in x."""
+    return Problem(N=N, nel_s=(3, 4, 2), nel_m=(2, 4, 2), v=v, flow=FLOW_SHEAR_X,
+                   fpar=(rho, p) + tuple(w), physics=NAVIER_STOKES, mu=mu)
+
+
 def config_poly_x(N: int = 3, v: float = 0.5, coeffs=(1.0, 0.1, -0.05, 0.02),
                   vel=(0.3, 0.2, -0.1), p: float = 1.0) -> Problem:
     """State polynomial in x (degree <= 3) with constant velocity and pressure."""
@@ -169,10 +181,14 @@ def wave_speed_bounds(p: Problem):
         a = np.abs(p.modes_array()[:, :, 0]).sum(axis=1)
         rho_min, pmax = f[0] - a[0], f[4] + a[4]
         vel = [abs(f[1]) + a[1], abs(f[2]) + a[2], abs(f[3]) + a[3]]
-    else:
+    elif p.flow == FLOW_POLY_X:
         c = f[:4]
         rho_min = min(c[0] + x * (c[1] + x * (c[2] + x * c[3])) for x in np.linspace(p.x0 - 1, p.x2, 401))
         pmax, vel = f[7], [abs(f[4]), abs(f[5]), abs(f[6])]
+    else:
+        xs = np.linspace(p.x0, p.x2, 401)
+        rho_min, pmax = f[0], f[1]
+        vel = [0.0, 0.0, float(np.abs(f[2] + xs * (f[3] + xs * f[4])).max())]
     return vel, math.sqrt(g * pmax / rho_min)
 
 
@@ -182,11 +198,18 @@ def cfl_dt(p: Problem, cfl: float = 0.9) -> float:
     vel, c = wave_speed_bounds(p)
     hy = (p.y1 - p.y0) / p.nel_s[1]
     hz = (p.z1 - p.z0) / p.nel_s[2]
-    rate = 0.0
+    rate, hmin = 0.0, min(hy, hz)
     for hx, vg in (((p.x1 - p.x0) / p.nel_s[0], 0.0), ((p.x2 - p.x1) / p.nel_m[0], p.v)):
         r = (vel[0] + c) / hx + (vel[1] + abs(vg) + c) / hy + (vel[2] + c) / hz
         rate = max(rate, r)
-    return cfl / ((2 * p.N + 1) * rate)
+        hmin = min(hmin, hx)
+    dt = cfl / ((2 * p.N + 1) * rate)
+    if p.physics == NAVIER_STOKES and p.mu > 0.0:
+        # diffusive limit: dt <= 0.5 h^2 / ((2N+1)^2 nu_max), nu_max = mu/rho * max(4/3, gamma/Pr)
+        rho_min = p.fpar[0] if p.flow in (FLOW_CONSTANT, FLOW_SHEAR_X, FLOW_MODES) else 0.5
+        nu = p.mu / rho_min * max(4.0 / 3.0, p.gamma / p.Pr)
+        dt = min(dt, 0.5 * hmin * hmin / ((2 * p.N + 1) ** 2 * nu))
+    return dt
 
 
 # ---------------------------------------------------------------------------------------
