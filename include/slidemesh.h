@@ -48,7 +48,9 @@ typedef enum {
 enum { SM_FP64 = 0, SM_FP32 = 1 };
 enum { SM_RUSANOV = 0, SM_ROE_HH = 1 };
 enum { SM_GEOM_PLANE = 0 };
-/* Flows used as initial data (sm_init_state) and as the weak Dirichlet state at x = x0, x2:
+enum { SM_EULER = 0, SM_NAVIER_STOKES = 1 };
+/* Flows used as initial data (sm_init_state) and as the weak Dirichlet state at x = x0, x2
+ * (SM_FLOW_SHEAR_X: rho = fpar0, p = fpar1, velocity (0, 0, fpar2 + fpar3 x + fpar4 x^2)):
  *  SM_FLOW_CONSTANT      primitive (rho, v1, v2, v3, p) = fpar[0..4]
  *  SM_FLOW_ENTROPY_WAVE  rho = fpar0 + fpar1 sin(2 pi k.(x - u t)), k = fpar2..4,
  *                        u = fpar5..7, p = fpar8
@@ -57,7 +59,7 @@ enum { SM_GEOM_PLANE = 0 };
  *                        the boundary state is the background
  *  SM_FLOW_POLY_X        rho = fpar0 + fpar1 x' + fpar2 x'^2 + fpar3 x'^3, x' = x - fpar4 t,
  *                        velocity fpar4..6, p = fpar7 */
-enum { SM_FLOW_CONSTANT = 0, SM_FLOW_ENTROPY_WAVE = 1, SM_FLOW_MODES = 2, SM_FLOW_POLY_X = 3 };
+enum { SM_FLOW_CONSTANT = 0, SM_FLOW_ENTROPY_WAVE = 1, SM_FLOW_MODES = 2, SM_FLOW_POLY_X = 3, SM_FLOW_SHEAR_X = 4 };
 
 /* Two structured hexahedral blocks sharing the plane sliding interface x = x1 (Sec. 3.3,
  * first geometry of Fig. sm_meshes_overview).  Static block x in [x0, x1], moving block
@@ -79,6 +81,8 @@ typedef struct {
   int flow;                /* SM_FLOW_* */
   double fpar[16];
   double modes[5][8][4];
+  int physics;             /* SM_EULER | SM_NAVIER_STOKES (BR1 lifting, Sec. 3.1) */
+  double mu, Pr, Rgas;     /* dynamic viscosity, Prandtl number, gas constant */
 } sm_mesh_desc;
 
 /* Motion of the moving block: displacement Delta(t) = delta0 + v t along +y (Sec. 4.3,
@@ -139,6 +143,12 @@ int sm_rhs(sm_solver* s, double t, const void* dU, void* dUt, void* stream);
  * writes both sides' face fluxes (layout above, 5 (N+1)^2 scalars per face) into the
  * caller-owned device arrays dF_static and dF_moving. */
 int sm_interface(sm_solver* s, double t, const void* dU, void* dF_static, void* dF_moving, void* stream);
+
+/* Navier-Stokes solvers: the BR1-lifted gradients (Sec. 3.1) of the primitive variables
+ * (rho, v1, v2, v3, p) of the device state dU at time t, into caller-owned dGrad laid out
+ * [e][axis][primitive][k][j][i] (axis x, y, z), solver precision.  SM_ERR_ARG for an Euler
+ * solver. */
+int sm_gradients(sm_solver* s, double t, const void* dU, void* dGrad, void* stream);
 
 /* Advances the solver state by nsteps low-storage RK4 steps of size dt (five stages each,
  * stage time t + c_k dt computed on the device as fma(c_k, dt, t)).  Asynchronous on

@@ -49,7 +49,10 @@ enum {
   MC_BC = 12,         // [5]: constant boundary state (flows 0 and 2)
   MC_H = 17,          // [4]: hx (static), hx (moving), hy, hz
   MC_X = 21,          // [4]: x0, x1, y0, z0
-  MC_COUNT = 25
+  MC_MU = 25,         // dynamic viscosity
+  MC_K = 26,          // heat conductivity mu gamma R / ((gamma - 1) Pr)
+  MC_R = 27,          // gas constant
+  MC_COUNT = 28
 };
 
 // Mesh and physics description passed to kernels by value.
@@ -62,6 +65,8 @@ struct MeshDev {
   double v, delta0;
   int conforming;
   int flow;
+  int physics;                // 0 Euler, 1 Navier-Stokes
+  double mu, Pr, Rgas;
   double fpar[16];
   const double* modes;        // [5][8][4] device
   const BasisDev* basis;      // device
@@ -283,6 +288,34 @@ __device__ __forceinline__ void rotate_from_x(const T R[5], int ax, T U[5]) {
   U[3] = ax == 0 ? R[3] : (ax == 1 ? R[2] : R[1]);
 }
 
+// Viscous flux along physical axis a (Sec. 2, Eqs. stress_tensor, heat_flux) from the state
+// and the 15 lifted gradients g[d*5 + c] = d(primitive c)/dx_d, primitives (rho, v, p):
+// (0, tau_1a, tau_2a, tau_3a, tau_aj v_j + k dT/dx_a), tau with Stokes' lambda = -2/3 mu,
+// T = p / (rho R).
+template <typename T>
+__device__ __forceinline__ void viscous_flux_axis(const T U[5], const T* g, int a, const T* c, T Fv[5]) {
+  const T ir = Prec<T>::rcp(U[0]);
+  const T v0 = U[1] * ir, v1 = U[2] * ir, v2 = U[3] * ir;
+  const T mu = c[MC_MU];
+  // column a of the velocity gradient and its transpose
+  const T da0 = g[a * 5 + 1], da1 = g[a * 5 + 2], da2 = g[a * 5 + 3];          // d v_b / d x_a
+  const T d0a = g[0 * 5 + 1 + a], d1a = g[1 * 5 + 1 + a], d2a = g[2 * 5 + 1 + a];  // d v_a / d x_b
+  const T div = g[0 * 5 + 1] + g[1 * 5 + 2] + g[2 * 5 + 3];
+  T t0 = mu * (da0 + d0a), t1 = mu * (da1 + d1a), t2 = mu * (da2 + d2a);
+  const T lam = T(-2.0 / 3.0) * mu * div;
+  t0 += a == 0 ? lam : T(0);
+  t1 += a == 1 ? lam : T(0);
+  t2 += a == 2 ? lam : T(0);
+  const T p = (c[MC_GAMMA] - T(1)) * (U[4] - T(0.5) * (U[1] * v0 + U[2] * v1 + U[3] * v2));
+  const T Tt = p * ir / c[MC_R];
+  const T dT = (g[a * 5 + 4] - Tt * c[MC_R] * g[a * 5 + 0]) * ir / c[MC_R];
+  Fv[0] = T(0);
+  Fv[1] = t0;
+  Fv[2] = t1;
+  Fv[3] = t2;
+  Fv[4] = t0 * v0 + t1 * v1 + t2 * v2 + c[MC_K] * dT;
+}
+
 // Exterior state of a weak Dirichlet face at physical position X and time t, in the
 // kernel's precision: the constant background (flows 0 and 2, precomputed) or the exact
 // solution (flows 1 and 3).
@@ -305,11 +338,15 @@ __device__ __forceinline__ void boundary_state(const MeshDev& m, const T X[3], T
     P[0] = Prec<T>::fpar(m, 0) + Prec<T>::fpar(m, 1) * sin_t(T(2.0 * SM_PI) * ph);
     P[1] = Prec<T>::fpar(m, 5); P[2] = Prec<T>::fpar(m, 6); P[3] = Prec<T>::fpar(m, 7);
     P[4] = Prec<T>::fpar(m, 8);
-  } else {
+  } else if (m.flow == 3) {
     const T xs = X[0] - Prec<T>::fpar(m, 4) * t;
     P[0] = Prec<T>::fpar(m, 0) + xs * (Prec<T>::fpar(m, 1) + xs * (Prec<T>::fpar(m, 2) + xs * Prec<T>::fpar(m, 3)));
     P[1] = Prec<T>::fpar(m, 4); P[2] = Prec<T>::fpar(m, 5); P[3] = Prec<T>::fpar(m, 6);
     P[4] = Prec<T>::fpar(m, 7);
+  } else {
+    P[0] = Prec<T>::fpar(m, 0); P[1] = T(0); P[2] = T(0);
+    P[3] = Prec<T>::fpar(m, 2) + X[0] * (Prec<T>::fpar(m, 3) + X[0] * Prec<T>::fpar(m, 4));
+    P[4] = Prec<T>::fpar(m, 1);
   }
   const T g = c[MC_GAMMA];
   U[0] = P[0];
@@ -340,10 +377,12 @@ __device__ __forceinline__ void flow_state(const MeshDev& m, double x, double y,
           const double* md = m.modes + (k * 8 + q) * 4;
           P[k] += md[0] * sin(2.0 * SM_PI * (md[1] * y + md[2] * z) + md[3]);
         }
-  } else {
+  } else if (m.flow == 3) {
     double xs = x - f[4] * t;
     P[0] = f[0] + xs * (f[1] + xs * (f[2] + xs * f[3]));
     P[1] = f[4]; P[2] = f[5]; P[3] = f[6]; P[4] = f[7];
+  } else {
+    P[0] = f[0]; P[1] = 0.0; P[2] = 0.0; P[3] = f[2] + x * (f[3] + x * f[4]); P[4] = f[1];
   }
   U[0] = P[0];
   U[1] = P[0] * P[1];

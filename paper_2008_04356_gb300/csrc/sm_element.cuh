@@ -87,6 +87,30 @@ template <> __device__ __forceinline__ double dhat_c<double>(int n, int idx) { r
 #define SM_ELEM_LINES 1
 #endif
 
+// Every contraction line (direction, variable, line) of the CTA's EPB elements once: read
+// its NP values, write sum_l Dhat_al value_l back in place (Dhat as constant-memory operands).
+template <int N, typename T>
+__device__ __forceinline__ void contract_lines_inplace(T* sF, int tid) {
+  using C = ElemCfg<N>;
+  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
+  for (int w = tid; w < EPB * 15 * NP2; w += THREADS) {
+    const int l2 = w / (15 * NP2);
+    const int rr = w - l2 * 15 * NP2;
+    T* line = sF + l2 * 15 * NN + (rr / NP2) * NN + (rr % NP2) * NP;
+    T rv[NP], ov[NP];
+    load_line<T, NP>(line, rv);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) s += dhat_c<T>(N, a * SM_MAXNP + l) * rv[l];
+      ov[a] = s;
+    }
+#pragma unroll
+    for (int a = 0; a < NP; ++a) line[a] = ov[a];
+  }
+}
+
 // The work of one CTA: elements e0 .. e0+EPB-1 of one solve.  Shared by the single-solve
 // kernel below and the batched persistent kernel.
 //
@@ -94,11 +118,15 @@ template <> __device__ __forceinline__ double dhat_c<double>(int n, int idx) { r
 // fluxes into shared memory and one face-node Riemann flux (own and neighbour traces both
 // read from the state in global memory, the neighbour codes from the topology table), so
 // no thread needs another thread's result until the volume/surface phase after it.
-template <int N, typename T, int RIEM, int MODE>
+// PHYS 1 (Navier-Stokes) adds the viscous fluxes of the BR1-lifted gradients Gr
+// ([E][15][NN], component 5 d + c = d(primitive c)/dx_d): F^c - F^v in the volume and the
+// mean of both sides' viscous fluxes on conforming and boundary faces (Sec. 2, 3.1).
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
 __device__ __forceinline__ void element_block(const MeshDev& m, const StageParams* __restrict__ sp,
                                               const T* __restrict__ U, T* __restrict__ out, T* __restrict__ G,
                                               const T* __restrict__ Fs, const T* __restrict__ Fm, const T rkA,
-                                              const T rkB, const T dt, const long long e0) {
+                                              const T rkB, const T dt, const long long e0,
+                                              const T* __restrict__ Gr = nullptr) {
   using C = ElemCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -131,13 +159,33 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
     const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
     T* Fe = sF + le * 15 * NN;
     const T a0 = c[MC_METRIC + 3 * blk], a1 = c[MC_METRIC + 3 * blk + 1], a2 = c[MC_METRIC + 3 * blk + 2];
+    T gn[PHYS ? 15 : 1], fv[5];
+    if (PHYS) {
+#pragma unroll
+      for (int kk = 0; kk < 15; ++kk) gn[kk] = Gr[(e * 15 + kk) * NN + nd];
+    }
     axis_flux<T, 1>(u, q, blk ? c[MC_VG] : T(0), f);          // xi^1 -> y (grid velocity)
+    if (PHYS) {
+      viscous_flux_axis(u, gn, 1, c, fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= fv[v];
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fe[v * NN + nd] = a0 * f[v];
     axis_flux<T, 2>(u, q, T(0), f);                             // xi^2 -> z
+    if (PHYS) {
+      viscous_flux_axis(u, gn, 2, c, fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= fv[v];
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN + j + NP * (i + NP * k)] = a1 * f[v];
     axis_flux<T, 0>(u, q, T(0), f);                             // xi^3 -> x
+    if (PHYS) {
+      viscous_flux_axis(u, gn, 0, c, fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= fv[v];
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN + k + NP * (i + NP * j)] = a2 * f[v];
   }
@@ -211,6 +259,19 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
       const T vgn = (d == 0 && blk2) ? c[MC_VG] : T(0);
       riemann_axis<T, 0, RIEM>(Lr, Rr, vgn, gamma, fl);
       rotate_from_x(fl, ax, fs);
+      if (PHYS) {
+        // BR1 viscous face flux: mean of both sides' viscous fluxes along the normal; a
+        // weak Dirichlet face pairs the exterior state with the interior gradients
+        T gi[15], go[15], fvi[5], fvo[5];
+        const T* gp = Gr + e2 * 15 * NN + vn;
+        const T* gq = nb >= 0 ? Gr + (long long)nb * 15 * NN + sab + (side ? 0 : N) * sn : gp;
+#pragma unroll
+        for (int kk = 0; kk < 15; ++kk) { gi[kk] = gp[kk * NN]; go[kk] = gq[kk * NN]; }
+        viscous_flux_axis(uin, gi, ax, c, fvi);
+        viscous_flux_axis(uout, go, ax, c, fvo);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) fs[v] -= T(0.5) * (fvi[v] + fvo[v]);
+      }
       const T sJ = c[MC_METRIC + 3 * blk2 + d];
       const T sg = side ? sJ : -sJ;
 #pragma unroll
@@ -224,25 +285,9 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
   const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
   T acc[5];
 #if SM_ELEM_LINES
-  // every contraction line (direction, variable, line) once: read its NP fluxes, write the
-  // NP derivative values back in place; Dhat entries are constant-memory operands
+  // every contraction line (direction, variable, line) once, in place
   __syncthreads();
-  for (int w = tid; w < EPB * 15 * NP2; w += THREADS) {
-    const int l2 = w / (15 * NP2);
-    const int rr = w - l2 * 15 * NP2;
-    T* line = sF + l2 * 15 * NN + (rr / NP2) * NN + (rr % NP2) * NP;
-    T rv[NP], ov[NP];
-    load_line<T, NP>(line, rv);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      T s = T(0);
-#pragma unroll
-      for (int l = 0; l < NP; ++l) s += dhat_c<T>(N, a * SM_MAXNP + l) * rv[l];
-      ov[a] = s;
-    }
-#pragma unroll
-    for (int a = 0; a < NP; ++a) line[a] = ov[a];
-  }
+  contract_lines_inplace<N, T>(sF, tid);
   __syncthreads();
   if (!active) return;
   {
@@ -312,32 +357,34 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
   }
 }
 
-template <int N, typename T, int RIEM, int MODE>
-__global__ void __launch_bounds__(ElemCfg<N>::THREADS, sizeof(T) == 4 ? ElemCfg<N>::MINB : 1)
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
+__global__ void __launch_bounds__(ElemCfg<N>::THREADS, (sizeof(T) == 4 && PHYS == 0) ? ElemCfg<N>::MINB : 1)
 dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
                   T* __restrict__ out, T* __restrict__ G, const T* __restrict__ Fs,
-                  const T* __restrict__ Fm, const T rkA, const T rkB, const T dt) {
-  element_block<N, T, RIEM, MODE>(m, sp, U, out, G, Fs, Fm, rkA, rkB, dt, (long long)blockIdx.x * ElemCfg<N>::EPB);
+                  const T* __restrict__ Fm, const T rkA, const T rkB, const T dt, const T* __restrict__ Gr) {
+  element_block<N, T, RIEM, MODE, PHYS>(m, sp, U, out, G, Fs, Fm, rkA, rkB, dt,
+                                        (long long)blockIdx.x * ElemCfg<N>::EPB, Gr);
 }
 
-template <int N, typename T, int RIEM, int MODE>
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
 static cudaError_t launch_elem_t(const ElemArgs& a, cudaStream_t st) {
   using C = ElemCfg<N>;
   const size_t smem = C::template smem_bytes<T>();
   const long long blocks = (a.m.E + C::EPB - 1) / C::EPB;
   if (blocks <= 0) return cudaSuccess;
-  dg_element_kernel<N, T, RIEM, MODE><<<(unsigned)blocks, C::THREADS, smem, st>>>(
-      a.m, a.sp, (const T*)a.U, (T*)a.out, (T*)a.G, (const T*)a.Fs, (const T*)a.Fm, (T)a.rkA, (T)a.rkB, (T)a.dt);
+  dg_element_kernel<N, T, RIEM, MODE, PHYS><<<(unsigned)blocks, C::THREADS, smem, st>>>(
+      a.m, a.sp, (const T*)a.U, (T*)a.out, (T*)a.G, (const T*)a.Fs, (const T*)a.Fm, (T)a.rkA, (T)a.rkB, (T)a.dt,
+      (const T*)a.Gr);
   return cudaGetLastError();
 }
 
-template <int N, typename T, int RIEM, int MODE>
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
 static cudaError_t prepare_elem_t() {
   using C = ElemCfg<N>;
-  cudaError_t e = cudaFuncSetAttribute(dg_element_kernel<N, T, RIEM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)C::template smem_bytes<T>());
+  cudaError_t e = cudaFuncSetAttribute(dg_element_kernel<N, T, RIEM, MODE, PHYS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::template smem_bytes<T>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(dg_element_kernel<N, T, RIEM, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  return cudaFuncSetAttribute(dg_element_kernel<N, T, RIEM, MODE, PHYS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                               (int)cudaSharedmemCarveoutMaxShared);
 }
 

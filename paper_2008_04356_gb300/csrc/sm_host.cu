@@ -187,6 +187,9 @@ void fill_constants(MeshDev& m, const BasisDev& b, const double* fpar) {
   c[MC_X + 1] = m.x1;
   c[MC_X + 2] = m.y0;
   c[MC_X + 3] = m.z0;
+  c[MC_MU] = m.mu;
+  c[MC_R] = m.Rgas;
+  c[MC_K] = m.Pr > 0.0 ? m.mu * m.gamma * m.Rgas / ((m.gamma - 1.0) * m.Pr) : 0.0;
   for (int k = 0; k < MC_COUNT; ++k) {
     m.cd[k] = c[k];
     m.cf[k] = (float)c[k];
@@ -219,6 +222,8 @@ cudaError_t ensure_dhat_constants() {
   if ((e = upload_dhat_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_batch(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_ns_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_ns_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   g_dhat_done[dev] = true;
   return cudaSuccess;
 }
@@ -248,6 +253,9 @@ struct sm_solver {
   double* t_d = nullptr;
   double* red_d = nullptr;      // partial sums [nblk][5] + outputs [3][5]
   int4* topo_d = nullptr;       // per-element neighbour table (2 int4 per element)
+  void* Gr = nullptr;           // lifted gradients [E][15][NN] (Navier-Stokes)
+  void* Ls = nullptr;           // interface lifting face values, static side (Navier-Stokes)
+  void* Lm = nullptr;           // ... moving side
   int red_blocks = 0;
   int cur = 0;
   double t_host = 0.0;
@@ -257,14 +265,39 @@ struct sm_solver {
 
 namespace {
 
-cudaError_t enqueue_rhs_parts(sm_solver* s, double t, const void* dU, void* Fs, void* Fm, cudaStream_t st) {
-  cudaError_t e = launch_stage_params(s->m, s->np, s->sp, s->t_d, t, 0.0, 0.0, 0, st);
-  if (e != cudaSuccess) return e;
-  if (!s->desc.interface_conforming) e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st);
+bool is_ns(const sm_solver* s) { return s->desc.physics == SM_NAVIER_STOKES; }
+
+// After the stage parameters: everything the element kernel reads besides U.  Navier-Stokes:
+// lifting face values on the interface, the lifted gradients, then the interface fluxes with
+// their viscous part; Euler: the interface fluxes.
+cudaError_t enqueue_flux_inputs(sm_solver* s, const void* dU, void* Fs, void* Fm, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  const bool sliding = !s->desc.interface_conforming;
+  if (is_ns(s)) {
+    if (sliding && (e = launch_interface_lift(s->N, s->prec, s->m, s->sp, dU, s->Ls, s->Lm, st)) != cudaSuccess) return e;
+    e = s->prec == SM_FP64 ? launch_lift_f64(s->N, s->m, s->sp, dU, s->Gr, s->Ls, s->Lm, st)
+                           : launch_lift_f32(s->N, s->m, s->sp, dU, s->Gr, s->Ls, s->Lm, st);
+    if (e != cudaSuccess) return e;
+    if (sliding) e = launch_interface_ns(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, s->Gr, Fs, Fm, st);
+    return e;
+  }
+  if (sliding) e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st);
   return e;
 }
 
-cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a, cudaStream_t st) {
+cudaError_t enqueue_rhs_parts(sm_solver* s, double t, const void* dU, void* Fs, void* Fm, cudaStream_t st) {
+  cudaError_t e = launch_stage_params(s->m, s->np, s->sp, s->t_d, t, 0.0, 0.0, 0, st);
+  if (e != cudaSuccess) return e;
+  return enqueue_flux_inputs(s, dU, Fs, Fm, st);
+}
+
+cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a0, cudaStream_t st) {
+  ElemArgs a = a0;
+  if (is_ns(s)) {
+    a.Gr = s->Gr;
+    return s->prec == SM_FP64 ? launch_element_ns_f64(s->N, s->desc.riemann, mode, a, st)
+                              : launch_element_ns_f32(s->N, s->desc.riemann, mode, a, st);
+  }
   return s->prec == SM_FP64 ? launch_element_f64(s->N, s->desc.riemann, mode, a, st)
                             : launch_element_f32(s->N, s->desc.riemann, mode, a, st);
 }
@@ -274,10 +307,7 @@ cudaError_t enqueue_step(sm_solver* s, double dt, int cur, cudaStream_t st) {
   for (int k = 0; k < 5; ++k) {
     cudaError_t e = launch_stage_params(s->m, s->np, s->sp, s->t_d, 0.0, RK_C[k], dt, k == 4 ? 2 : 1, st);
     if (e != cudaSuccess) return e;
-    if (!s->desc.interface_conforming) {
-      e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, s->U[c], s->Fs, s->Fm, st);
-      if (e != cudaSuccess) return e;
-    }
+    if ((e = enqueue_flux_inputs(s, s->U[c], s->Fs, s->Fm, st)) != cudaSuccess) return e;
     ElemArgs a{s->m, s->sp, s->U[c], s->U[1 - c], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
     e = launch_elem(s, k == 0 ? ELEM_STAGE_FIRST : ELEM_STAGE, a, st);
     if (e != cudaSuccess) return e;
@@ -314,7 +344,8 @@ void free_solver(sm_solver* s) {
   if (!s) return;
   clear_graphs(s);
   if (s->cap) cudaStreamDestroy(s->cap);
-  void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->t_d, s->red_d, s->topo_d};
+  void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->t_d, s->red_d, s->topo_d,
+                  s->Gr, s->Ls, s->Lm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -332,7 +363,10 @@ int valid_desc(const sm_mesh_desc* d) {
   if (!(d->gamma > 1.0)) return fail(SM_ERR_ARG, "gamma must exceed 1");
   if (d->riemann != SM_RUSANOV && d->riemann != SM_ROE_HH) return fail(SM_ERR_ARG, "unknown Riemann solver");
   if (d->precision != SM_FP64 && d->precision != SM_FP32) return fail(SM_ERR_ARG, "unknown precision");
-  if (d->flow < 0 || d->flow > 3) return fail(SM_ERR_ARG, "unknown flow");
+  if (d->flow < 0 || d->flow > 4) return fail(SM_ERR_ARG, "unknown flow");
+  if (d->physics != SM_EULER && d->physics != SM_NAVIER_STOKES) return fail(SM_ERR_ARG, "unknown physics");
+  if (d->physics == SM_NAVIER_STOKES && !(d->mu >= 0.0 && d->Pr > 0.0 && d->Rgas > 0.0))
+    return fail(SM_ERR_ARG, "Navier-Stokes needs mu >= 0, Pr > 0, Rgas > 0");
   long long E = (long long)(d->nel_static[0] + d->nel_moving[0]) * d->nel_static[1] * d->nel_static[2];
   if (E > (1LL << 31)) return fail(SM_ERR_ARG, "too many elements");
   return SM_OK;
@@ -393,6 +427,10 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   m.gamma = desc->gamma;
   m.conforming = desc->interface_conforming;
   m.flow = desc->flow;
+  m.physics = desc->physics;
+  m.mu = desc->mu;
+  m.Pr = desc->Pr;
+  m.Rgas = desc->Rgas;
   for (int k = 0; k < 16; ++k) m.fpar[k] = desc->fpar[k];
   s->nstate = m.E * 5 * s->nn;
   s->nface_vals = (long long)m.ny * m.nz * 5 * s->np * s->np;
@@ -417,6 +455,11 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   SM_ALLOC(s->t_d, sizeof(double));
   SM_ALLOC(s->red_d, sizeof(double) * (s->red_blocks * 5 + 15));
   SM_ALLOC(s->topo_d, sizeof(int4) * 2 * (size_t)m.E);
+  if (desc->physics == SM_NAVIER_STOKES) {
+    SM_ALLOC(s->Gr, (size_t)m.E * 15 * s->nn * s->sb);
+    SM_ALLOC(s->Ls, fbytes);
+    SM_ALLOC(s->Lm, fbytes);
+  }
 #undef SM_ALLOC
   m.basis = s->basis_d;
   m.modes = s->modes_d;
@@ -447,6 +490,9 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   else if ((e = (s->prec == SM_FP64 ? prepare_element_f64(s->N) : prepare_element_f32(s->N))) != cudaSuccess) what = "element kernel attributes";
   else if ((e = ensure_dhat_constants()) != cudaSuccess) what = "derivative constants";
   else if ((e = prepare_interface(s->N, s->prec)) != cudaSuccess) what = "interface kernel attributes";
+  else if (desc->physics == SM_NAVIER_STOKES &&
+           ((e = (s->prec == SM_FP64 ? prepare_ns_f64(s->N) : prepare_ns_f32(s->N))) != cudaSuccess ||
+            (e = prepare_interface_ns(s->N, s->prec)) != cudaSuccess)) what = "Navier-Stokes kernel attributes";
   else if ((e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking)) != cudaSuccess) what = "capture stream";
   else if ((e = cudaDeviceSynchronize()) != cudaSuccess) what = "init sync";
   if (what) {
@@ -531,6 +577,19 @@ int sm_interface(sm_solver* s, double t, const void* dU, void* dFs, void* dFm, v
   return SM_OK;
 }
 
+int sm_gradients(sm_solver* s, double t, const void* dU, void* dGrad, void* stream) {
+  if (!s || !dU || !dGrad) return fail(SM_ERR_ARG, "NULL argument");
+  if (!is_ns(s)) return fail(SM_ERR_ARG, "gradients are lifted for Navier-Stokes solvers only");
+  if (!std::isfinite(t)) return fail(SM_ERR_ARG, "non-finite time");
+  cudaStream_t st = (cudaStream_t)stream;
+  SM_CK(launch_stage_params(s->m, s->np, s->sp, s->t_d, t, 0.0, 0.0, 0, st), "stage parameters");
+  if (!s->desc.interface_conforming)
+    SM_CK(launch_interface_lift(s->N, s->prec, s->m, s->sp, dU, s->Ls, s->Lm, st), "interface lifting");
+  SM_CK(s->prec == SM_FP64 ? launch_lift_f64(s->N, s->m, s->sp, dU, dGrad, s->Ls, s->Lm, st)
+                           : launch_lift_f32(s->N, s->m, s->sp, dU, dGrad, s->Ls, s->Lm, st), "lifting");
+  return SM_OK;
+}
+
 int sm_step(sm_solver* s, double dt, int nsteps, void* stream) {
   if (!s) return fail(SM_ERR_ARG, "NULL solver");
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(SM_ERR_ARG, "dt must be positive, nsteps >= 0");
@@ -560,8 +619,7 @@ int sm_step_profiled(sm_solver* s, double dt, int nsteps, void* stream, double* 
       cudaError_t e = cudaEventRecord(ev[0], st);
       if (e == cudaSuccess) e = launch_stage_params(s->m, s->np, s->sp, s->t_d, 0.0, RK_C[k], dt, k == 4 ? 2 : 1, st);
       if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-      if (e == cudaSuccess && !s->desc.interface_conforming)
-        e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, s->U[s->cur], s->Fs, s->Fm, st);
+      if (e == cudaSuccess) e = enqueue_flux_inputs(s, s->U[s->cur], s->Fs, s->Fm, st);
       if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
       ElemArgs a{s->m, s->sp, s->U[s->cur], s->U[1 - s->cur], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
       if (e == cudaSuccess) e = launch_elem(s, k == 0 ? ELEM_STAGE_FIRST : ELEM_STAGE, a, st);
@@ -744,6 +802,7 @@ extern "C" int sm_batch_create(sm_solver* const* solvers, const double* dt, int 
     if (!solvers[i]) return fail(SM_ERR_ARG, "NULL solver in batch");
     if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return fail(SM_ERR_ARG, "batch time steps must be positive");
     if (solvers[i]->prec != SM_FP32) return fail(SM_ERR_UNSUPPORTED, "batched kernels are FP32; step FP64 solvers with sm_step");
+    if (solvers[i]->desc.physics != SM_EULER) return fail(SM_ERR_UNSUPPORTED, "batched kernels are Euler; step Navier-Stokes solvers with sm_step");
   }
   sm_batch* b = new (std::nothrow) sm_batch();
   if (!b) return fail(SM_ERR_OOM, "host allocation");
@@ -987,6 +1046,7 @@ extern "C" int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, 
                              void* dUt, void* stream) {
   int rc = valid_desc(desc);
   if (rc != SM_OK) return rc;
+  if (desc->physics != SM_EULER) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes the Euler operator only");
   if (!motion || !dU || !dUt) return fail(SM_ERR_ARG, "NULL argument");
   if (dU == dUt) return fail(SM_ERR_ARG, "dU and dUt must not overlap");
   if (motion->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");

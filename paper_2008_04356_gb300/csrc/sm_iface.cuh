@@ -24,24 +24,34 @@ template <int N> struct IfCfg {
   static constexpr int TF = N == 1 ? 32 : (N == 2 ? 16 : 8);   // default tile: static faces per CTA
 #endif
   static constexpr int THREADS = 256;
-  template <typename T, int TFV = TF> static constexpr size_t smem_bytes() {
-    return sizeof(T) * (size_t)(8 * NP2 + 2 * (TFV + 1) * 5 * NP2 + (2 * TFV + 1) * 5 * NP2);
+  static constexpr int TF_NS = 4;   // tile of the Navier-Stokes flux mode (gradient traces staged too)
+  template <typename T, int TFV = TF, int MODE = 0> static constexpr size_t smem_bytes() {
+    return sizeof(T) * (size_t)(8 * NP2 + 2 * (TFV + 1) * 5 * NP2 + (MODE == 1 ? 2 * (TFV + 1) * 15 * NP2 : 0) +
+                                (2 * TFV + 1) * 5 * NP2);
   }
 };
 
+// Interface tile modes: Euler flux, Navier-Stokes flux (BR1 viscous mean of both sides'
+// projected gradients on each mortar, Sec. 3.2), lifting (mortar mean of both sides'
+// projected primitive traces, the BR1 face value of the gradient computation).
+enum { IF_EULER = 0, IF_NS = 1, IF_LIFT = 2 };
+
 // One tile: static faces tile_x * TF .. +TF-1 of perpendicular line iz.  Shared by the
-// single-solve kernel and the batched persistent kernel.
-template <int N, typename T, int RIEM, int TF>
+// single-solve kernel and the batched persistent kernel.  In IF_LIFT mode Fs / Fm receive
+// the lifting face values; IF_NS reads the lifted gradients Gr.
+template <int N, typename T, int RIEM, int TF, int MODE = IF_EULER>
 __device__ __forceinline__ void interface_tile(const MeshDev& m, const StageParams* __restrict__ sp,
                                                const T* __restrict__ U, T* __restrict__ Fs, T* __restrict__ Fm,
-                                               const int tile_x, const int iz) {
+                                               const int tile_x, const int iz, const T* __restrict__ Gr = nullptr) {
   using C = IfCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sMat = reinterpret_cast<T*>(smem_raw);          // [8][NP2]
   T* sTs = sMat + 8 * NP2;                           // [TF+1][5][NP2] static traces
   T* sTm = sTs + (TF + 1) * 5 * NP2;                 // [TF+1][5][NP2] moving traces
-  T* sFm = sTm + (TF + 1) * 5 * NP2;                 // [2TF+1][5][NP2] mortar fluxes
+  T* sGs = sTm + (TF + 1) * 5 * NP2;                 // [TF+1][15][NP2] static gradient traces (IF_NS)
+  T* sGm = sGs + (MODE == IF_NS ? (TF + 1) * 15 * NP2 : 0);
+  T* sFm = sGm + (MODE == IF_NS ? (TF + 1) * 15 * NP2 : 0);   // [2TF+1][5][NP2] mortar fluxes
 
   const int tid = threadIdx.x;
   const int i0 = tile_x * TF;
@@ -89,7 +99,40 @@ __device__ __forceinline__ void interface_tile(const MeshDev& m, const StagePara
       (side ? sTm : sTs)[ww] = U[s_base[side][r] + rem / NP2 * NN + rem % NP2];
     }
   }
+  if (MODE == IF_NS) {
+    // gradient traces: the same node layers of the 15 lifted components
+    const int ngr = 2 * (TFe + 1) * 15 * NP2;
+    for (int w = tid; w < ngr; w += THREADS) {
+      const int ab = w % NP2;
+      const int rest = w / NP2;
+      const int kk = rest % 15;
+      const int sr = rest / 15;
+      const int side = sr >= TFe + 1, r = sr - side * (TFe + 1);
+      const long long eb = s_base[side][r] / (5 * NN);            // element index
+      const int layer = side ? 0 : NP2 * N;
+      (side ? sGm : sGs)[(r * 15 + kk) * NP2 + ab] = Gr[(eb * 15 + kk) * NN + layer + ab];
+    }
+  }
   __syncthreads();
+  if (MODE == IF_LIFT) {
+    // primitive traces (rho, v, p) in place
+    const T gam = Prec<T>::c(m)[MC_GAMMA];
+    for (int w = tid; w < 2 * (TFe + 1) * NP2; w += THREADS) {
+      const int side = w >= (TFe + 1) * NP2;
+      const int ww = w - side * (TFe + 1) * NP2;
+      const int r = ww / NP2, ab = ww - r * NP2;
+      T* t = (side ? sTm : sTs) + r * 5 * NP2 + ab;
+      T u[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) u[v] = t[v * NP2];
+      const Prim<T> q = primitives(u, gam);
+      t[NP2] = q.u[0];
+      t[2 * NP2] = q.u[1];
+      t[3 * NP2] = q.u[2];
+      t[4 * NP2] = q.p;
+    }
+    __syncthreads();
+  }
 
   // mortars mi = 2 r + i_sub for r < TFe, plus mi = 2 TFe (the halo mortar (i0+TFe, 0))
   const T sJ = Prec<T>::c(m)[MC_SJ_IF];
@@ -115,7 +158,32 @@ __device__ __forceinline__ void interface_tile(const MeshDev& m, const StagePara
       QL[v] = al;
       QR[v] = ar;
     }
+    if (MODE == IF_LIFT) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sFm[(mi * 5 + v) * NP2 + ab] = sJ * T(0.5) * (QL[v] + QR[v]);
+      continue;
+    }
     riemann_axis<T, 0, RIEM>(QL, QR, T(0), gamma, F);
+    if (MODE == IF_NS) {
+      T GL[15], GR[15], fvl[5], fvr[5];
+      const T* gs = sGs + r * 15 * NP2 + q * NP;
+      const T* gm = sGm + (r + isub) * 15 * NP2 + q * NP;
+#pragma unroll
+      for (int kk = 0; kk < 15; ++kk) {
+        T al = T(0), ar = T(0);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          al += Ps[i] * gs[kk * NP2 + i];
+          ar += Pm[i] * gm[kk * NP2 + i];
+        }
+        GL[kk] = al;
+        GR[kk] = ar;
+      }
+      viscous_flux_axis(QL, GL, 0, Prec<T>::c(m), fvl);
+      viscous_flux_axis(QR, GR, 0, Prec<T>::c(m), fvr);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) F[v] -= T(0.5) * (fvl[v] + fvr[v]);
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) sFm[(mi * 5 + v) * NP2 + ab] = F[v] * sJ;
   }
@@ -145,4 +213,5 @@ __device__ __forceinline__ void interface_tile(const MeshDev& m, const StagePara
     }
   }
 }
+
 

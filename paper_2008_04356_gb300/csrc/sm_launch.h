@@ -22,6 +22,7 @@ struct ElemArgs {
   const void* Fs;    // interface face fluxes, static side
   const void* Fm;    // interface face fluxes, moving side
   double rkA, rkB, dt;
+  const void* Gr = nullptr;   // lifted gradients (Navier-Stokes)
 };
 
 // sm_elem_f32.cu / sm_elem_f64.cu
@@ -34,6 +35,23 @@ cudaError_t prepare_element_f64(int N);
 cudaError_t upload_dhat_f32(const float* f, const double* d);
 cudaError_t upload_dhat_f64(const float* f, const double* d);
 cudaError_t upload_dhat_batch(const float* f, const double* d);
+
+// Navier-Stokes (sm_elem_ns_f32.cu / sm_elem_ns_f64.cu / sm_iface_ns.cu)
+cudaError_t launch_element_ns_f32(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t launch_element_ns_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t launch_lift_f32(int N, const MeshDev& m, const StageParams* sp, const void* U, void* Gr, const void* Ls,
+                            const void* Lm, cudaStream_t st);
+cudaError_t launch_lift_f64(int N, const MeshDev& m, const StageParams* sp, const void* U, void* Gr, const void* Ls,
+                            const void* Lm, cudaStream_t st);
+cudaError_t prepare_ns_f32(int N);
+cudaError_t prepare_ns_f64(int N);
+cudaError_t upload_dhat_ns_f32(const float* f, const double* d);
+cudaError_t upload_dhat_ns_f64(const float* f, const double* d);
+cudaError_t launch_interface_ns(int N, int prec, int riemann, const MeshDev& m, const StageParams* sp, const void* U,
+                                const void* Gr, void* Fs, void* Fm, cudaStream_t st);
+cudaError_t launch_interface_lift(int N, int prec, const MeshDev& m, const StageParams* sp, const void* U, void* Ls,
+                                  void* Lm, cudaStream_t st);
+cudaError_t prepare_interface_ns(int N, int prec);
 
 // sm_iface.cu
 cudaError_t launch_interface(int N, int prec, int riemann, const MeshDev& m, const StageParams* sp, const void* U,

@@ -40,7 +40,9 @@ size_t request_bytes(const sm_mesh_desc& d) {
   const size_t np = d.N + 1, nn = np * np * np, sb = d.precision == SM_FP64 ? 8 : 4;
   const size_t E = (size_t)(d.nel_static[0] + d.nel_moving[0]) * d.nel_static[1] * d.nel_static[2];
   const size_t faces = (size_t)d.nel_static[1] * d.nel_static[2];
-  return 3 * E * nn * 5 * sb + 2 * faces * 5 * np * np * sb + 32 * E + (64 << 10);
+  size_t b = 3 * E * nn * 5 * sb + 2 * faces * 5 * np * np * sb + 32 * E + (64 << 10);
+  if (d.physics == SM_NAVIER_STOKES) b += E * nn * 15 * sb + 2 * faces * 5 * np * np * sb;   // gradients, lifting
+  return b;
 }
 
 }  // namespace
@@ -150,7 +152,10 @@ void sm_server::run() {
       std::vector<sm_solver*> sol;
       std::vector<double> dts;
       for (Job* j : active)
-        if (j->req.desc.precision == SM_FP32) { sol.push_back(j->solver); dts.push_back(j->req.dt); }
+        if (j->req.desc.precision == SM_FP32 && j->req.desc.physics == SM_EULER) {
+          sol.push_back(j->solver);
+          dts.push_back(j->req.dt);
+        }
       if (!sol.empty()) {
         int rc = sm_batch_create(sol.data(), dts.data(), (int)sol.size(), &batch);
         if (rc == SM_OK) rc = sm_batch_autotune_missing(batch, (void*)st);
@@ -170,7 +175,8 @@ void sm_server::run() {
     if (k > 0) {
       if (batch) rc = sm_batch_step(batch, k, (void*)st);
       for (Job* j : active)
-        if (rc == SM_OK && j->req.desc.precision == SM_FP64) rc = sm_step(j->solver, j->req.dt, k, (void*)st);
+        if (rc == SM_OK && (j->req.desc.precision == SM_FP64 || j->req.desc.physics != SM_EULER))
+          rc = sm_step(j->solver, j->req.dt, k, (void*)st);
       if (rc == SM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SM_ERR_CUDA;
       std::lock_guard<std::mutex> lk(mu);
       stats.batched_steps += k;

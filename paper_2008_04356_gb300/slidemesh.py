@@ -25,7 +25,8 @@ class SmMeshDesc(C.Structure):
                 ("x0", C.c_double), ("x1", C.c_double), ("x2", C.c_double), ("y0", C.c_double),
                 ("y1", C.c_double), ("z0", C.c_double), ("z1", C.c_double), ("gamma", C.c_double),
                 ("riemann", C.c_int), ("precision", C.c_int), ("interface_conforming", C.c_int),
-                ("flow", C.c_int), ("fpar", C.c_double * 16), ("modes", C.c_double * 160)]
+                ("flow", C.c_int), ("fpar", C.c_double * 16), ("modes", C.c_double * 160),
+                ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double)]
 
 
 class SmMotion(C.Structure):
@@ -68,6 +69,7 @@ _SIGS = {
     "sm_rhs": (C.c_int, [_vp, C.c_double, _vp, _vp, _vp]),
     "sm_interface": (C.c_int, [_vp, C.c_double, _vp, _vp, _vp, _vp]),
     "sm_step": (C.c_int, [_vp, C.c_double, C.c_int, _vp]),
+    "sm_gradients": (C.c_int, [_vp, C.c_double, _vp, _vp, _vp]),
     "sm_step_profiled": (C.c_int, [_vp, C.c_double, C.c_int, _vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "sm_diag": (C.c_int, [_vp, C.POINTER(SmDiag), _vp]),
     "sm_state_ptr": (_vp, [_vp]),
@@ -144,6 +146,7 @@ def mesh_desc(p: synth.Problem) -> SmMeshDesc:
         d.fpar[k] = f
     for k, m in enumerate(p.modes_array().ravel()):
         d.modes[k] = m
+    d.physics, d.mu, d.Pr, d.Rgas = int(p.physics), float(p.mu), float(p.Pr), float(p.Rgas)
     return d
 
 
@@ -256,6 +259,13 @@ class Solver:
         check(lib().sm_interface(self.h, float(t), dU.data_ptr(), Fs.data_ptr(), Fm.data_ptr(), _stream(stream)),
               "sm_interface")
         return Fs, Fm
+
+    def gradients(self, dU, t: float, stream=None):
+        """BR1-lifted gradients of the primitive variables, shape (E, 3, 5, np^3)."""
+        import torch
+        out = torch.empty((self.E, 3, 5, self.nn), dtype=self.torch_dtype, device=dU.device)
+        check(lib().sm_gradients(self.h, float(t), dU.data_ptr(), out.data_ptr(), _stream(stream)), "sm_gradients")
+        return out
 
     def step(self, dt: float, nsteps: int, stream=None):
         check(lib().sm_step(self.h, float(dt), int(nsteps), _stream(stream)), "sm_step")
