@@ -446,9 +446,24 @@ int orc_num_threads(void) {
  *   Global element id: static block first, e = ix + nx (iy + ny iz), then the moving block.
  *   State layout: U[(e*5 + var)*np^3 + node], conservative (rho, rho v1..3, rho e).
  * ==================================================================================== */
+/* the curvilinear operator (dg_curved.cpp) */
+void* orc_curved_create(const orc_problem* p);
+void orc_curved_destroy(void* h);
+long long orc_curved_nelem(void* h);
+void orc_curved_coords(void* h, double t, double* xyz);
+void orc_curved_fill(void* h, double t, double* U);
+void orc_curved_metrics(void* h, double t, double* Ja, double* J);
+void orc_curved_lifting(void* h, const double* U, double t, double* grad);
+void orc_curved_interface(void* h, const double* U, double t, double* Fs, double* Fm);
+void orc_curved_rhs(void* h, const double* U, double t, const long long* elems, int count, double* Ut);
+void orc_curved_step(void* h, double* U, double* G, double* t, double dt, int nsteps);
+void orc_curved_totals(void* h, const double* U, double* tot5);
+double orc_curved_l2_error_rho(void* h, const double* U, double t);
+
 namespace {
 
 struct Oracle {
+  int kind = 0;          /* 0: this Cartesian operator; 1: the curvilinear one (dg_curved.cpp) */
   orc_problem p;
   int N, np, nn;
   long long Es, Em, E;
@@ -543,12 +558,30 @@ void flow_state(const orc_problem& p, const double* X, double t, int boundary, d
       P[1] = f[4]; P[2] = f[5]; P[3] = f[6]; P[4] = f[7];
       break;
     }
-    default: {
-      /* 4: rho = fpar0, p = fpar1, velocity (0, 0, w(x)) with w = fpar2 + fpar3 x + fpar4 x^2 */
+    case 4: {
+      /* rho = fpar0, p = fpar1, velocity (0, 0, w(x)) with w = fpar2 + fpar3 x + fpar4 x^2 */
       P[0] = f[0];
       P[1] = 0.0; P[2] = 0.0;
       P[3] = f[2] + X[0] * (f[3] + X[0] * f[4]);
       P[4] = f[1];
+      break;
+    }
+    case 5: {
+      /* axial stream (0, 0, fpar2) with a Gaussian pressure pulse of amplitude fpar3 and
+       * width fpar7 centred at (r, theta, z) = (fpar4, fpar5, fpar6) */
+      double xc = f[4] * std::cos(f[5]), yc = f[4] * std::sin(f[5]), zc = f[6];
+      double d2 = (X[0] - xc) * (X[0] - xc) + (X[1] - yc) * (X[1] - yc) + (X[2] - zc) * (X[2] - zc);
+      P[0] = f[0];
+      P[1] = 0.0; P[2] = 0.0; P[3] = f[2];
+      P[4] = f[1] + (boundary ? 0.0 : f[3] * std::exp(-d2 / (2.0 * f[7] * f[7])));
+      break;
+    }
+    default: {
+      /* 6: rigid rotation with angular speed fpar2 about the z axis */
+      double r2 = X[0] * X[0] + X[1] * X[1];
+      P[0] = f[0];
+      P[1] = -f[2] * X[1]; P[2] = f[2] * X[0]; P[3] = 0.0;
+      P[4] = f[1] + 0.5 * f[0] * f[2] * f[2] * r2;
       break;
     }
   }
@@ -1000,7 +1033,10 @@ void compute_lifting(const Oracle& o, const Interface& I, const double* U, doubl
 
 extern "C" {
 
+static bool curved(void* h) { return *(int*)h == 1; }
+
 void* orc_create(const orc_problem* p) {
+  if (p->geom != 0) return orc_curved_create(p);
   if (p->N < 1 || p->N > 15) return nullptr;
   if (p->nel_s[1] != p->nel_m[1] || p->nel_s[2] != p->nel_m[2]) return nullptr;
   Oracle* o = new Oracle();
@@ -1025,10 +1061,14 @@ void* orc_create(const orc_problem* p) {
   return o;
 }
 
-void orc_destroy(void* h) { delete (Oracle*)h; }
-long long orc_nelem(void* h) { return ((Oracle*)h)->E; }
+void orc_destroy(void* h) {
+  if (curved(h)) orc_curved_destroy(h);
+  else delete (Oracle*)h;
+}
+long long orc_nelem(void* h) { return curved(h) ? orc_curved_nelem(h) : ((Oracle*)h)->E; }
 
 void orc_node_coords(void* h, double t, double* xyz) {
+  if (curved(h)) { orc_curved_coords(h, t, xyz); return; }
   Oracle& o = *(Oracle*)h;
   for (long long e = 0; e < o.E; ++e) {
     ElemId id = elem_id(o, e);
@@ -1059,10 +1099,35 @@ static void fill_flow(Oracle& o, double t, double* U) {
   }
 }
 
-void orc_init_state(void* h, double* U) { fill_flow(*(Oracle*)h, 0.0, U); }
-void orc_exact_state(void* h, double t, double* U) { fill_flow(*(Oracle*)h, t, U); }
+void orc_init_state(void* h, double* U) {
+  if (curved(h)) orc_curved_fill(h, 0.0, U);
+  else fill_flow(*(Oracle*)h, 0.0, U);
+}
+void orc_exact_state(void* h, double t, double* U) {
+  if (curved(h)) orc_curved_fill(h, t, U);
+  else fill_flow(*(Oracle*)h, t, U);
+}
+
+void orc_flow_state(const orc_problem* p, const double* X, double t, int boundary, double* U) {
+  flow_state(*p, X, t, boundary, U);
+}
+
+void orc_metrics(void* h, double t, double* Ja, double* J) {
+  if (curved(h)) { orc_curved_metrics(h, t, Ja, J); return; }
+  Oracle& o = *(Oracle*)h;
+  for (long long e = 0; e < o.E; ++e) {
+    int blk = elem_id(o, e).blk;
+    for (int nd = 0; nd < o.nn; ++nd) {
+      for (int i = 0; i < 3; ++i)
+        for (int n = 0; n < 3; ++n)
+          Ja[((e * 3 + i) * 3 + n) * o.nn + nd] = n == phys_axis(i) ? metric(o, blk, i) : 0.0;
+      J[e * o.nn + nd] = jacobian(o, blk);
+    }
+  }
+}
 
 void orc_rhs(void* h, const double* U, double t, double* Ut) {
+  if (curved(h)) { orc_curved_rhs(h, U, t, nullptr, 0, Ut); return; }
   Oracle& o = *(Oracle*)h;
   Interface I;
   interface_config(o, t, I);
@@ -1077,6 +1142,7 @@ void orc_rhs(void* h, const double* U, double t, double* Ut) {
 }
 
 void orc_rhs_elements(void* h, const double* U, double t, const long long* elems, int count, double* Ut) {
+  if (curved(h)) { orc_curved_rhs(h, U, t, elems, count, Ut); return; }
   Oracle& o = *(Oracle*)h;
   Interface I;
   interface_config(o, t, I);
@@ -1088,6 +1154,7 @@ void orc_rhs_elements(void* h, const double* U, double t, const long long* elems
 }
 
 void orc_lifting(void* h, const double* U, double t, double* grad) {
+  if (curved(h)) { orc_curved_lifting(h, U, t, grad); return; }
   Oracle& o = *(Oracle*)h;
   Interface I;
   interface_config(o, t, I);
@@ -1095,6 +1162,7 @@ void orc_lifting(void* h, const double* U, double t, double* grad) {
 }
 
 void orc_interface_fluxes(void* h, const double* U, double t, double* F_static, double* F_moving) {
+  if (curved(h)) { orc_curved_interface(h, U, t, F_static, F_moving); return; }
   Oracle& o = *(Oracle*)h;
   Interface I;
   interface_config(o, t, I);
@@ -1108,6 +1176,7 @@ void orc_interface_fluxes(void* h, const double* U, double t, double* F_static, 
 
 /* Low-storage RK: per step, stages k = 0..4 at t_k = fma(c_k, dt, t); t advances by dt. */
 void orc_step(void* h, double* U, double* G, double* t, double dt, int nsteps) {
+  if (curved(h)) { orc_curved_step(h, U, G, t, dt, nsteps); return; }
   Oracle& o = *(Oracle*)h;
   long long ndof = o.E * 5 * o.nn;
   std::vector<double> Ut(ndof);
@@ -1126,6 +1195,7 @@ void orc_step(void* h, double* U, double* G, double* t, double dt, int nsteps) {
 }
 
 void orc_totals(void* h, const double* U, double* tot5) {
+  if (curved(h)) { orc_curved_totals(h, U, tot5); return; }
   Oracle& o = *(Oracle*)h;
   for (int v = 0; v < 5; ++v) tot5[v] = 0.0;
   for (long long e = 0; e < o.E; ++e) {
@@ -1155,6 +1225,7 @@ void orc_face_flux_sums(const orc_problem* p, const double* F_static, const doub
 }
 
 double orc_l2_error_rho(void* h, const double* U, double t) {
+  if (curved(h)) return orc_curved_l2_error_rho(h, U, t);
   Oracle& o = *(Oracle*)h;
   double err = 0.0, vol = 0.0;
   for (long long e = 0; e < o.E; ++e) {

@@ -38,7 +38,20 @@ typedef struct {
   double modes[5][8][4]; /* flow 2: per primitive variable, 8 modes of (amp, ky, kz, phase) */
   int physics;           /* 0 Euler, 1 Navier-Stokes with BR1 lifting */
   double mu, Pr, Rgas;   /* viscosity, Prandtl number, gas constant (Navier-Stokes) */
+  int geom;              /* 0 plane interface (Cartesian operator); 1 cylindrical interface
+                            (curvilinear operator); 2 plane interface through the
+                            curvilinear operator (general metrics) */
 } orc_problem;
+
+/* geom 1, the cylindrical sliding interface of Sec. 3.3 (a rotor inside the circle):
+ * x0 < x1 < x2 are the radii (block 0 = rotor, r in [x0, x1]; block 1 = stator, r in
+ * [x1, x2]), [y0, y1] the periodic angular sector (the state crosses its ends rotated by
+ * the sector angle), [z0, z1] the periodic axial extent; v is the rotor's angular speed
+ * omega and delta0 its angle at t = 0.  Reference axes: xi^1 -> theta (sliding), xi^2 -> z,
+ * xi^3 -> r.  Walls r = x0 and r = x2 are slip walls.  Flows for the cylinder: 0 constant
+ * (axial velocity only), 5 axial stream with a Gaussian pressure pulse (fpar: rho, p, w,
+ * amplitude, r_c, theta_c, z_c, width), 6 rigid rotation about z (fpar: rho, p0, Omega;
+ * p = p0 + rho Omega^2 r^2 / 2, a steady solution of the Euler equations). */
 
 /* ---- 1-D basis (Sec. 3.1) ---- */
 int  orc_lgl(int N, double* x, double* w);           /* N+1 Legendre-Gauss-Lobatto nodes/weights */
@@ -81,6 +94,8 @@ void      orc_lifting(void* h, const double* U, double t, double* grad);  /* [E]
 void      orc_viscous_flux(const double* U, const double* grad15, double mu, double Pr, double Rgas,
                            double gamma, double* Fv15);                    /* [3][5] at one point */
 void      orc_totals(void* h, const double* U, double* tot5);      /* sum J w w w U */
+void      orc_metrics(void* h, double t, double* Ja, double* J);   /* Ja[E][3 (i)][3 (n)][np^3] = Ja^i_n, J[E][np^3] */
+void      orc_flow_state(const orc_problem* p, const double* X, double t, int boundary, double* U);
 void      orc_face_flux_sums(const orc_problem* p, const double* F_static, const double* F_moving,
                              double* sum_static5, double* sum_moving5);
 double    orc_l2_error_rho(void* h, const double* U, double t);

@@ -29,7 +29,8 @@ class OrcProblem(C.Structure):
                 ("v", C.c_double), ("delta0", C.c_double), ("gamma", C.c_double),
                 ("riemann", C.c_int), ("interface_conforming", C.c_int), ("flow", C.c_int),
                 ("fpar", C.c_double * 16), ("modes", C.c_double * 160),
-                ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double)]
+                ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double),
+                ("geom", C.c_int)]
 
 
 _LIB = None
@@ -71,6 +72,8 @@ def lib():
         L.orc_l2_error_rho.argtypes = [C.c_void_p, _dp, C.c_double]
         L.orc_l2_error_rho.restype = C.c_double
         L.orc_num_threads.restype = C.c_int
+        L.orc_metrics.argtypes = [C.c_void_p, C.c_double, _dp, _dp]
+        L.orc_flow_state.argtypes = [C.POINTER(OrcProblem), _dp, C.c_double, C.c_int, _dp]
         _LIB = L
     return _LIB
 
@@ -190,6 +193,7 @@ def to_orc_problem(p) -> OrcProblem:
         s.modes[k] = m
     s.physics = int(p.physics)
     s.mu, s.Pr, s.Rgas = float(p.mu), float(p.Pr), float(p.Rgas)
+    s.geom = int(getattr(p, "geom", 0))
     return s
 
 
@@ -261,6 +265,13 @@ class Oracle:
         tt = C.c_double(t)
         lib().orc_step(self.h, _p(U), _p(G), C.byref(tt), float(dt), int(nsteps))
         return tt.value
+
+    def metrics(self, t=0.0):
+        """Ja^i_n at the nodes, shape (E, 3 (i), 3 (n), np^3), and J, shape (E, np^3)."""
+        Ja = np.zeros((self.E, 3, 3, self.nn))
+        J = np.zeros((self.E, self.nn))
+        lib().orc_metrics(self.h, float(t), _p(Ja), _p(J))
+        return Ja, J
 
     def lifting(self, U, t):
         """BR1 gradients of the primitive variables, shape (E, 3, 5, np^3)."""

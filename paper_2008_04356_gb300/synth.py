@@ -21,6 +21,8 @@ M1 = np.uint64(0xBF58476D1CE4E5B9)
 M2 = np.uint64(0x94D049BB133111EB)
 
 FLOW_CONSTANT, FLOW_ENTROPY_WAVE, FLOW_MODES, FLOW_POLY_X, FLOW_SHEAR_X = 0, 1, 2, 3, 4
+FLOW_AXIAL_PULSE, FLOW_RIGID_ROTATION = 5, 6
+GEOM_PLANE, GEOM_CYLINDER, GEOM_PLANE_CURVILINEAR = 0, 1, 2
 EULER, NAVIER_STOKES = 0, 1
 RUSANOV, ROE_HH = 0, 1
 FP64, FP32 = 0, 1
@@ -50,6 +52,11 @@ class Problem:
     z in [z0, z1], periodic in y and z.  The moving block translates along +y with speed v
     (displacement delta0 + v t).  Boundaries x = x0 and x = x2 take the flow's exact (or
     background) state weakly.
+
+    geom GEOM_CYLINDER: the cylindrical sliding interface; x0 < x1 < x2 are radii (block 0,
+    the rotor, inside), [y0, y1] the periodic angular sector, v the rotor's angular speed and
+    delta0 its initial angle; walls r = x0, x2 are slip walls.  GEOM_PLANE_CURVILINEAR: the
+    plane box through the curvilinear operator (general metrics).
     """
     N: int = 3
     nel_s: tuple = (4, 4, 2)
@@ -74,6 +81,7 @@ class Problem:
     mu: float = 0.0
     Pr: float = 0.72
     Rgas: float = 1.0
+    geom: int = GEOM_PLANE
 
     @property
     def np_(self) -> int:
@@ -156,6 +164,30 @@ def config_shear_x(N: int = 3, v: float = 0.5, mu: float = 0.01, w=(0.1, 0.3, -0
     """Navier-Stokes, rho and p constant, velocity (0, 0, w(x)) with w quadratic in x."""
     return Problem(N=N, nel_s=(3, 4, 2), nel_m=(2, 4, 2), v=v, flow=FLOW_SHEAR_X,
                    fpar=(rho, p) + tuple(w), physics=NAVIER_STOKES, mu=mu)
+
+
+def config_cylinder(N: int = 3, nel=(3, 8, 2), omega: float = 0.4, phi0: float = 0.0,
+                    r=(1.0, 1.25, 1.5), sector: float = math.pi / 4, z=(0.0, 0.5),
+                    flow: str = "pulse", mach: float = 0.3, precision: int = FP64,
+                    physics: int = EULER, reynolds: float = 1.0e4) -> Problem:
+    """Cylindrical sliding interface: rotor r in [r0, r1] inside, stator r in [r1, r2],
+    angular sector [0, sector] periodic, z periodic, nel = (radial per block, angular, axial).
+    flow "pulse": axial stream Mach `mach` (rho = 1, p = 1) with a pressure pulse of 1e-2
+    at the interface; "rotation": rigid rotation with the rotor's angular speed; "free":
+    uniform axial stream.  Navier-Stokes: mu = rho |u| L / Re with L the axial length."""
+    c = math.sqrt(1.4)
+    w = mach * c
+    if flow == "pulse":
+        fl, fpar = FLOW_AXIAL_PULSE, (1.0, 1.0, w, 1.0e-2, r[1], 0.5 * sector, 0.5 * (z[0] + z[1]), 0.05)
+    elif flow == "rotation":
+        fl, fpar = FLOW_RIGID_ROTATION, (1.0, 1.0, omega)
+    else:
+        fl, fpar = FLOW_CONSTANT, (1.0, 0.0, 0.0, w, 1.0)
+    mu = 1.0 * w * (z[1] - z[0]) / reynolds if physics == NAVIER_STOKES else 0.0
+    return Problem(N=N, nel_s=(nel[0], nel[1], nel[2]), nel_m=(nel[0], nel[1], nel[2]),
+                   x0=r[0], x1=r[1], x2=r[2], y0=0.0, y1=sector, z0=z[0], z1=z[1],
+                   v=omega, delta0=phi0, flow=fl, fpar=fpar, precision=precision,
+                   physics=physics, mu=mu, geom=GEOM_CYLINDER)
 
 
 def config_poly_x(N: int = 3, v: float = 0.5, coeffs=(1.0, 0.1, -0.05, 0.02),
