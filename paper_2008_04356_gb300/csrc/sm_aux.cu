@@ -1,8 +1,11 @@
 // Initial data and deterministic diagnostics (not on the per-stage path).
 //   - init_state: the flow's state at every node at t = 0 (moving block displaced by delta0);
 //   - totals: sum_e sum_ijk J w_i w_j w_k U (the conserved integrals of Sec. 3.1's weak form);
-//   - face sums: sum over interface faces of w_p w_q F (discrete mortar conservation).
+//   - face sums: sum over interface faces of w_p w_q F (discrete mortar conservation);
+//   - gather traces: the interface node layers of a state in the face-flux layout.
 // Reductions are two-pass in FP64 with a fixed order, so repeated calls agree bit for bit.
+#include <algorithm>
+
 #include "sm_launch.h"
 
 namespace {
@@ -78,7 +81,37 @@ __global__ void finish_sum_kernel(const double* partial, int nblk, double* out5)
   }
 }
 
+// Interface traces of U: static face (iy, iz) is the xi^3 = +1 layer of static element
+// (nxs-1, iy, iz), moving face the xi^3 = -1 layer of moving element (0, iy, iz); output
+// [iz][iy][var][(N+1)^2] per side.
+template <typename T>
+__global__ void gather_traces_kernel(const MeshDev m, int np, const T* __restrict__ U, T* __restrict__ Ts,
+                                     T* __restrict__ Tm) {
+  const long long np2 = (long long)np * np, nn = np2 * np;
+  const long long per_side = (long long)m.ny * m.nz * 5 * np2;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 2 * per_side;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int side = g >= per_side;
+    const long long w = g - side * per_side;
+    const long long f = w / (5 * np2);
+    const int r = (int)(w - f * 5 * np2);
+    const int v = r / (int)np2, ab = r - v * (int)np2;
+    const int iy = (int)(f % m.ny), iz = (int)(f / m.ny);
+    const long long e = encode_elem(m, side, side ? 0 : m.nxs - 1, iy, iz);
+    (side ? Tm : Ts)[w] = U[(e * 5 + v) * nn + (side ? 0 : np2 * (np - 1)) + ab];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_gather_traces(int N, int prec, const MeshDev& m, const void* U, void* Ts, void* Tm, cudaStream_t st) {
+  const int np = N + 1;
+  const long long total = 2LL * m.ny * m.nz * 5 * np * np;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+  if (prec == 0) gather_traces_kernel<double><<<grid, 256, 0, st>>>(m, np, (const double*)U, (double*)Ts, (double*)Tm);
+  else gather_traces_kernel<float><<<grid, 256, 0, st>>>(m, np, (const float*)U, (float*)Ts, (float*)Tm);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init_state(int N, int prec, const MeshDev& m, void* U, cudaStream_t st) {
   const int np = N + 1;

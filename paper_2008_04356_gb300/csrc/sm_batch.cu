@@ -44,13 +44,14 @@ dg_element_batch_kernel(const BatchSolveDev* __restrict__ bs, const int* __restr
     const int c = b.cur ^ (stage & 1);
     element_block<N, float, RIEM, MODE>(b.m, b.sp, (const float*)b.U[c], (float*)b.U[1 - c], (float*)b.G,
                                         (const float*)b.Fs, (const float*)b.Fm, rkA, rkB, (float)b.dt,
-                                        (long long)(item - s_off[s]) * ElemCfg<N>::EPB);
+                                        (long long)(item - s_off[s]) * ElemCfg<N>::EPB, nullptr, (float*)b.Ts,
+                                        (float*)b.Tm);
     __syncthreads();
   }
 }
 
 template <int N, int RIEM, int TF>
-__global__ void __launch_bounds__(IfCfg<N>::THREADS)
+__global__ void __launch_bounds__(IfCfg<N>::THREADS, IfCfg<N>::MINB)
 sliding_interface_batch_kernel(const BatchSolveDev* __restrict__ bs, const int* __restrict__ offs, int nsolve, int stage) {
   __shared__ int s_off[SM_MAX_BATCH + 1];
   for (int i = threadIdx.x; i <= nsolve; i += blockDim.x) s_off[i] = offs[i];
@@ -63,7 +64,7 @@ sliding_interface_batch_kernel(const BatchSolveDev* __restrict__ bs, const int* 
     const int ntx = (b.m.ny + TF - 1) / TF;
     const int c = b.cur ^ (stage & 1);
     interface_tile<N, float, RIEM, TF>(b.m, b.sp, (const float*)b.U[c], (float*)b.Fs, (float*)b.Fm, local % ntx,
-                                       local / ntx);
+                                       local / ntx, nullptr, (const float*)b.Ts, (const float*)b.Tm);
     __syncthreads();
   }
 }

@@ -126,7 +126,8 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
                                               const T* __restrict__ U, T* __restrict__ out, T* __restrict__ G,
                                               const T* __restrict__ Fs, const T* __restrict__ Fm, const T rkA,
                                               const T rkB, const T dt, const long long e0,
-                                              const T* __restrict__ Gr = nullptr) {
+                                              const T* __restrict__ Gr = nullptr, T* __restrict__ Ts = nullptr,
+                                              T* __restrict__ Tm = nullptr) {
   using C = ElemCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -347,12 +348,24 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
 #pragma unroll
     for (int v = 0; v < 5; ++v) out[base + v * NN] = acc[v] * mInvJ;
   } else {
+    T un[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const T ut = acc[v] * mInvJ;
       const T gn = (MODE == ELEM_STAGE_FIRST) ? dt * ut : rkA * g[v] + dt * ut;
       G[base + v * NN] = gn;
-      out[base + v * NN] = u[v] + rkB * gn;
+      un[v] = u[v] + rkB * gn;
+      out[base + v * NN] = un[v];
+    }
+    // the interface node layers of the updated state, for the next stage's interface kernel
+    const int blk = e >= m.Es;
+    if (Ts && k == (blk ? 0 : N)) {
+      const ElemPos p = decode_elem(m, e);
+      if (p.ix == (blk ? 0 : m.nxs - 1)) {
+        T* dst = (blk ? Tm : Ts) + ((long long)p.iz * m.ny + p.iy) * 5 * NP2 + i + NP * j;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dst[v * NP2] = un[v];
+      }
     }
   }
 }
@@ -361,9 +374,10 @@ template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
 __global__ void __launch_bounds__(ElemCfg<N>::THREADS, (sizeof(T) == 4 && PHYS == 0) ? ElemCfg<N>::MINB : 1)
 dg_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
                   T* __restrict__ out, T* __restrict__ G, const T* __restrict__ Fs,
-                  const T* __restrict__ Fm, const T rkA, const T rkB, const T dt, const T* __restrict__ Gr) {
+                  const T* __restrict__ Fm, const T rkA, const T rkB, const T dt, const T* __restrict__ Gr,
+                  T* __restrict__ Ts, T* __restrict__ Tm) {
   element_block<N, T, RIEM, MODE, PHYS>(m, sp, U, out, G, Fs, Fm, rkA, rkB, dt,
-                                        (long long)blockIdx.x * ElemCfg<N>::EPB, Gr);
+                                        (long long)blockIdx.x * ElemCfg<N>::EPB, Gr, Ts, Tm);
 }
 
 template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
@@ -374,7 +388,7 @@ static cudaError_t launch_elem_t(const ElemArgs& a, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
   dg_element_kernel<N, T, RIEM, MODE, PHYS><<<(unsigned)blocks, C::THREADS, smem, st>>>(
       a.m, a.sp, (const T*)a.U, (T*)a.out, (T*)a.G, (const T*)a.Fs, (const T*)a.Fm, (T)a.rkA, (T)a.rkB, (T)a.dt,
-      (const T*)a.Gr);
+      (const T*)a.Gr, (T*)a.Ts, (T*)a.Tm);
   return cudaGetLastError();
 }
 

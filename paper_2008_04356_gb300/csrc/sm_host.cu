@@ -256,6 +256,9 @@ struct sm_solver {
   void* Gr = nullptr;           // lifted gradients [E][15][NN] (Navier-Stokes)
   void* Ls = nullptr;           // interface lifting face values, static side (Navier-Stokes)
   void* Lm = nullptr;           // ... moving side
+  void* Ts = nullptr;           // interface traces of the current state (Euler, sliding interface)
+  void* Tm = nullptr;
+  bool traces_ok = false;       // Ts / Tm hold the traces of U[cur]
   int red_blocks = 0;
   int cur = 0;
   double t_host = 0.0;
@@ -270,7 +273,9 @@ bool is_ns(const sm_solver* s) { return s->desc.physics == SM_NAVIER_STOKES; }
 // After the stage parameters: everything the element kernel reads besides U.  Navier-Stokes:
 // lifting face values on the interface, the lifted gradients, then the interface fluxes with
 // their viscous part; Euler: the interface fluxes.
-cudaError_t enqueue_flux_inputs(sm_solver* s, const void* dU, void* Fs, void* Fm, cudaStream_t st) {
+// from_traces: the interface kernel reads the compact traces Ts / Tm (of U[cur]) instead of U.
+cudaError_t enqueue_flux_inputs(sm_solver* s, const void* dU, void* Fs, void* Fm, cudaStream_t st,
+                                bool from_traces = false) {
   cudaError_t e = cudaSuccess;
   const bool sliding = !s->desc.interface_conforming;
   if (is_ns(s)) {
@@ -281,7 +286,20 @@ cudaError_t enqueue_flux_inputs(sm_solver* s, const void* dU, void* Fs, void* Fm
     if (sliding) e = launch_interface_ns(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, s->Gr, Fs, Fm, st);
     return e;
   }
-  if (sliding) e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st);
+  if (sliding)
+    e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st, from_traces ? s->Ts : nullptr,
+                         from_traces ? s->Tm : nullptr);
+  return e;
+}
+
+// Stepping keeps the interface traces of the current state in Ts / Tm: each stage's element
+// kernel writes those of the state it produces; after a new state they are gathered once.
+bool use_traces(const sm_solver* s) { return s->Ts != nullptr; }
+
+cudaError_t ensure_traces(sm_solver* s, cudaStream_t st) {
+  if (!use_traces(s) || s->traces_ok) return cudaSuccess;
+  cudaError_t e = launch_gather_traces(s->N, s->prec, s->m, s->U[s->cur], s->Ts, s->Tm, st);
+  if (e == cudaSuccess) s->traces_ok = true;
   return e;
 }
 
@@ -307,8 +325,10 @@ cudaError_t enqueue_step(sm_solver* s, double dt, int cur, cudaStream_t st) {
   for (int k = 0; k < 5; ++k) {
     cudaError_t e = launch_stage_params(s->m, s->np, s->sp, s->t_d, 0.0, RK_C[k], dt, k == 4 ? 2 : 1, st);
     if (e != cudaSuccess) return e;
-    if ((e = enqueue_flux_inputs(s, s->U[c], s->Fs, s->Fm, st)) != cudaSuccess) return e;
+    if ((e = enqueue_flux_inputs(s, s->U[c], s->Fs, s->Fm, st, use_traces(s))) != cudaSuccess) return e;
     ElemArgs a{s->m, s->sp, s->U[c], s->U[1 - c], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
+    a.Ts = s->Ts;
+    a.Tm = s->Tm;
     e = launch_elem(s, k == 0 ? ELEM_STAGE_FIRST : ELEM_STAGE, a, st);
     if (e != cudaSuccess) return e;
     c ^= 1;
@@ -345,7 +365,7 @@ void free_solver(sm_solver* s) {
   clear_graphs(s);
   if (s->cap) cudaStreamDestroy(s->cap);
   void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->t_d, s->red_d, s->topo_d,
-                  s->Gr, s->Ls, s->Lm};
+                  s->Gr, s->Ls, s->Lm, s->Ts, s->Tm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -459,6 +479,9 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
     SM_ALLOC(s->Gr, (size_t)m.E * 15 * s->nn * s->sb);
     SM_ALLOC(s->Ls, fbytes);
     SM_ALLOC(s->Lm, fbytes);
+  } else if (!desc->interface_conforming) {
+    SM_ALLOC(s->Ts, fbytes);
+    SM_ALLOC(s->Tm, fbytes);
   }
 #undef SM_ALLOC
   m.basis = s->basis_d;
@@ -526,6 +549,7 @@ int sm_init_state(sm_solver* s, void* stream) {
   if (!s) return fail(SM_ERR_ARG, "NULL solver");
   cudaStream_t st = (cudaStream_t)stream;
   SM_CK(launch_init_state(s->N, s->prec, s->m, s->U[s->cur], st), "init state");
+  s->traces_ok = false;
   SM_CK(cudaMemsetAsync(s->G, 0, (size_t)s->nstate * s->sb, st), "clear G");
   s->t_host = 0.0;
   SM_CK(cudaMemsetAsync(s->t_d, 0, sizeof(double), st), "clear t");
@@ -538,6 +562,7 @@ int sm_set_state(sm_solver* s, const void* U, int on_device, double t, void* str
   cudaStream_t st = (cudaStream_t)stream;
   SM_CK(cudaMemcpyAsync(s->U[s->cur], U, (size_t)s->nstate * s->sb,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "copy state in");
+  s->traces_ok = false;
   s->t_host = t;
   SM_CK(cudaMemcpyAsync(s->t_d, &s->t_host, sizeof(double), cudaMemcpyHostToDevice, st), "copy time in");
   SM_CK(cudaMemsetAsync(s->G, 0, (size_t)s->nstate * s->sb, st), "clear G");
@@ -594,6 +619,7 @@ int sm_step(sm_solver* s, double dt, int nsteps, void* stream) {
   if (!s) return fail(SM_ERR_ARG, "NULL solver");
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(SM_ERR_ARG, "dt must be positive, nsteps >= 0");
   cudaStream_t st = (cudaStream_t)stream;
+  if (nsteps > 0) SM_CK(ensure_traces(s, st), "gather interface traces");
   for (int n = 0; n < nsteps; ++n) {
     cudaGraphExec_t exec;
     int rc = get_graph(s, dt, s->cur, &exec);
@@ -614,14 +640,17 @@ int sm_step_profiled(sm_solver* s, double dt, int nsteps, void* stream, double* 
   double ms[3] = {0, 0, 0};
   int cnt[3] = {0, 0, 0};
   int rc = SM_OK;
+  if (nsteps > 0 && ensure_traces(s, st) != cudaSuccess) rc = fail(SM_ERR_CUDA, "gather interface traces");
   for (int n = 0; n < nsteps && rc == SM_OK; ++n) {
     for (int k = 0; k < 5; ++k) {
       cudaError_t e = cudaEventRecord(ev[0], st);
       if (e == cudaSuccess) e = launch_stage_params(s->m, s->np, s->sp, s->t_d, 0.0, RK_C[k], dt, k == 4 ? 2 : 1, st);
       if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-      if (e == cudaSuccess) e = enqueue_flux_inputs(s, s->U[s->cur], s->Fs, s->Fm, st);
+      if (e == cudaSuccess) e = enqueue_flux_inputs(s, s->U[s->cur], s->Fs, s->Fm, st, use_traces(s));
       if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
       ElemArgs a{s->m, s->sp, s->U[s->cur], s->U[1 - s->cur], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
+      a.Ts = s->Ts;
+      a.Tm = s->Tm;
       if (e == cudaSuccess) e = launch_elem(s, k == 0 ? ELEM_STAGE_FIRST : ELEM_STAGE, a, st);
       if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
       if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
@@ -840,6 +869,8 @@ extern "C" int sm_batch_create(sm_solver* const* solvers, const double* dt, int 
       d.G = s->G;
       d.Fs = s->Fs;
       d.Fm = s->Fm;
+      d.Ts = s->Ts;
+      d.Tm = s->Tm;
       d.t_d = s->t_d;
       d.dt = b->dt[g.members[q]];
       d.cur = s->cur;
@@ -871,6 +902,8 @@ extern "C" int sm_batch_create(sm_solver* const* solvers, const double* dt, int 
 static int batch_autotune(sm_batch* b, void* stream, bool only_missing) {
   if (!b) return fail(SM_ERR_ARG, "NULL batch");
   cudaStream_t st = (cudaStream_t)stream;
+  // the timed interface launches read the compact traces
+  for (sm_solver* s : b->solvers) SM_CK(ensure_traces(s, st), "gather interface traces");
   cudaEvent_t e0, e1;
   SM_CK(cudaEventCreate(&e0), "event");
   SM_CK(cudaEventCreate(&e1), "event");
@@ -929,6 +962,8 @@ static int batch_autotune(sm_batch* b, void* stream, bool only_missing) {
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return fail(SM_ERR_CUDA, "autotune", err);
   if (tuned && b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  // the timed first-stage element launches wrote the traces of the spare buffer
+  for (sm_solver* s : b->solvers) s->traces_ok = false;
   SM_CK(cudaStreamSynchronize(st), "autotune sync");
   return SM_OK;
 }
@@ -953,6 +988,7 @@ extern "C" int sm_batch_step(sm_batch* b, int nsteps, void* stream) {
       SM_CK(cudaMemcpyAsync(g.d_bs, g.host.data(), sizeof(BatchSolveDev) * g.host.size(), cudaMemcpyHostToDevice, st),
             "batch parity upload");
   }
+  for (sm_solver* s : b->solvers) SM_CK(ensure_traces(s, st), "gather interface traces");
   if (!b->graph) {
     SM_CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t e = enqueue_batch_step(b, b->cap);

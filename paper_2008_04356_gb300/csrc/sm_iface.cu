@@ -4,18 +4,19 @@
 namespace {
 
 template <int N, typename T, int RIEM>
-__global__ void __launch_bounds__(IfCfg<N>::THREADS)
+__global__ void __launch_bounds__(IfCfg<N>::THREADS, sizeof(T) == 4 ? IfCfg<N>::MINB : 1)
 sliding_interface_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
-                         T* __restrict__ Fs, T* __restrict__ Fm) {
-  interface_tile<N, T, RIEM, IfCfg<N>::TF>(m, sp, U, Fs, Fm, blockIdx.x, blockIdx.y);
+                         T* __restrict__ Fs, T* __restrict__ Fm, const T* __restrict__ Ts, const T* __restrict__ Tm) {
+  interface_tile<N, T, RIEM, IfCfg<N>::TF>(m, sp, U, Fs, Fm, blockIdx.x, blockIdx.y, nullptr, Ts, Tm);
 }
 
 template <int N, typename T, int RIEM>
-cudaError_t launch_if_t(const MeshDev& m, const StageParams* sp, const void* U, void* Fs, void* Fm, cudaStream_t st) {
+cudaError_t launch_if_t(const MeshDev& m, const StageParams* sp, const void* U, void* Fs, void* Fm, cudaStream_t st,
+                        const void* Ts, const void* Tm) {
   using C = IfCfg<N>;
   dim3 grid((m.ny + C::TF - 1) / C::TF, m.nz);
   sliding_interface_kernel<N, T, RIEM><<<grid, C::THREADS, C::template smem_bytes<T>(), st>>>(
-      m, sp, (const T*)U, (T*)Fs, (T*)Fm);
+      m, sp, (const T*)U, (T*)Fs, (T*)Fm, (const T*)Ts, (const T*)Tm);
   return cudaGetLastError();
 }
 
@@ -31,9 +32,12 @@ cudaError_t prepare_if_t() {
 
 template <int N>
 cudaError_t launch_if_n(int prec, int riemann, const MeshDev& m, const StageParams* sp, const void* U, void* Fs,
-                        void* Fm, cudaStream_t st) {
-  if (prec == 0) return riemann ? launch_if_t<N, double, 1>(m, sp, U, Fs, Fm, st) : launch_if_t<N, double, 0>(m, sp, U, Fs, Fm, st);
-  return riemann ? launch_if_t<N, float, 1>(m, sp, U, Fs, Fm, st) : launch_if_t<N, float, 0>(m, sp, U, Fs, Fm, st);
+                        void* Fm, cudaStream_t st, const void* Ts, const void* Tm) {
+  if (prec == 0)
+    return riemann ? launch_if_t<N, double, 1>(m, sp, U, Fs, Fm, st, Ts, Tm)
+                   : launch_if_t<N, double, 0>(m, sp, U, Fs, Fm, st, Ts, Tm);
+  return riemann ? launch_if_t<N, float, 1>(m, sp, U, Fs, Fm, st, Ts, Tm)
+                 : launch_if_t<N, float, 0>(m, sp, U, Fs, Fm, st, Ts, Tm);
 }
 
 template <int N>
@@ -44,15 +48,15 @@ cudaError_t prepare_if_n(int prec) {
 }  // namespace
 
 cudaError_t launch_interface(int N, int prec, int riemann, const MeshDev& m, const StageParams* sp, const void* U,
-                             void* Fs, void* Fm, cudaStream_t st) {
+                             void* Fs, void* Fm, cudaStream_t st, const void* Ts, const void* Tm) {
   switch (N) {
-    case 1: return launch_if_n<1>(prec, riemann, m, sp, U, Fs, Fm, st);
-    case 2: return launch_if_n<2>(prec, riemann, m, sp, U, Fs, Fm, st);
-    case 3: return launch_if_n<3>(prec, riemann, m, sp, U, Fs, Fm, st);
-    case 4: return launch_if_n<4>(prec, riemann, m, sp, U, Fs, Fm, st);
-    case 5: return launch_if_n<5>(prec, riemann, m, sp, U, Fs, Fm, st);
-    case 6: return launch_if_n<6>(prec, riemann, m, sp, U, Fs, Fm, st);
-    case 7: return launch_if_n<7>(prec, riemann, m, sp, U, Fs, Fm, st);
+    case 1: return launch_if_n<1>(prec, riemann, m, sp, U, Fs, Fm, st, Ts, Tm);
+    case 2: return launch_if_n<2>(prec, riemann, m, sp, U, Fs, Fm, st, Ts, Tm);
+    case 3: return launch_if_n<3>(prec, riemann, m, sp, U, Fs, Fm, st, Ts, Tm);
+    case 4: return launch_if_n<4>(prec, riemann, m, sp, U, Fs, Fm, st, Ts, Tm);
+    case 5: return launch_if_n<5>(prec, riemann, m, sp, U, Fs, Fm, st, Ts, Tm);
+    case 6: return launch_if_n<6>(prec, riemann, m, sp, U, Fs, Fm, st, Ts, Tm);
+    case 7: return launch_if_n<7>(prec, riemann, m, sp, U, Fs, Fm, st, Ts, Tm);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -24,23 +24,181 @@ template <int N> struct IfCfg {
   static constexpr int TF = N == 1 ? 32 : (N == 2 ? 16 : 8);   // default tile: static faces per CTA
 #endif
   static constexpr int THREADS = 256;
+  // resident CTAs per SM asked of the register allocator for the FP32 Euler tile
+  static constexpr int MINB = 4;
   static constexpr int TF_NS = 4;   // tile of the Navier-Stokes flux mode (gradient traces staged too)
   template <typename T, int TFV = TF, int MODE = 0> static constexpr size_t smem_bytes() {
-    return sizeof(T) * (size_t)(8 * NP2 + 2 * (TFV + 1) * 5 * NP2 + (MODE == 1 ? 2 * (TFV + 1) * 15 * NP2 : 0) +
-                                (2 * TFV + 1) * 5 * NP2);
+    // Euler: operators + both sides' projected traces on the 2 TF + 1 mortars; the other
+    // modes also stage the face traces (and the gradient traces)
+    return MODE == 0 ? sizeof(T) * (size_t)(8 * NP2 + 2 * (2 * TFV + 1) * 5 * NP2)
+                     : sizeof(T) * (size_t)(8 * NP2 + 2 * (TFV + 1) * 5 * NP2 +
+                                            (MODE == 1 ? 2 * (TFV + 1) * 15 * NP2 : 0) + (2 * TFV + 1) * 5 * NP2);
   }
 };
+
+// NP consecutive values of a node row; 8-byte accesses where rows are 8-byte aligned (FP32
+// with an even row length: every row offset in the state, the face fluxes and the operator
+// tables is then even).
+template <int NP, typename T> __device__ __forceinline__ void ld_row(const T* __restrict__ p, T* r) {
+  if constexpr (sizeof(T) == 4 && NP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP / 2; ++i) {
+      const float2 v = reinterpret_cast<const float2*>(p)[i];
+      r[2 * i] = v.x;
+      r[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) r[i] = p[i];
+  }
+}
+template <int NP, typename T> __device__ __forceinline__ void st_row(T* __restrict__ p, const T* r) {
+  if constexpr (sizeof(T) == 4 && NP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP / 2; ++i) reinterpret_cast<float2*>(p)[i] = make_float2(r[2 * i], r[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) p[i] = r[i];
+  }
+}
+
+// Euler flux tile, three phases over the tile's 2 TF + 1 mortars:
+//   1. one work item per (mortar, side, row q, variable): the face's trace row goes from
+//      HBM into registers and is projected along the sliding direction (Sec. 3.2, Eq.
+//      projection_domain_mortar) with the side's operator rows, broadcast from shared
+//      memory; the projected row is stored in shared memory;
+//   2. one work item per mortar node: Riemann flux of the two projected states, times the
+//      surface element, in place of the static side's projection;
+//   3. one work item per (side, face, row q, variable): the face's two mortar flux rows are
+//      projected back (Eq. projection_mortar_domain) and written to the face flux array.
+// The traces come from the compact arrays Ts / Tm ([n_perp][n_par][5][(N+1)^2], the face
+// fluxes' layout) when given, else from the element node layers of U.
+template <int N, typename T, int RIEM, int TF>
+__device__ __forceinline__ void interface_tile_euler(const MeshDev& m, const StageParams* __restrict__ sp,
+                                                     const T* __restrict__ U, T* __restrict__ Fs,
+                                                     T* __restrict__ Fm, const int tile_x, const int iz,
+                                                     const T* __restrict__ Ts, const T* __restrict__ Tm) {
+  using C = IfCfg<N>;
+  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, THREADS = C::THREADS, NM = 2 * TF + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sMat = reinterpret_cast<T*>(smem_raw);   // [8][NP2]
+  T* sQ = sMat + 8 * NP2;                     // [side][NM][5][NP2]; side 0 then holds the mortar fluxes
+  __shared__ long long s_base[2][TF + 1];
+
+  const int tid = threadIdx.x;
+  const int i0 = tile_x * TF;
+  const int ny = m.ny;
+  const int TFe = min(TF, ny - i0);
+  const int nmort = 2 * TFe + 1;
+  long long nl = sp->n % ny;
+  const int nmod = (int)(nl < 0 ? nl + ny : nl);
+
+  for (int w = tid; w < 8 * NP2; w += THREADS) {
+    const int k = w / NP2, r = w - k * NP2;
+    sMat[w] = Prec<T>::mat(sp, k)[r];
+  }
+  // trace base offsets: static faces i0+r and moving faces i0-n-1+r (mod n_par), r = 0..TFe;
+  // in U a static trace is its element's xi^3 = +1 node layer, a moving one the xi^3 = -1 layer
+  const bool compact = Ts != nullptr;
+  const int vstride = compact ? NP2 : NN;
+  if (tid < 2 * (TFe + 1)) {
+    const int side = tid / (TFe + 1), r = tid - side * (TFe + 1);
+    int f = side ? i0 - nmod - 1 + r : i0 + r;
+    f %= ny;
+    if (f < 0) f += ny;
+    s_base[side][r] = compact ? ((long long)iz * ny + f) * 5 * NP2
+                              : encode_elem(m, side, side ? 0 : m.nxs - 1, f, iz) * 5 * NN + (side ? 0 : NP2 * N);
+  }
+  __syncthreads();
+
+  // 1. projections, one (mortar, side, row q, variable) per work item; mortar mi = 2 r + i_sub
+  // meets static face r and moving face r + i_sub
+  for (int w = tid; w < nmort * 2 * NP * 5; w += THREADS) {
+    const int q = w % NP;
+    int rest = w / NP;
+    const int v = rest % 5;
+    rest /= 5;
+    const int side = rest & 1, mi = rest >> 1;
+    const int r = mi >> 1, isub = mi & 1;
+    T t[NP];
+    ld_row<NP>((compact ? (side ? Tm : Ts) : U) + s_base[side][r + side * isub] + v * vstride + q * NP, t);
+    // the static lower mortar meets the moving face's upper part and vice versa
+    const T* P = sMat + (side ? (isub ? 2 : 3) : (isub ? 1 : 0)) * NP2;
+    T o[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      T pr[NP];
+      ld_row<NP>(P + j * NP, pr);
+      T acc = T(0);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) acc += pr[i] * t[i];
+      o[j] = acc;
+    }
+    st_row<NP>(sQ + ((side * NM + mi) * 5 + v) * NP2 + q * NP, o);
+  }
+  __syncthreads();
+
+  // 2. mortar Riemann fluxes, static outward normal +x, times the surface element
+  const T sJ = Prec<T>::c(m)[MC_SJ_IF];
+  const T gamma = Prec<T>::c(m)[MC_GAMMA];
+  for (int w = tid; w < nmort * NP2; w += THREADS) {
+    const int mi = w / NP2, ab = w - mi * NP2;
+    T* qs = sQ + (mi * 5) * NP2 + ab;
+    const T* qm = sQ + ((NM + mi) * 5) * NP2 + ab;
+    T QL[5], QR[5], F[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      QL[v] = qs[v * NP2];
+      QR[v] = qm[v * NP2];
+    }
+    riemann_axis<T, 0, RIEM>(QL, QR, T(0), gamma, F);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qs[v * NP2] = F[v] * sJ;
+  }
+  __syncthreads();
+
+  // 3. back-projection, one (side, face, row q, variable) per work item: static face i0+r
+  // from mortars (2r, 2r+1); moving face i0-n+r from mortars 2r+1 (its lower part) and 2r+2
+  // (its upper part), with the opposite sign
+  for (int w = tid; w < 2 * TFe * NP * 5; w += THREADS) {
+    const int q = w % NP;
+    int rest = w / NP;
+    const int v = rest % 5;
+    rest /= 5;
+    const int side = rest >= TFe;
+    const int r = rest - side * TFe;
+    T a[NP], b[NP], o[NP];
+    ld_row<NP>(sQ + ((2 * r + side) * 5 + v) * NP2 + q * NP, a);
+    ld_row<NP>(sQ + ((2 * r + 1 + side) * 5 + v) * NP2 + q * NP, b);
+    const T* Blo = sMat + (side ? 6 : 4) * NP2;
+    const T* Bhi = sMat + (side ? 7 : 5) * NP2;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T bl[NP], bh[NP];
+      ld_row<NP>(Blo + i * NP, bl);
+      ld_row<NP>(Bhi + i * NP, bh);
+      T acc = T(0);
+#pragma unroll
+      for (int jj = 0; jj < NP; ++jj) acc += bl[jj] * a[jj] + bh[jj] * b[jj];
+      o[i] = side ? -acc : acc;
+    }
+    int f = side ? i0 - nmod + r : i0 + r;
+    f %= ny;
+    if (f < 0) f += ny;
+    st_row<NP>((side ? Fm : Fs) + (((long long)iz * ny + f) * 5 + v) * NP2 + q * NP, o);
+  }
+}
 
 // Interface tile modes: Euler flux, Navier-Stokes flux (BR1 viscous mean of both sides'
 // projected gradients on each mortar, Sec. 3.2), lifting (mortar mean of both sides'
 // projected primitive traces, the BR1 face value of the gradient computation).
 enum { IF_EULER = 0, IF_NS = 1, IF_LIFT = 2 };
 
-// One tile: static faces tile_x * TF .. +TF-1 of perpendicular line iz.  Shared by the
-// single-solve kernel and the batched persistent kernel.  In IF_LIFT mode Fs / Fm receive
+// Staged tile (lifting and Navier-Stokes flux): static faces tile_x * TF .. +TF-1 of line iz,
+// face traces staged in shared memory, one thread per mortar node.  In IF_LIFT mode Fs / Fm receive
 // the lifting face values; IF_NS reads the lifted gradients Gr.
-template <int N, typename T, int RIEM, int TF, int MODE = IF_EULER>
-__device__ __forceinline__ void interface_tile(const MeshDev& m, const StageParams* __restrict__ sp,
+template <int N, typename T, int RIEM, int TF, int MODE>
+__device__ __forceinline__ void interface_tile_staged(const MeshDev& m, const StageParams* __restrict__ sp,
                                                const T* __restrict__ U, T* __restrict__ Fs, T* __restrict__ Fm,
                                                const int tile_x, const int iz, const T* __restrict__ Gr = nullptr) {
   using C = IfCfg<N>;
@@ -215,3 +373,15 @@ __device__ __forceinline__ void interface_tile(const MeshDev& m, const StagePara
 }
 
 
+// One tile of any mode: the Euler flux takes the register-blocked form, lifting and the
+// Navier-Stokes flux the staged form.
+template <int N, typename T, int RIEM, int TF, int MODE = IF_EULER>
+__device__ __forceinline__ void interface_tile(const MeshDev& m, const StageParams* __restrict__ sp,
+                                               const T* __restrict__ U, T* __restrict__ Fs, T* __restrict__ Fm,
+                                               const int tile_x, const int iz, const T* __restrict__ Gr = nullptr,
+                                               const T* __restrict__ Ts = nullptr, const T* __restrict__ Tm = nullptr) {
+  if constexpr (MODE == IF_EULER)
+    interface_tile_euler<N, T, RIEM, TF>(m, sp, U, Fs, Fm, tile_x, iz, Ts, Tm);
+  else
+    interface_tile_staged<N, T, RIEM, TF, MODE>(m, sp, U, Fs, Fm, tile_x, iz, Gr);
+}

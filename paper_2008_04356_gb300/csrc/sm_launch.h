@@ -23,7 +23,21 @@ struct ElemArgs {
   const void* Fm;    // interface face fluxes, moving side
   double rkA, rkB, dt;
   const void* Gr = nullptr;   // lifted gradients (Navier-Stokes)
+  void* Ts = nullptr;         // stage modes: interface traces of the updated state, static side
+  void* Tm = nullptr;         // ... moving side ([n_perp][n_par][5][(N+1)^2], nullptr: not written)
 };
+
+// sm_curved_f32.cu / sm_curved_f64.cu: curvilinear geometries (MeshDev::geom != 0)
+cudaError_t launch_curved_element_f32(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t launch_curved_element_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t launch_curved_interface_f32(int N, int riemann, const MeshDev& m, const StageParams* sp, const void* U,
+                                        void* Fs, void* Fm, cudaStream_t st);
+cudaError_t launch_curved_interface_f64(int N, int riemann, const MeshDev& m, const StageParams* sp, const void* U,
+                                        void* Fs, void* Fm, cudaStream_t st);
+cudaError_t prepare_curved_f32(int N);
+cudaError_t prepare_curved_f64(int N);
+cudaError_t upload_dhat_curved_f32(const float* f, const double* d);
+cudaError_t upload_dhat_curved_f64(const float* f, const double* d);
 
 // sm_elem_f32.cu / sm_elem_f64.cu
 cudaError_t launch_element_f32(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
@@ -54,8 +68,12 @@ cudaError_t launch_interface_lift(int N, int prec, const MeshDev& m, const Stage
 cudaError_t prepare_interface_ns(int N, int prec);
 
 // sm_iface.cu
+// Ts / Tm: the interface traces of U in the compact layout of the face fluxes (written by
+// the stage-mode element kernel or launch_gather_traces), or nullptr to read them from U.
 cudaError_t launch_interface(int N, int prec, int riemann, const MeshDev& m, const StageParams* sp, const void* U,
-                             void* Fs, void* Fm, cudaStream_t st);
+                             void* Fs, void* Fm, cudaStream_t st, const void* Ts = nullptr, const void* Tm = nullptr);
+// sm_aux.cu: the interface traces of U into Ts / Tm
+cudaError_t launch_gather_traces(int N, int prec, const MeshDev& m, const void* U, void* Ts, void* Tm, cudaStream_t st);
 cudaError_t prepare_interface(int N, int prec);
 
 // sm_aux.cu: initial data, reductions
@@ -75,6 +93,8 @@ struct BatchSolveDev {
   void* G;
   void* Fs;
   void* Fm;
+  void* Ts;          // interface traces of the current state (static, moving side)
+  void* Tm;
   double* t_d;
   double dt;
   int cur;
