@@ -12,7 +12,8 @@
  * Readings (the paper does not print them):
  *   - metrics: conservative curl form of Kopriva (2006), antisymmetrised,
  *       Ja^i_n = -1/2 [curl_xi (X_l grad_xi X_m - X_m grad_xi X_l)]_i,  (n, m, l) cyclic,
- *     from the node coordinates of the analytic map; J = a_1 . (a_2 x a_3) with
+ *     from the node coordinates of the analytic map (relative to the element's centre,
+ *     which the form does not see: it is translation invariant); J = a_1 . (a_2 x a_3) with
  *     a_d = D_d X.  The discrete metric identities sum_i D_i Ja^i_n = 0 hold, and the
  *     form commutes with a rotation of the mesh;
  *   - the rotor (block 0 of geom 1) turns about the z axis by phi(t) = fma(omega, t, phi0):
@@ -192,6 +193,19 @@ void build_geometry(Curved& o) {
           }
           X[2 * nn + nd] = s2;
         }
+    /* coordinates relative to the element's centre: the curl form is invariant under a
+     * translation of X (the D_d commute), and local coordinates keep its products from
+     * cancelling digits */
+    double Xc[3];
+    {
+      double s1 = o.p.y0 + (id.iy + 0.5) * o.h1, s2 = o.p.z0 + (id.iz + 0.5) * o.h2;
+      double s3 = lo3 + (id.ix + 0.5) * o.h3[id.blk];
+      Xc[0] = o.cyl ? s3 * std::cos(s1) : s3;
+      Xc[1] = o.cyl ? s3 * std::sin(s1) : s1;
+      Xc[2] = s2;
+    }
+    for (int n = 0; n < 3; ++n)
+      for (int nd = 0; nd < nn; ++nd) X[n * nn + nd] -= Xc[n];
     /* derivative along reference direction d of a nodal field f */
     auto Dd = [&](int d, const double* f, double* out) {
       for (int k = 0; k < np; ++k)
@@ -234,7 +248,7 @@ void build_geometry(Curved& o) {
       }
     }
     for (int n = 0; n < 3; ++n)
-      for (int nd = 0; nd < nn; ++nd) o.X0[(e * 3 + n) * nn + nd] = X[n * nn + nd];
+      for (int nd = 0; nd < nn; ++nd) o.X0[(e * 3 + n) * nn + nd] = X[n * nn + nd] + Xc[n];
   }
 }
 
