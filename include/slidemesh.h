@@ -47,7 +47,7 @@ typedef enum {
 
 enum { SM_FP64 = 0, SM_FP32 = 1 };
 enum { SM_RUSANOV = 0, SM_ROE_HH = 1 };
-enum { SM_GEOM_PLANE = 0 };
+enum { SM_GEOM_PLANE = 0, SM_GEOM_CYLINDER = 1, SM_GEOM_PLANE_CURVILINEAR = 2 };
 enum { SM_EULER = 0, SM_NAVIER_STOKES = 1 };
 /* Flows used as initial data (sm_init_state) and as the weak Dirichlet state at x = x0, x2
  * (SM_FLOW_SHEAR_X: rho = fpar0, p = fpar1, velocity (0, 0, fpar2 + fpar3 x + fpar4 x^2)):
@@ -58,15 +58,29 @@ enum { SM_EULER = 0, SM_NAVIER_STOKES = 1 };
  *                        modes[var][m] = (amp, ky, kz, phase): amp sin(2 pi (ky y + kz z) + phase);
  *                        the boundary state is the background
  *  SM_FLOW_POLY_X        rho = fpar0 + fpar1 x' + fpar2 x'^2 + fpar3 x'^3, x' = x - fpar4 t,
- *                        velocity fpar4..6, p = fpar7 */
-enum { SM_FLOW_CONSTANT = 0, SM_FLOW_ENTROPY_WAVE = 1, SM_FLOW_MODES = 2, SM_FLOW_POLY_X = 3, SM_FLOW_SHEAR_X = 4 };
+ *                        velocity fpar4..6, p = fpar7
+ *  SM_FLOW_AXIAL_PULSE   (cylinder) rho = fpar0, velocity (0, 0, fpar2), p = fpar1 plus a
+ *                        Gaussian of amplitude fpar3 and width fpar7 centred at
+ *                        (r, theta, z) = (fpar4, fpar5, fpar6)
+ *  SM_FLOW_RIGID_ROTATION (cylinder) rho = fpar0, velocity fpar2 e_z x X,
+ *                        p = fpar1 + rho fpar2^2 r^2 / 2 (a steady Euler solution) */
+enum { SM_FLOW_CONSTANT = 0, SM_FLOW_ENTROPY_WAVE = 1, SM_FLOW_MODES = 2, SM_FLOW_POLY_X = 3, SM_FLOW_SHEAR_X = 4,
+       SM_FLOW_AXIAL_PULSE = 5, SM_FLOW_RIGID_ROTATION = 6 };
 
 /* Two structured hexahedral blocks sharing the plane sliding interface x = x1 (Sec. 3.3,
  * first geometry of Fig. sm_meshes_overview).  Static block x in [x0, x1], moving block
  * x in [x1, x2]; both y in [y0, y1] and z in [z0, z1], periodic in y and z.  The faces
  * along the interface are equispaced (Sec. 3.3): nel_static[1..2] must equal
  * nel_moving[1..2].  interface_conforming = 1 couples the two blocks as an ordinary
- * conforming face instead (valid only while the displacement is zero). */
+ * conforming face instead (valid only while the displacement is zero).
+ *
+ * geom SM_GEOM_CYLINDER: the cylindrical sliding interface (Sec. 3.3, a rotor inside the
+ * circle and a stator outside, relative motion a rotation): x0 < x1 < x2 are radii (the
+ * static-block slot holds the rotor, r in [x0, x1]; the moving-block slot the stator, r in
+ * [x1, x2]), [y0, y1] is the periodic angular sector (states crossing its ends turn by the
+ * sector angle), [z0, z1] the periodic axial extent; r = x0 and r = x2 are slip walls.
+ * Curved elements from the analytic map, metric terms in conservative curl form; Euler.
+ * geom SM_GEOM_PLANE_CURVILINEAR: the plane box through the same curvilinear kernels. */
 typedef struct {
   int N;                   /* polynomial degree, 1..7 */
   int geom;                /* SM_GEOM_PLANE */
@@ -86,7 +100,9 @@ typedef struct {
 } sm_mesh_desc;
 
 /* Motion of the moving block: displacement Delta(t) = delta0 + v t along +y (Sec. 4.3,
- * Fig. coordinates).  omega is reserved for rotating geometries and must be 0. */
+ * Fig. coordinates); omega must be 0.  Cylinder: the rotor turns about the z axis by the
+ * angle delta0 + omega t (v must be 0); the stator's displacement seen from the rotor is
+ * minus that angle, in units of the angular face size. */
 typedef struct {
   double v;
   double omega;

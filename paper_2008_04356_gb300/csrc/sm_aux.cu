@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(256) totals_kernel(const MeshDev m, int np, co
     const long long e = g / nn;
     const int nd = (int)(g - e * nn);
     const int i = nd % np, j = (nd / np) % np, k = nd / (np * np);
-    const double wq = elem_jacobian(m, e >= m.Es) * w[i] * w[j] * w[k];
+    const double J = m.geom ? (double)reinterpret_cast<const T*>(m.geo)[(e * 13 + 9) * nn + nd] : elem_jacobian(m, e >= m.Es);
+    const double wq = J * w[i] * w[j] * w[k];
     for (int v = 0; v < 5; ++v) acc[v] += wq * (double)U[(e * 5 + v) * nn + nd];
   }
   for (int v = 0; v < 5; ++v) red[v][threadIdx.x] = acc[v];

@@ -35,6 +35,14 @@ struct StageParams {
   double sig_s, sig_m;
   double mat[8][SM_MAXNP * SM_MAXNP];
   float mat_f[8][SM_MAXNP * SM_MAXNP];
+  // cylindrical interface: cos, sin of the rotor angle phi = -delta, and of the angles
+  // w Theta - phi that carry a stator face seen through w periodic wraps into the rotor's
+  // frame, for w = w0 and w0 + 1 (w0 = floor((-n-1) / n_par), the smallest wrap count)
+  double rot[2];
+  double arot[2][2];
+  long long w0;
+  float rot_f[2];
+  float arot_f[2][2];
 };
 
 // Per-precision constants of the discrete operator, precomputed on the host so that the
@@ -52,7 +60,9 @@ enum {
   MC_MU = 25,         // dynamic viscosity
   MC_K = 26,          // heat conductivity mu gamma R / ((gamma - 1) Pr)
   MC_R = 27,          // gas constant
-  MC_COUNT = 28
+  MC_PCOS = 28,       // cos, sin of the periodic sector angle Theta (cylinder)
+  MC_PSIN = 29,
+  MC_COUNT = 30
 };
 
 // Mesh and physics description passed to kernels by value.
@@ -77,6 +87,15 @@ struct MeshDev {
   // (nb4, nb5, (ix << 1) | blk, iz * ny + iy), neighbour codes as in the element kernel
   // (>= 0 element, -1 weak Dirichlet face, -2 sliding interface).  NULL: computed on the fly.
   const int4* topo;
+  // Curvilinear geometries: 0 plane interface (Cartesian kernels), 1 cylindrical interface
+  // (rotor = block 0 inside, slip walls at the radial ends, periodic angular sector of
+  // angle Theta), 2 the plane box through the curvilinear kernels.
+  int geom;
+  double Theta;
+  // per-node geometry [E][13][NN] in solver precision: Ja^i_n at t = 0 (slot 3 i + n),
+  // J (slot 9), and the grid-velocity factors Ja^i . v^g / |v| of the moving block
+  // (slots 10..12; the grid speed is MC_VG)
+  const void* geo;
 };
 
 template <typename T> struct Prec;
@@ -89,6 +108,8 @@ template <> struct Prec<double> {
   static __device__ __forceinline__ const double* w(const BasisDev* b) { return b->w; }
   static __device__ __forceinline__ const double* x(const BasisDev* b) { return b->x; }
   static __device__ __forceinline__ const double* mat(const StageParams* p, int k) { return p->mat[k]; }
+  static __device__ __forceinline__ const double* rot(const StageParams* p) { return p->rot; }
+  static __device__ __forceinline__ const double* arot(const StageParams* p, int k) { return p->arot[k]; }
 };
 // FP32 mode uses the hardware reciprocal and reciprocal square root (about 1-2 ulp), well
 // inside the 1e-5 relative tolerance of the FP32 path; FP64 mode keeps IEEE division/sqrt.
@@ -101,6 +122,8 @@ template <> struct Prec<float> {
   static __device__ __forceinline__ const float* w(const BasisDev* b) { return b->w_f; }
   static __device__ __forceinline__ const float* x(const BasisDev* b) { return b->x_f; }
   static __device__ __forceinline__ const float* mat(const StageParams* p, int k) { return p->mat_f[k]; }
+  static __device__ __forceinline__ const float* rot(const StageParams* p) { return p->rot_f; }
+  static __device__ __forceinline__ const float* arot(const StageParams* p, int k) { return p->arot_f[k]; }
 };
 
 __device__ __forceinline__ const double* Prec<double>::c(const MeshDev& m) { return m.cd; }
@@ -288,6 +311,101 @@ __device__ __forceinline__ void rotate_from_x(const T R[5], int ax, T U[5]) {
   U[3] = ax == 0 ? R[3] : (ax == 1 ? R[2] : R[1]);
 }
 
+// Flux along a unit normal n minus grid transport vgn * U (curvilinear faces).
+template <typename T>
+__device__ __forceinline__ void normal_flux(const T U[5], const Prim<T>& q, const T n[3], T vgn, T F[5]) {
+  const T un = q.u[0] * n[0] + q.u[1] * n[1] + q.u[2] * n[2];
+  const T w = un - vgn;
+  F[0] = U[0] * w;
+  F[1] = U[1] * w + q.p * n[0];
+  F[2] = U[2] * w + q.p * n[1];
+  F[3] = U[3] * w + q.p * n[2];
+  F[4] = U[4] * w + q.p * un;
+}
+
+// Riemann flux across a face with unit normal n (from L to R), grid normal velocity vgn:
+// the same Rusanov and Roe / Harten-Hyman solvers as riemann_axis, for any direction.
+template <typename T, int RIEM>
+__device__ __forceinline__ void riemann_normal(const T UL[5], const T UR[5], const T n[3], T vgn, T gamma, T F[5]) {
+  const Prim<T> qL = primitives(UL, gamma), qR = primitives(UR, gamma);
+  T FL[5], FR[5];
+  normal_flux(UL, qL, n, vgn, FL);
+  normal_flux(UR, qR, n, vgn, FR);
+  const T unL = qL.u[0] * n[0] + qL.u[1] * n[1] + qL.u[2] * n[2];
+  const T unR = qR.u[0] * n[0] + qR.u[1] * n[1] + qR.u[2] * n[2];
+  const T cL = Prec<T>::sqrt_(gamma * qL.p * qL.ir), cR = Prec<T>::sqrt_(gamma * qR.p * qR.ir);
+  if (RIEM == 0) {
+    const T a = fmax(fabs(unL - vgn) + cL, fabs(unR - vgn) + cR);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * a * (UR[k] - UL[k]);
+    return;
+  }
+  const T sL = Prec<T>::sqrt_(UL[0]), sR = Prec<T>::sqrt_(UR[0]);
+  const T iss = Prec<T>::rcp(sL + sR);
+  T uh[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) uh[d] = (sL * qL.u[d] + sR * qR.u[d]) * iss;
+  const T HL = (UL[4] + qL.p) * qL.ir, HR = (UR[4] + qR.p) * qR.ir;
+  const T Hh = (sL * HL + sR * HR) * iss;
+  const T q2 = uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2];
+  const T ch = Prec<T>::sqrt_((gamma - T(1)) * (Hh - T(0.5) * q2));
+  const T rh = sL * sR;
+  const T unh = uh[0] * n[0] + uh[1] * n[1] + uh[2] * n[2];
+  const T dp = qR.p - qL.p, dr = UR[0] - UL[0], dun = unR - unL;
+  const T ic2 = Prec<T>::rcp(ch * ch);
+  const T a1 = T(0.5) * (dp - rh * ch * dun) * ic2;
+  const T a5 = T(0.5) * (dp + rh * ch * dun) * ic2;
+  const T a2 = dr - dp * ic2;
+  const T l1 = unh - ch - vgn, l2 = unh - vgn, l5 = unh + ch - vgn;
+  T al1 = fabs(l1), al5 = fabs(l5);
+  const T al2 = fabs(l2);
+  const T d1 = fmax(T(0), fmax(l1 - (unL - cL - vgn), (unR - cR - vgn) - l1));
+  if (al1 < d1) al1 = (l1 * l1 + d1 * d1) / (T(2) * d1);
+  const T d5 = fmax(T(0), fmax(l5 - (unL + cL - vgn), (unR + cR - vgn) - l5));
+  if (al5 < d5) al5 = (l5 * l5 + d5 * d5) / (T(2) * d5);
+  const T w1 = al1 * a1, w5 = al5 * a5, w2 = al2 * a2;
+  T du[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) du[d] = qR.u[d] - qL.u[d];
+  T D[5];
+  D[0] = w1 + w2 + w5;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T shear = du[d] - dun * n[d];
+    const T nd = ch * n[d];
+    D[1 + d] = w1 * (uh[d] - nd) + w2 * uh[d] + al2 * rh * shear + w5 * (uh[d] + nd);
+  }
+  const T udu = uh[0] * du[0] + uh[1] * du[1] + uh[2] * du[2];
+  D[4] = w1 * (Hh - unh * ch) + w2 * T(0.5) * q2 + al2 * rh * (udu - unh * dun) + w5 * (Hh + unh * ch);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * D[k];
+}
+
+// Rotation about the z axis by the angle with cosine c and sine s: of the momentum of a
+// state, and of the 15 primitive gradients g[a*5 + p] (a the derivative direction; the
+// velocity components p = 1..3 turn too).
+template <typename T>
+__device__ __forceinline__ void rotate_state_z(T U[5], T c, T s) {
+  const T x = c * U[1] - s * U[2], y = s * U[1] + c * U[2];
+  U[1] = x;
+  U[2] = y;
+}
+template <typename T>
+__device__ __forceinline__ void rotate_grad_z(T g[15], T c, T s) {
+#pragma unroll
+  for (int p = 0; p < 5; ++p) {
+    const T x = c * g[p] - s * g[5 + p], y = s * g[p] + c * g[5 + p];
+    g[p] = x;
+    g[5 + p] = y;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T x = c * g[a * 5 + 1] - s * g[a * 5 + 2], y = s * g[a * 5 + 1] + c * g[a * 5 + 2];
+    g[a * 5 + 1] = x;
+    g[a * 5 + 2] = y;
+  }
+}
+
 // Viscous flux along physical axis a (Sec. 2, Eqs. stress_tensor, heat_flux) from the state
 // and the 15 lifted gradients g[d*5 + c] = d(primitive c)/dx_d, primitives (rho, v, p):
 // (0, tau_1a, tau_2a, tau_3a, tau_aj v_j + k dT/dx_a), tau with Stokes' lambda = -2/3 mu,
@@ -381,8 +499,19 @@ __device__ __forceinline__ void flow_state(const MeshDev& m, double x, double y,
     double xs = x - f[4] * t;
     P[0] = f[0] + xs * (f[1] + xs * (f[2] + xs * f[3]));
     P[1] = f[4]; P[2] = f[5]; P[3] = f[6]; P[4] = f[7];
-  } else {
+  } else if (m.flow == 4) {
     P[0] = f[0]; P[1] = 0.0; P[2] = 0.0; P[3] = f[2] + x * (f[3] + x * f[4]); P[4] = f[1];
+  } else if (m.flow == 5) {
+    // axial stream (0, 0, f2) with a Gaussian pressure pulse (amplitude f3, width f7) at
+    // (r, theta, z) = (f4, f5, f6)
+    const double xc = f[4] * cos(f[5]), yc = f[4] * sin(f[5]), zc = f[6];
+    const double d2 = (x - xc) * (x - xc) + (y - yc) * (y - yc) + (z - zc) * (z - zc);
+    P[0] = f[0]; P[1] = 0.0; P[2] = 0.0; P[3] = f[2];
+    P[4] = f[1] + (boundary ? 0.0 : f[3] * exp(-d2 / (2.0 * f[7] * f[7])));
+  } else {
+    // rigid rotation with angular speed f2 about the z axis
+    P[0] = f[0]; P[1] = -f[2] * y; P[2] = f[2] * x; P[3] = 0.0;
+    P[4] = f[1] + 0.5 * f[0] * f[2] * f[2] * (x * x + y * y);
   }
   U[0] = P[0];
   U[1] = P[0] * P[1];
@@ -391,12 +520,24 @@ __device__ __forceinline__ void flow_state(const MeshDev& m, double x, double y,
   U[4] = P[4] / (m.gamma - 1.0) + 0.5 * P[0] * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
 }
 
-// Physical position of node (i, j, k) of element p; the moving block is shifted by delta.
+// Physical position of node (i, j, k) of element p; the moving block is shifted by delta
+// (cylinder: the rotor, block 0, is turned by phi = -delta).
 __device__ __forceinline__ void node_position(const MeshDev& m, const ElemPos& p, int i, int j, int k,
                                               double delta, double X[3]) {
   const double* xi = m.basis->x;
   double hx = p.blk ? m.hx1 : m.hx0;
   double xlo = p.blk ? m.x1 : m.x0;
+  if (m.geom == 1) {
+    const double r = xlo + p.ix * hx + (xi[k] + 1.0) * 0.5 * hx;
+    const double th = m.y0 + p.iy * m.hy + (xi[i] + 1.0) * 0.5 * m.hy;
+    const double a0 = r * cos(th), a1 = r * sin(th);
+    double c = 1.0, s = 0.0;
+    if (p.blk == 0) sincos(-delta, &s, &c);
+    X[0] = c * a0 - s * a1;
+    X[1] = s * a0 + c * a1;
+    X[2] = m.z0 + p.iz * m.hz + (xi[j] + 1.0) * 0.5 * m.hz;
+    return;
+  }
   X[0] = xlo + p.ix * hx + (xi[k] + 1.0) * 0.5 * hx;
   X[1] = m.y0 + p.iy * m.hy + (xi[i] + 1.0) * 0.5 * m.hy + (p.blk ? delta : 0.0);
   X[2] = m.z0 + p.iz * m.hz + (xi[j] + 1.0) * 0.5 * m.hz;

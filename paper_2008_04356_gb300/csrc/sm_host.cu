@@ -159,6 +159,107 @@ const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 136
 const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
                         2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
 
+// Curvilinear geometry at t = 0 for MeshDev::geom 1 and 2: node coordinates of the analytic
+// map (cylinder: (r cos theta, r sin theta, z) with xi^1 -> theta, xi^2 -> z, xi^3 -> r;
+// plane: xi^1 -> y, xi^2 -> z, xi^3 -> x; relative to the element's centre), the Jacobian
+// J = a_1 . (a_2 x a_3) with
+// a_d = D_d X, and the metric terms in Kopriva's conservative curl form, antisymmetrised,
+//   Ja^i_n = -1/2 (D_j V_k - D_k V_j),  V_k = X_l D_k X_m - X_m D_k X_l,
+// (i, j, k) and (n, m, l) cyclic: the discrete metric identities sum_i D_i Ja^i_n = 0 hold
+// and the form commutes with a rotation of the mesh.  Per node 13 values: Ja^i_n (3 i + n),
+// J (9), Ja^i . v^g / |v| of the moving block (10 + i; the rotor's v^g / omega = e_z x X,
+// the plane's v^g / v = e_y).
+void curvilinear_geometry(const MeshDev& m, const BasisDev& b, int N, std::vector<double>& geo) {
+  const int np = N + 1, nn = np * np * np;
+  double D[SM_MAXNP][SM_MAXNP];
+  for (int i = 0; i < np; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < np; ++j)
+      if (j != i) {
+        D[i][j] = (b.lam[j] / b.lam[i]) / (b.x[i] - b.x[j]);
+        diag -= D[i][j];
+      }
+    D[i][i] = diag;
+  }
+  auto idx = [np](int i, int j, int k) { return i + np * (j + np * k); };
+  // derivative along reference direction d of nodal data f
+  auto deriv = [&](int d, const double* f, double* out) {
+    for (int k = 0; k < np; ++k)
+      for (int j = 0; j < np; ++j)
+        for (int i = 0; i < np; ++i) {
+          double acc = 0.0;
+          for (int l = 0; l < np; ++l) {
+            const int row = d == 0 ? i : (d == 1 ? j : k);
+            const int src = d == 0 ? idx(l, j, k) : (d == 1 ? idx(i, l, k) : idx(i, j, l));
+            acc += D[row][l] * f[src];
+          }
+          out[idx(i, j, k)] = acc;
+        }
+  };
+  geo.assign((size_t)m.E * 13 * nn, 0.0);
+  std::vector<double> X(3 * nn), dX(9 * nn), V(3 * nn), T1(nn), T2(nn);
+  for (long long e = 0; e < m.E; ++e) {
+    const ElemPos p = decode_elem(m, e);
+    const double h3 = p.blk ? m.hx1 : m.hx0, lo3 = p.blk ? m.x1 : m.x0;
+    for (int k = 0; k < np; ++k)
+      for (int j = 0; j < np; ++j)
+        for (int i = 0; i < np; ++i) {
+          const double s1 = m.y0 + p.iy * m.hy + (b.x[i] + 1.0) * 0.5 * m.hy;
+          const double s2 = m.z0 + p.iz * m.hz + (b.x[j] + 1.0) * 0.5 * m.hz;
+          const double s3 = lo3 + p.ix * h3 + (b.x[k] + 1.0) * 0.5 * h3;
+          const int q = idx(i, j, k);
+          if (m.geom == 1) {
+            X[q] = s3 * cos(s1);
+            X[nn + q] = s3 * sin(s1);
+          } else {
+            X[q] = s3;
+            X[nn + q] = s1;
+          }
+          X[2 * nn + q] = s2;
+        }
+    // the curl form is translation invariant: evaluate it on coordinates relative to the
+    // element's centre so that its products do not cancel digits
+    double Xc[3];
+    {
+      const double s1 = m.y0 + (p.iy + 0.5) * m.hy, s2 = m.z0 + (p.iz + 0.5) * m.hz, s3 = lo3 + (p.ix + 0.5) * h3;
+      Xc[0] = m.geom == 1 ? s3 * cos(s1) : s3;
+      Xc[1] = m.geom == 1 ? s3 * sin(s1) : s1;
+      Xc[2] = s2;
+    }
+    std::vector<double> Xg(X);   // global coordinates for the grid-velocity factors
+    for (int c = 0; c < 3; ++c)
+      for (int q = 0; q < nn; ++q) X[c * nn + q] -= Xc[c];
+    for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < 3; ++c) deriv(d, &X[c * nn], &dX[(d * 3 + c) * nn]);
+    double* g = &geo[(size_t)e * 13 * nn];
+    for (int q = 0; q < nn; ++q) {
+      const double* a1 = &dX[0]; const double* a2 = &dX[3 * nn]; const double* a3 = &dX[6 * nn];
+      const double c0 = a2[nn + q] * a3[2 * nn + q] - a2[2 * nn + q] * a3[nn + q];
+      const double c1 = a2[2 * nn + q] * a3[q] - a2[q] * a3[2 * nn + q];
+      const double c2 = a2[q] * a3[nn + q] - a2[nn + q] * a3[q];
+      g[9 * nn + q] = a1[q] * c0 + a1[nn + q] * c1 + a1[2 * nn + q] * c2;
+    }
+    for (int n = 0; n < 3; ++n) {
+      const int mm = (n + 1) % 3, l = (n + 2) % 3;
+      for (int k = 0; k < 3; ++k)
+        for (int q = 0; q < nn; ++q)
+          V[k * nn + q] = X[l * nn + q] * dX[(k * 3 + mm) * nn + q] - X[mm * nn + q] * dX[(k * 3 + l) * nn + q];
+      for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        deriv(j, &V[k * nn], T1.data());
+        deriv(k, &V[j * nn], T2.data());
+        for (int q = 0; q < nn; ++q) g[(3 * i + n) * nn + q] = -0.5 * (T1[q] - T2[q]);
+      }
+    }
+    const bool moving = m.geom == 1 ? p.blk == 0 : p.blk == 1;
+    if (moving)
+      for (int i = 0; i < 3; ++i)
+        for (int q = 0; q < nn; ++q)
+          g[(10 + i) * nn + q] = m.geom == 1 ? -Xg[nn + q] * g[(3 * i) * nn + q] + Xg[q] * g[(3 * i + 1) * nn + q]
+                                            : g[(3 * i + 1) * nn + q];
+  }
+}
+
 // Fills the per-precision constant block of the kernels (FP64 values, rounded once for FP32).
 void fill_constants(MeshDev& m, const BasisDev& b, const double* fpar) {
   double c[MC_COUNT] = {0};
@@ -190,6 +291,8 @@ void fill_constants(MeshDev& m, const BasisDev& b, const double* fpar) {
   c[MC_MU] = m.mu;
   c[MC_R] = m.Rgas;
   c[MC_K] = m.Pr > 0.0 ? m.mu * m.gamma * m.Rgas / ((m.gamma - 1.0) * m.Pr) : 0.0;
+  c[MC_PCOS] = cos(m.Theta);
+  c[MC_PSIN] = sin(m.Theta);
   for (int k = 0; k < MC_COUNT; ++k) {
     m.cd[k] = c[k];
     m.cf[k] = (float)c[k];
@@ -224,6 +327,10 @@ cudaError_t ensure_dhat_constants() {
   if ((e = upload_dhat_batch(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_ns_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_ns_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_curved_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_curved_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_curved_ns_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_curved_ns_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   g_dhat_done[dev] = true;
   return cudaSuccess;
 }
@@ -259,6 +366,7 @@ struct sm_solver {
   void* Ts = nullptr;           // interface traces of the current state (Euler, sliding interface)
   void* Tm = nullptr;
   bool traces_ok = false;       // Ts / Tm hold the traces of U[cur]
+  void* geo = nullptr;          // curvilinear geometry per node (MeshDev::geom != 0)
   int red_blocks = 0;
   int cur = 0;
   double t_host = 0.0;
@@ -278,6 +386,17 @@ cudaError_t enqueue_flux_inputs(sm_solver* s, const void* dU, void* Fs, void* Fm
                                 bool from_traces = false) {
   cudaError_t e = cudaSuccess;
   const bool sliding = !s->desc.interface_conforming;
+  if (is_ns(s) && s->m.geom != 0) {
+    const bool f64 = s->prec == SM_FP64;
+    if (sliding && (e = f64 ? launch_curved_interface_lift_f64(s->N, s->m, s->sp, dU, s->Ls, s->Lm, st)
+                            : launch_curved_interface_lift_f32(s->N, s->m, s->sp, dU, s->Ls, s->Lm, st)) != cudaSuccess)
+      return e;
+    e = f64 ? launch_curved_lift_f64(s->N, s->m, s->sp, dU, s->Gr, s->Ls, s->Lm, st)
+            : launch_curved_lift_f32(s->N, s->m, s->sp, dU, s->Gr, s->Ls, s->Lm, st);
+    if (e != cudaSuccess || !sliding) return e;
+    return f64 ? launch_curved_interface_ns_f64(s->N, s->desc.riemann, s->m, s->sp, dU, s->Gr, Fs, Fm, st)
+               : launch_curved_interface_ns_f32(s->N, s->desc.riemann, s->m, s->sp, dU, s->Gr, Fs, Fm, st);
+  }
   if (is_ns(s)) {
     if (sliding && (e = launch_interface_lift(s->N, s->prec, s->m, s->sp, dU, s->Ls, s->Lm, st)) != cudaSuccess) return e;
     e = s->prec == SM_FP64 ? launch_lift_f64(s->N, s->m, s->sp, dU, s->Gr, s->Ls, s->Lm, st)
@@ -286,6 +405,9 @@ cudaError_t enqueue_flux_inputs(sm_solver* s, const void* dU, void* Fs, void* Fm
     if (sliding) e = launch_interface_ns(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, s->Gr, Fs, Fm, st);
     return e;
   }
+  if (sliding && s->m.geom != 0)
+    return s->prec == SM_FP64 ? launch_curved_interface_f64(s->N, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st)
+                              : launch_curved_interface_f32(s->N, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st);
   if (sliding)
     e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st, from_traces ? s->Ts : nullptr,
                          from_traces ? s->Tm : nullptr);
@@ -311,6 +433,14 @@ cudaError_t enqueue_rhs_parts(sm_solver* s, double t, const void* dU, void* Fs, 
 
 cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a0, cudaStream_t st) {
   ElemArgs a = a0;
+  if (s->m.geom != 0 && is_ns(s)) {
+    a.Gr = s->Gr;
+    return s->prec == SM_FP64 ? launch_curved_element_ns_f64(s->N, s->desc.riemann, mode, a, st)
+                              : launch_curved_element_ns_f32(s->N, s->desc.riemann, mode, a, st);
+  }
+  if (s->m.geom != 0)
+    return s->prec == SM_FP64 ? launch_curved_element_f64(s->N, s->desc.riemann, mode, a, st)
+                              : launch_curved_element_f32(s->N, s->desc.riemann, mode, a, st);
   if (is_ns(s)) {
     a.Gr = s->Gr;
     return s->prec == SM_FP64 ? launch_element_ns_f64(s->N, s->desc.riemann, mode, a, st)
@@ -365,7 +495,7 @@ void free_solver(sm_solver* s) {
   clear_graphs(s);
   if (s->cap) cudaStreamDestroy(s->cap);
   void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->t_d, s->red_d, s->topo_d,
-                  s->Gr, s->Ls, s->Lm, s->Ts, s->Tm};
+                  s->Gr, s->Ls, s->Lm, s->Ts, s->Tm, s->geo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -374,7 +504,16 @@ void free_solver(sm_solver* s) {
 int valid_desc(const sm_mesh_desc* d) {
   if (!d) return fail(SM_ERR_ARG, "desc is NULL");
   if (d->N < 1 || d->N > 7) return fail(SM_ERR_UNSUPPORTED, "N must be in 1..7");
-  if (d->geom != SM_GEOM_PLANE) return fail(SM_ERR_UNSUPPORTED, "only the plane interface geometry is built");
+  if (d->geom != SM_GEOM_PLANE && d->geom != SM_GEOM_CYLINDER && d->geom != SM_GEOM_PLANE_CURVILINEAR)
+    return fail(SM_ERR_UNSUPPORTED, "unknown interface geometry");
+  if (d->geom == SM_GEOM_CYLINDER) {
+    if (!(d->x0 > 0.0)) return fail(SM_ERR_ARG, "cylinder radii must be positive");
+    if (!(d->y1 - d->y0 <= 2.0 * M_PI + 1e-12)) return fail(SM_ERR_ARG, "the angular sector exceeds 2 pi");
+    if (d->flow != SM_FLOW_CONSTANT && d->flow != SM_FLOW_AXIAL_PULSE && d->flow != SM_FLOW_RIGID_ROTATION)
+      return fail(SM_ERR_ARG, "cylinder flows: constant, axial pulse, rigid rotation");
+  } else if (d->flow > SM_FLOW_SHEAR_X) {
+    return fail(SM_ERR_ARG, "the axial pulse and rigid rotation flows need the cylinder");
+  }
   for (int k = 0; k < 3; ++k)
     if (d->nel_static[k] < 1 || d->nel_moving[k] < 1) return fail(SM_ERR_ARG, "element counts must be >= 1");
   if (d->nel_static[1] != d->nel_moving[1] || d->nel_static[2] != d->nel_moving[2])
@@ -383,7 +522,7 @@ int valid_desc(const sm_mesh_desc* d) {
   if (!(d->gamma > 1.0)) return fail(SM_ERR_ARG, "gamma must exceed 1");
   if (d->riemann != SM_RUSANOV && d->riemann != SM_ROE_HH) return fail(SM_ERR_ARG, "unknown Riemann solver");
   if (d->precision != SM_FP64 && d->precision != SM_FP32) return fail(SM_ERR_ARG, "unknown precision");
-  if (d->flow < 0 || d->flow > 4) return fail(SM_ERR_ARG, "unknown flow");
+  if (d->flow < 0 || d->flow > SM_FLOW_RIGID_ROTATION) return fail(SM_ERR_ARG, "unknown flow");
   if (d->physics != SM_EULER && d->physics != SM_NAVIER_STOKES) return fail(SM_ERR_ARG, "unknown physics");
   if (d->physics == SM_NAVIER_STOKES && !(d->mu >= 0.0 && d->Pr > 0.0 && d->Rgas > 0.0))
     return fail(SM_ERR_ARG, "Navier-Stokes needs mu >= 0, Pr > 0, Rgas > 0");
@@ -451,6 +590,8 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   m.mu = desc->mu;
   m.Pr = desc->Pr;
   m.Rgas = desc->Rgas;
+  m.geom = desc->geom;
+  m.Theta = desc->y1 - desc->y0;
   for (int k = 0; k < 16; ++k) m.fpar[k] = desc->fpar[k];
   s->nstate = m.E * 5 * s->nn;
   s->nface_vals = (long long)m.ny * m.nz * 5 * s->np * s->np;
@@ -476,13 +617,16 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   SM_ALLOC(s->red_d, sizeof(double) * (s->red_blocks * 5 + 15));
   SM_ALLOC(s->topo_d, sizeof(int4) * 2 * (size_t)m.E);
   if (desc->physics == SM_NAVIER_STOKES) {
+    // lifting values per interface face node: 5 on the plane (normal +x), 15 (q* N_a) curved
+    const size_t lbytes = desc->geom == SM_GEOM_PLANE ? fbytes : 3 * fbytes;
     SM_ALLOC(s->Gr, (size_t)m.E * 15 * s->nn * s->sb);
-    SM_ALLOC(s->Ls, fbytes);
-    SM_ALLOC(s->Lm, fbytes);
-  } else if (!desc->interface_conforming) {
+    SM_ALLOC(s->Ls, lbytes);
+    SM_ALLOC(s->Lm, lbytes);
+  } else if (!desc->interface_conforming && desc->geom == SM_GEOM_PLANE) {
     SM_ALLOC(s->Ts, fbytes);
     SM_ALLOC(s->Tm, fbytes);
   }
+  if (desc->geom != SM_GEOM_PLANE) SM_ALLOC(s->geo, (size_t)m.E * 13 * s->nn * s->sb);
 #undef SM_ALLOC
   m.basis = s->basis_d;
   m.modes = s->modes_d;
@@ -502,7 +646,20 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
     topo[2 * e + 1] = make_int4(nb[4], nb[5], (p.ix << 1) | p.blk, p.iz * m.ny + p.iy);
   }
   const char* what = nullptr;
-  if ((e = cudaMemcpy(s->basis_d, &s->basis_h, sizeof(BasisDev), cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload basis";
+  if (s->geo) {
+    std::vector<double> g;
+    curvilinear_geometry(m, s->basis_h, s->N, g);
+    if (s->prec == SM_FP64) {
+      e = cudaMemcpy(s->geo, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float> gf(g.begin(), g.end());
+      e = cudaMemcpy(s->geo, gf.data(), sizeof(float) * gf.size(), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) what = "upload geometry";
+    m.geo = s->geo;
+  }
+  if (what) {
+  } else if ((e = cudaMemcpy(s->basis_d, &s->basis_h, sizeof(BasisDev), cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload basis";
   else if ((e = cudaMemcpy(s->modes_d, &desc->modes[0][0][0], sizeof(double) * 160, cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload modes";
   else if ((e = cudaMemcpy(s->topo_d, topo.data(), sizeof(int4) * topo.size(), cudaMemcpyHostToDevice)) != cudaSuccess) what = "upload topology";
   else if ((e = cudaMemset(s->G, 0, sbytes)) != cudaSuccess) what = "clear G";
@@ -513,6 +670,12 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   else if ((e = (s->prec == SM_FP64 ? prepare_element_f64(s->N) : prepare_element_f32(s->N))) != cudaSuccess) what = "element kernel attributes";
   else if ((e = ensure_dhat_constants()) != cudaSuccess) what = "derivative constants";
   else if ((e = prepare_interface(s->N, s->prec)) != cudaSuccess) what = "interface kernel attributes";
+  else if (desc->geom != SM_GEOM_PLANE &&
+           (e = (s->prec == SM_FP64 ? prepare_curved_f64(s->N) : prepare_curved_f32(s->N))) != cudaSuccess)
+    what = "curvilinear kernel attributes";
+  else if (desc->geom != SM_GEOM_PLANE && desc->physics == SM_NAVIER_STOKES &&
+           (e = (s->prec == SM_FP64 ? prepare_curved_ns_f64(s->N) : prepare_curved_ns_f32(s->N))) != cudaSuccess)
+    what = "curvilinear Navier-Stokes kernel attributes";
   else if (desc->physics == SM_NAVIER_STOKES &&
            ((e = (s->prec == SM_FP64 ? prepare_ns_f64(s->N) : prepare_ns_f32(s->N))) != cudaSuccess ||
             (e = prepare_interface_ns(s->N, s->prec)) != cudaSuccess)) what = "Navier-Stokes kernel attributes";
@@ -528,15 +691,21 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
 
 int sm_set_motion(sm_solver* s, const sm_motion* mo) {
   if (!s || !mo) return fail(SM_ERR_ARG, "NULL argument");
-  if (mo->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");
-  if (!std::isfinite(mo->v) || !std::isfinite(mo->delta0)) return fail(SM_ERR_ARG, "non-finite motion");
-  if (s->desc.interface_conforming && (mo->v != 0.0 || mo->delta0 != 0.0))
+  const bool cyl = s->desc.geom == SM_GEOM_CYLINDER;
+  if (!cyl && mo->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");
+  if (cyl && mo->v != 0.0) return fail(SM_ERR_UNSUPPORTED, "the cylinder's rotor rotates (omega), it does not translate");
+  if (!std::isfinite(mo->v) || !std::isfinite(mo->omega) || !std::isfinite(mo->delta0))
+    return fail(SM_ERR_ARG, "non-finite motion");
+  const double speed = cyl ? mo->omega : mo->v;
+  if (s->desc.interface_conforming && (speed != 0.0 || mo->delta0 != 0.0))
     return fail(SM_ERR_ARG, "a conforming interface cannot move");
   s->motion = *mo;
-  s->m.v = mo->v;
-  s->m.delta0 = mo->delta0;
-  s->m.cd[MC_VG] = mo->v;
-  s->m.cf[MC_VG] = (float)mo->v;
+  // the mapper takes the displacement of block 1 relative to block 0: the rotor (block 0)
+  // turning by phi = delta0 + omega t displaces the stator by -phi
+  s->m.v = cyl ? -mo->omega : mo->v;
+  s->m.delta0 = cyl ? -mo->delta0 : mo->delta0;
+  s->m.cd[MC_VG] = speed;
+  s->m.cf[MC_VG] = (float)speed;
   clear_graphs(s);
   return SM_OK;
 }
@@ -608,6 +777,15 @@ int sm_gradients(sm_solver* s, double t, const void* dU, void* dGrad, void* stre
   if (!std::isfinite(t)) return fail(SM_ERR_ARG, "non-finite time");
   cudaStream_t st = (cudaStream_t)stream;
   SM_CK(launch_stage_params(s->m, s->np, s->sp, s->t_d, t, 0.0, 0.0, 0, st), "stage parameters");
+  if (s->m.geom != 0) {
+    const bool f64 = s->prec == SM_FP64;
+    if (!s->desc.interface_conforming)
+      SM_CK(f64 ? launch_curved_interface_lift_f64(s->N, s->m, s->sp, dU, s->Ls, s->Lm, st)
+                : launch_curved_interface_lift_f32(s->N, s->m, s->sp, dU, s->Ls, s->Lm, st), "interface lifting");
+    SM_CK(f64 ? launch_curved_lift_f64(s->N, s->m, s->sp, dU, dGrad, s->Ls, s->Lm, st)
+              : launch_curved_lift_f32(s->N, s->m, s->sp, dU, dGrad, s->Ls, s->Lm, st), "lifting");
+    return SM_OK;
+  }
   if (!s->desc.interface_conforming)
     SM_CK(launch_interface_lift(s->N, s->prec, s->m, s->sp, dU, s->Ls, s->Lm, st), "interface lifting");
   SM_CK(s->prec == SM_FP64 ? launch_lift_f64(s->N, s->m, s->sp, dU, dGrad, s->Ls, s->Lm, st)
@@ -832,6 +1010,7 @@ extern "C" int sm_batch_create(sm_solver* const* solvers, const double* dt, int 
     if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return fail(SM_ERR_ARG, "batch time steps must be positive");
     if (solvers[i]->prec != SM_FP32) return fail(SM_ERR_UNSUPPORTED, "batched kernels are FP32; step FP64 solvers with sm_step");
     if (solvers[i]->desc.physics != SM_EULER) return fail(SM_ERR_UNSUPPORTED, "batched kernels are Euler; step Navier-Stokes solvers with sm_step");
+    if (solvers[i]->desc.geom != SM_GEOM_PLANE) return fail(SM_ERR_UNSUPPORTED, "batched kernels are for the plane interface");
   }
   sm_batch* b = new (std::nothrow) sm_batch();
   if (!b) return fail(SM_ERR_OOM, "host allocation");
@@ -1083,6 +1262,7 @@ extern "C" int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, 
   int rc = valid_desc(desc);
   if (rc != SM_OK) return rc;
   if (desc->physics != SM_EULER) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes the Euler operator only");
+  if (desc->geom != SM_GEOM_PLANE) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes the plane interface only");
   if (!motion || !dU || !dUt) return fail(SM_ERR_ARG, "NULL argument");
   if (dU == dUt) return fail(SM_ERR_ARG, "dU and dUt must not overlap");
   if (motion->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");

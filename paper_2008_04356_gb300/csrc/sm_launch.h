@@ -38,6 +38,21 @@ cudaError_t prepare_curved_f32(int N);
 cudaError_t prepare_curved_f64(int N);
 cudaError_t upload_dhat_curved_f32(const float* f, const double* d);
 cudaError_t upload_dhat_curved_f64(const float* f, const double* d);
+// sm_curved_ns_f32.cu / sm_curved_ns_f64.cu: curvilinear Navier-Stokes (lifting values per
+// interface face node: 15, a * 5 + c)
+#define SM_CURVED_NS_DECL(S)                                                                                       \
+  cudaError_t launch_curved_element_ns_##S(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);     \
+  cudaError_t launch_curved_lift_##S(int N, const MeshDev& m, const StageParams* sp, const void* U, void* Gr,     \
+                                     const void* Ls, const void* Lm, cudaStream_t st);                            \
+  cudaError_t launch_curved_interface_lift_##S(int N, const MeshDev& m, const StageParams* sp, const void* U,     \
+                                               void* Ls, void* Lm, cudaStream_t st);                              \
+  cudaError_t launch_curved_interface_ns_##S(int N, int riemann, const MeshDev& m, const StageParams* sp,         \
+                                             const void* U, const void* Gr, void* Fs, void* Fm, cudaStream_t st); \
+  cudaError_t prepare_curved_ns_##S(int N);                                                                        \
+  cudaError_t upload_dhat_curved_ns_##S(const float* f, const double* d);
+SM_CURVED_NS_DECL(f32)
+SM_CURVED_NS_DECL(f64)
+#undef SM_CURVED_NS_DECL
 
 // sm_elem_f32.cu / sm_elem_f64.cu
 cudaError_t launch_element_f32(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);

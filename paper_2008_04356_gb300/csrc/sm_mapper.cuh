@@ -96,6 +96,24 @@ __device__ __forceinline__ void stage_params_body(const MeshDev& m, int np, Stag
     sp->sig_m = __dsub_rn(1.0, two_s);
     s_sig[0] = sp->sig_s;
     s_sig[1] = sp->sig_m;
+    if (m.geom == 1) {
+      // the rotor turns by phi = -delta; stator faces seen through w wraps: w Theta - phi
+      const double phi = -delta;
+      double c0, s0;
+      sincos(phi, &s0, &c0);
+      sp->rot[0] = c0; sp->rot[1] = s0;
+      sp->rot_f[0] = (float)c0; sp->rot_f[1] = (float)s0;
+      long long a = -n - 1, q = a / m.ny;
+      if (a % m.ny != 0 && a < 0) q -= 1;
+      sp->w0 = q;
+      for (int k = 0; k < 2; ++k) {
+        const double ang = __dsub_rn(__dmul_rn((double)(q + k), m.Theta), phi);
+        double ck, sk;
+        sincos(ang, &sk, &ck);
+        sp->arot[k][0] = ck; sp->arot[k][1] = sk;
+        sp->arot_f[k][0] = (float)ck; sp->arot_f[k][1] = (float)sk;
+      }
+    }
     if (mode == 2) *t_dev = __dadd_rn(*t_dev, dt);
   }
   __syncthreads();

@@ -3,9 +3,10 @@
 // A worker thread owns the device work.  Requests wait in arrival order; a request is
 // admitted when a slot is free and its device memory fits in the budget next to the
 // resident solves.  Every iteration advances all resident solves together by the same
-// number of RK steps (FP32 solves through one batch with shared launches, FP64 solves one
-// at a time), at most a few steps so that new arrivals join quickly, then retires the
-// finished ones and frees their memory.  Built on the library's own C-ABI.
+// number of RK steps (FP32 Euler plane-interface solves through one batch with shared
+// launches, the others one at a time), at most a few steps so that new arrivals join
+// quickly, then retires the finished ones and frees their memory.  Built on the library's
+// own C-ABI.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -42,7 +43,13 @@ size_t request_bytes(const sm_mesh_desc& d) {
   const size_t faces = (size_t)d.nel_static[1] * d.nel_static[2];
   size_t b = 3 * E * nn * 5 * sb + 2 * faces * 5 * np * np * sb + 32 * E + (64 << 10);
   if (d.physics == SM_NAVIER_STOKES) b += E * nn * 15 * sb + 2 * faces * 5 * np * np * sb;   // gradients, lifting
+  if (d.geom != SM_GEOM_PLANE) b += E * nn * 13 * sb;                                          // curvilinear geometry
   return b;
+}
+
+// FP32 Euler solves on the plane interface share the batched kernels; the others step alone
+bool batchable(const sm_mesh_desc& d) {
+  return d.precision == SM_FP32 && d.physics == SM_EULER && d.geom == SM_GEOM_PLANE;
 }
 
 }  // namespace
@@ -152,7 +159,7 @@ void sm_server::run() {
       std::vector<sm_solver*> sol;
       std::vector<double> dts;
       for (Job* j : active)
-        if (j->req.desc.precision == SM_FP32 && j->req.desc.physics == SM_EULER) {
+        if (batchable(j->req.desc)) {
           sol.push_back(j->solver);
           dts.push_back(j->req.dt);
         }
@@ -175,7 +182,7 @@ void sm_server::run() {
     if (k > 0) {
       if (batch) rc = sm_batch_step(batch, k, (void*)st);
       for (Job* j : active)
-        if (rc == SM_OK && (j->req.desc.precision == SM_FP64 || j->req.desc.physics != SM_EULER))
+        if (rc == SM_OK && !batchable(j->req.desc))
           rc = sm_step(j->solver, j->req.dt, k, (void*)st);
       if (rc == SM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SM_ERR_CUDA;
       std::lock_guard<std::mutex> lk(mu);

@@ -135,7 +135,7 @@ def _stream(stream):
 
 def mesh_desc(p: synth.Problem) -> SmMeshDesc:
     d = SmMeshDesc()
-    d.N, d.geom = p.N, 0
+    d.N, d.geom = p.N, int(getattr(p, "geom", 0))
     for k in range(3):
         d.nel_static[k], d.nel_moving[k] = int(p.nel_s[k]), int(p.nel_m[k])
     for name in ("x0", "x1", "x2", "y0", "y1", "z0", "z1", "gamma"):
@@ -218,7 +218,12 @@ class Solver:
             pass
 
     def set_motion(self, v: float, delta0: float = 0.0):
-        mo = SmMotion(float(v), 0.0, float(delta0))
+        """Plane: block speed v and initial displacement; cylinder: rotor angular speed v
+        and initial angle delta0."""
+        if getattr(self.problem, "geom", 0) == synth.GEOM_CYLINDER:
+            mo = SmMotion(0.0, float(v), float(delta0))
+        else:
+            mo = SmMotion(float(v), 0.0, float(delta0))
         check(lib().sm_set_motion(self.h, C.byref(mo)), "sm_set_motion")
 
     def init_state(self, stream=None):
@@ -342,7 +347,10 @@ class Server:
     def submit(self, problem: synth.Problem, dt: float, nsteps: int, keep_state: bool = False) -> int:
         req = SmRequest()
         req.desc = mesh_desc(problem)
-        req.motion = SmMotion(float(problem.v), 0.0, float(problem.delta0))
+        if getattr(problem, "geom", 0) == synth.GEOM_CYLINDER:
+            req.motion = SmMotion(0.0, float(problem.v), float(problem.delta0))
+        else:
+            req.motion = SmMotion(float(problem.v), 0.0, float(problem.delta0))
         req.dt, req.nsteps, req.keep_state = float(dt), int(nsteps), int(keep_state)
         t = C.c_uint64()
         check(lib().sm_submit(self.h, C.byref(req), C.byref(t)), "sm_submit")

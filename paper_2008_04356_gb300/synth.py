@@ -213,6 +213,12 @@ def wave_speed_bounds(p: Problem):
         a = np.abs(p.modes_array()[:, :, 0]).sum(axis=1)
         rho_min, pmax = f[0] - a[0], f[4] + a[4]
         vel = [abs(f[1]) + a[1], abs(f[2]) + a[2], abs(f[3]) + a[3]]
+    elif p.flow == FLOW_AXIAL_PULSE:
+        rho_min, pmax, vel = f[0], f[1] + abs(f[3]), [0.0, 0.0, abs(f[2])]
+    elif p.flow == FLOW_RIGID_ROTATION:
+        rmax = max(abs(p.x0), abs(p.x2))
+        w = abs(f[2]) * rmax
+        rho_min, pmax, vel = f[0], f[1] + 0.5 * f[0] * w * w, [w, w, 0.0]
     elif p.flow == FLOW_POLY_X:
         c = f[:4]
         rho_min = min(c[0] + x * (c[1] + x * (c[2] + x * c[3])) for x in np.linspace(p.x0 - 1, p.x2, 401))
@@ -228,6 +234,21 @@ def cfl_dt(p: Problem, cfl: float = 0.9) -> float:
     """dt = CFL / ((2N+1) * sum_d (|v_d - v^g_d| + c) / h_d), the largest over both blocks
     (grid velocity 0 in the static block, v along y in the moving one)."""
     vel, c = wave_speed_bounds(p)
+    if p.geom == GEOM_CYLINDER:
+        # radial, angular (arc length at the inner radius) and axial sizes; the rotor's grid
+        # speed is omega r
+        ha = p.x0 * (p.y1 - p.y0) / p.nel_s[1]
+        hz = (p.z1 - p.z0) / p.nel_s[2]
+        vmax = math.sqrt(vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)
+        rate, hmin = 0.0, min(ha, hz)
+        for hr, vg in (((p.x1 - p.x0) / p.nel_s[0], abs(p.v) * p.x1), ((p.x2 - p.x1) / p.nel_m[0], 0.0)):
+            rate = max(rate, (vmax + c) / hr + (vmax + vg + c) / ha + (vmax + c) / hz)
+            hmin = min(hmin, hr)
+        dt = cfl / ((2 * p.N + 1) * rate)
+        if p.physics == NAVIER_STOKES and p.mu > 0.0:
+            nu = p.mu / p.fpar[0] * max(4.0 / 3.0, p.gamma / p.Pr)
+            dt = min(dt, 0.5 * hmin * hmin / ((2 * p.N + 1) ** 2 * nu))
+        return dt
     hy = (p.y1 - p.y0) / p.nel_s[1]
     hz = (p.z1 - p.z0) / p.nel_s[2]
     rate, hmin = 0.0, min(hy, hz)
