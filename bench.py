@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=256, help="elements along z (256 = the full workload)")
-    ap.add_argument("--workload", choices=["interface-heavy", "serving"], default="interface-heavy")
+    ap.add_argument("--workload", choices=["interface-heavy", "serving", "cylinder"], default="interface-heavy")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32", help="cylinder workload state precision")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--serve-steps", type=int, default=100)
     ap.add_argument("--load", type=float, default=0.8, help="offered load as a fraction of measured capacity")
@@ -291,6 +292,77 @@ def run_serving(args):
 
 
 # ------------------------------------------------------------------------------ our arm
+CYL_WORKLOAD = ("rotating cylindrical sliding interface, Navier-Stokes with BR1 lifting: annular sector "
+                "r in [1,1.5], theta in [0,pi/4] periodic, z in [0,0.5]; rotor (inside) and stator blocks "
+                "of 24x48x16 curved hexes each (36,864 elements, 768 sliding faces per side), rotor "
+                "omega=0.4, N=7 (18.9M DOF), Re=1e4, Pr=0.72, Mach 0.3 axial stream with a pressure pulse")
+
+
+def run_cylinder(args, rank, world, local):
+    """The rotating cylindrical interface with Navier-Stokes at N = 7: RK steps through the
+    curvilinear kernels (interface lifting, lifting, viscous interface flux, element)."""
+    import torch
+    from paper_2008_04356_gb300 import build as B, slidemesh, synth
+    torch.cuda.set_device(local)
+    B.build_library()
+    stream = torch.cuda.current_stream()
+    prec = synth.FP64 if args.precision == "fp64" else synth.FP32
+    p = synth.config_cylinder(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec,
+                              physics=synth.NAVIER_STOKES)
+    sol = slidemesh.Solver(p)
+    sol.init_state()
+    dt = synth.cfl_dt(p)
+    sol.step(dt, args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sol.step(dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    value = world * p.ndof * 5 * args.steps / (ms * 1e-3)
+    kms, kcnt = sol.step_profiled(dt, args.profile_steps)
+    sb = 8 if prec == synth.FP64 else 4
+    # element kernel per DOF-update: U in/out, G in (4 of 5 stages)/out, 13 geometry values,
+    # 15 gradients
+    elem_bytes = ((2 + 1 + 0.8) * 5 + 13 + 15) * sb * p.ndof
+    elem_ms = kms[2] / kcnt[2]
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    achieved = elem_bytes / (elem_ms * 1e-3) / 1e9
+    d = sol.diag()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32", "data": "synthetic",
+        "config": {"workload": CYL_WORKLOAD, "elements": p.nelem, "N": p.N, "dof": p.ndof,
+                   "sliding_faces_per_side": p.n_faces, "riemann": "rusanov", "mu": p.mu,
+                   "l2": "inputs larger than L2 (%.2f GB state + %.2f GB geometry)" % (
+                       p.ndof * 5 * sb / 1e9, p.ndof * 13 * sb / 1e9),
+                   "parallelism": "single GPU", "dt": dt, "final_t": d["t"]},
+        "interface_face_updates_per_s": p.n_faces * 5 * args.steps / (ms * 1e-3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "curved_element_kernel<N=7, %s, Rusanov, stage, NS>" % (
+                         "double" if prec == synth.FP64 else "float"),
+                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": elem_bytes, "avg_launch_ms": elem_ms},
+        "kernels": {"stage_params": {"launches": kcnt[0], "ms": kms[0]},
+                    "lifting_and_interface": {"launches": kcnt[1], "ms": kms[1], "avg_ms": kms[1] / max(kcnt[1], 1)},
+                    "curved_element": {"launches": kcnt[2], "ms": kms[2], "avg_ms": elem_ms}},
+        "gpu_launches": 5 * 5 * args.steps,
+        "clocks": clk,
+        "diag": {"n_delta": d["n_delta"], "s_delta": d["s_delta"], "finite": d["status"] == 0,
+                 "totals": d["totals"]},
+    }
+    sol.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -302,6 +374,9 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             run_serving(args)
+        return
+    if args.workload == "cylinder":
+        run_cylinder(args, rank, world, local)
         return
     import numpy as np
     import torch

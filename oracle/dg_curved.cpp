@@ -173,6 +173,7 @@ void build_geometry(Curved& o) {
   o.X0.assign(o.E * 3 * nn, 0.0);
   o.Ja0.assign(o.E * 9 * nn, 0.0);
   o.J0.assign(o.E * nn, 0.0);
+  #pragma omp parallel for schedule(static)
   for (long long e = 0; e < o.E; ++e) {
     Id id = elem_id(o, e);
     double lo3 = id.blk == 0 ? o.p.x0 : o.p.x1;

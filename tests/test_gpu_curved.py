@@ -186,3 +186,26 @@ def test_cylinder_ns_steps(sm, N):
     s32.step(dt, 3)
     U32, _ = s32.get_state()
     assert rel_l2(U32.cpu().numpy(), Uo) < FP32_TOL
+
+
+@pytest.mark.slow
+def test_cylinder_full_size_sampled(sm):
+    """The 2 x 24x48x16 cylinder at N = 7 (18.9 M DOF) in the benchmark's launch
+    configuration: sampled elements (walls, interface, periodic ends, interior) of the GPU
+    RHS against the oracle element by element (Euler; FP64 1e-12, FP32 1e-5 rel L2)."""
+    p = synth.config_cylinder(N=7, nel=(24, 48, 16), omega=0.4, phi0=0.913, flow="pulse")
+    o = O.Oracle(p)
+    U = synth.random_state(p, seed=77)
+    rng = np.random.default_rng(5)
+    nx, ny, nz = 24, 48, 16
+    pick = [(b, ix, iy, iz) for b in (0, 1) for ix in (0, nx - 1) for iy in (0, ny - 1) for iz in (0, nz - 1)]
+    pick += [(int(rng.integers(2)), int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))) for _ in range(16)]
+    elems = np.array([b * nx * ny * nz + ix + nx * (iy + ny * iz) for b, ix, iy, iz in pick], dtype=np.int64)
+    t = 0.37
+    ref = o.rhs_elements(U, t, elems)
+    got = sm.Solver(p).rhs(dev(U), t).cpu().numpy()[elems]
+    assert rel_max(got, ref) < FP64_TOL
+    p32 = copy.deepcopy(p)
+    p32.precision = synth.FP32
+    got32 = sm.Solver(p32).rhs(dev(U, torch.float32), t).cpu().numpy()[elems]
+    assert rel_l2(got32, ref) < FP32_TOL
