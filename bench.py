@@ -9,6 +9,7 @@ Every stage runs the mapper/mortar-matrix kernel, the fused interface kernel and
 element kernel (volume, surface, RK update), replayed from a CUDA graph.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload interface-heavy|serving|cylinder] [--precision fp32|fp64]
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the host
 cores on a bounded sample of the same workload (fewer elements along z).

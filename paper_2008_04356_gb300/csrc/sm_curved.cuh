@@ -55,7 +55,7 @@ __device__ __forceinline__ void curved_element_block(const MeshDev& m, const Sta
   using C = ElemCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sF = reinterpret_cast<T*>(smem_raw);        // [EPB][3][5][NN], contraction index contiguous
+  T* sF = reinterpret_cast<T*>(smem_raw);        // [EPB][3][5][NN], node order
   T* sS = sF + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
   const T* c = Prec<T>::c(m);
   const T* geo = reinterpret_cast<const T*>(m.geo);
@@ -105,14 +105,13 @@ __device__ __forceinline__ void curved_element_block(const MeshDev& m, const Sta
     const T* ge = geo + e * 13 * NN + nd;
     const T vs = moving_block(m, blk) ? vspeed : T(0);
     const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
-    const int lay[3] = {nd, j + NP * (i + NP * k), k + NP * (i + NP * j)};
     T* Fe = sF + le * 15 * NN;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const T J0 = ge[(3 * d) * NN], J1 = ge[(3 * d + 1) * NN], J2 = ge[(3 * d + 2) * NN];
       const T V = vs * ge[(10 + d) * NN];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Fe[(5 * d + v) * NN + lay[d]] = J0 * F[0][v] + J1 * F[1][v] + J2 * F[2][v] - V * ub[v];
+      for (int v = 0; v < 5; ++v) Fe[(5 * d + v) * NN + nd] = J0 * F[0][v] + J1 * F[1][v] + J2 * F[2][v] - V * ub[v];
     }
   }
 
@@ -238,11 +237,9 @@ __device__ __forceinline__ void curved_element_block(const MeshDev& m, const Sta
   const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
   T acc[5];
   {
-    const T* F1 = sF + le * 15 * NN + nd;
-    const T* F2 = sF + le * 15 * NN + 5 * NN + j + NP * (i + NP * k);
-    const T* F3 = sF + le * 15 * NN + 10 * NN + k + NP * (i + NP * j);
+    const T* Fe = sF + le * 15 * NN + nd;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = F1[v * NN] + F2[v * NN] + F3[v * NN];
+    for (int v = 0; v < 5; ++v) acc[v] = Fe[v * NN] + Fe[(5 + v) * NN] + Fe[(10 + v) * NN];
   }
   const T iw0 = c[MC_IW0];
   const T* Se = sS + le * 30 * NP2;
@@ -627,7 +624,6 @@ __device__ __forceinline__ void curved_lift_block(const MeshDev& m, const StageP
   }
   T g[15];
   const T* ge = geo + e * 13 * NN + nd;
-  const int lay[3] = {nd, j + NP * (i + NP * k), k + NP * (i + NP * j)};
 #pragma unroll 1
   for (int a = 0; a < 3; ++a) {
     if (active) {
@@ -636,7 +632,7 @@ __device__ __forceinline__ void curved_lift_block(const MeshDev& m, const StageP
       for (int d = 0; d < 3; ++d) {
         const T Ja = ge[(3 * d + a) * NN];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) Fe[(5 * d + v) * NN + lay[d]] = Ja * Q[v];
+        for (int v = 0; v < 5; ++v) Fe[(5 * d + v) * NN + nd] = Ja * Q[v];
       }
     }
     __syncthreads();
@@ -648,7 +644,7 @@ __device__ __forceinline__ void curved_lift_block(const MeshDev& m, const StageP
       const T iw0 = c[MC_IW0];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        T acc = Fe[v * NN + lay[0]] + Fe[(5 + v) * NN + lay[1]] + Fe[(10 + v) * NN + lay[2]];
+        T acc = Fe[v * NN + nd] + Fe[(5 + v) * NN + nd] + Fe[(10 + v) * NN + nd];
         if (i == 0) acc += iw0 * Se[(0 * 15 + a * 5 + v) * NP2 + j + NP * k];
         if (i == N) acc += iw0 * Se[(1 * 15 + a * 5 + v) * NP2 + j + NP * k];
         if (j == 0) acc += iw0 * Se[(2 * 15 + a * 5 + v) * NP2 + i + NP * k];

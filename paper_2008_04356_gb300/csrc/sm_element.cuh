@@ -25,7 +25,7 @@ template <int N> struct ElemCfg {
   static constexpr int MINB = N == 1 ? 4 : (N == 6 ? 4 : (N == 7 ? 2 : (N == 2 || N == 3 || N == 4 ? 5 : 6)));
 #endif
   template <typename T> static constexpr size_t smem_bytes() {
-    return sizeof(T) * (size_t)(EPB * 15 * NN + EPB * 30 * NP2 + NP2 + 8);
+    return sizeof(T) * (size_t)(EPB * 15 * NN + EPB * 30 * NP2);
   }
 };
 
@@ -64,6 +64,28 @@ __device__ __forceinline__ void load_line(const T* p, T (&r)[NP]) {
   }
 }
 
+// Stores a line with the vector widths of load_line (scalar stores at a line stride of NP
+// words would hit each bank twice per warp).
+template <typename T, int NP>
+__device__ __forceinline__ void store_line(T* p, const T (&r)[NP]) {
+  if constexpr (sizeof(T) == 4 && NP % 4 == 0) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int h = 0; h < NP / 4; ++h) q[h] = make_float4(r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
+  } else if constexpr (sizeof(T) == 4 && NP % 2 == 0) {
+    float2* q = reinterpret_cast<float2*>(p);
+#pragma unroll
+    for (int h = 0; h < NP / 2; ++h) q[h] = make_float2(r[2 * h], r[2 * h + 1]);
+  } else if constexpr (sizeof(T) == 8 && NP % 2 == 0) {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int h = 0; h < NP / 2; ++h) q[h] = make_double2(r[2 * h], r[2 * h + 1]);
+  } else {
+#pragma unroll
+    for (int l = 0; l < NP; ++l) p[l] = r[l];
+  }
+}
+
 // Weak-form derivative matrices Dhat for N = 1..7 in constant memory, [N-1][i*8 + l]; the
 // line contractions below index them with compile-time constants, so every Dhat entry is
 // an operand of the multiply-add itself.  Each translation unit that instantiates the
@@ -81,21 +103,18 @@ template <typename T> __device__ __forceinline__ T dhat_c(int n, int idx);
 template <> __device__ __forceinline__ float dhat_c<float>(int n, int idx) { return c_dhat_f[n - 1][idx]; }
 template <> __device__ __forceinline__ double dhat_c<double>(int n, int idx) { return c_dhat_d[n - 1][idx]; }
 
-// Volume integral as one in-place contraction per (direction, variable, line) (1), or per
-// node over its three lines (0).
-#ifndef SM_ELEM_LINES
-#define SM_ELEM_LINES 1
-#endif
-
 // Every contraction line (direction, variable, line) of the CTA's EPB elements once: read
 // its NP values, write sum_l Dhat_al value_l back in place (Dhat as constant-memory operands).
+// The three flux arrays of an element are in node order [v][k][j][i]: xi^1 lines are
+// contiguous (vector accesses), xi^2 and xi^3 lines have strides NP and NP^2 and are
+// numbered so that consecutive lanes take consecutive words (no bank conflicts).
 template <int N, typename T>
 __device__ __forceinline__ void contract_lines_inplace(T* sF, int tid) {
   using C = ElemCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
-  for (int w = tid; w < EPB * 15 * NP2; w += THREADS) {
-    const int l2 = w / (15 * NP2);
-    const int rr = w - l2 * 15 * NP2;
+  for (int w = tid; w < EPB * 5 * NP2; w += THREADS) {
+    const int l2 = w / (5 * NP2);
+    const int rr = w - l2 * 5 * NP2;
     T* line = sF + l2 * 15 * NN + (rr / NP2) * NN + (rr % NP2) * NP;
     T rv[NP], ov[NP];
     load_line<T, NP>(line, rv);
@@ -106,8 +125,29 @@ __device__ __forceinline__ void contract_lines_inplace(T* sF, int tid) {
       for (int l = 0; l < NP; ++l) s += dhat_c<T>(N, a * SM_MAXNP + l) * rv[l];
       ov[a] = s;
     }
+    store_line<T, NP>(line, ov);
+  }
 #pragma unroll
-    for (int a = 0; a < NP; ++a) line[a] = ov[a];
+  for (int d = 1; d < 3; ++d) {
+    const int stride = d == 1 ? NP : NP2;
+    for (int w = tid; w < EPB * 5 * NP2; w += THREADS) {
+      const int l2 = w / (5 * NP2);
+      const int rr = w - l2 * 5 * NP2;
+      const int v = rr / NP2, q = rr - v * NP2;
+      // xi^2 line (i, k): base i + NP^2 k; xi^3 line (i, j): base i + NP j
+      const int base = d == 1 ? (q % NP) + NP2 * (q / NP) : q;
+      T* line = sF + l2 * 15 * NN + (5 * d + v) * NN + base;
+      T rv[NP];
+#pragma unroll
+      for (int l = 0; l < NP; ++l) rv[l] = line[l * stride];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < NP; ++l) s += dhat_c<T>(N, a * SM_MAXNP + l) * rv[l];
+        line[a * stride] = s;
+      }
+    }
   }
 }
 
@@ -131,11 +171,9 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
   using C = ElemCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // contravariant fluxes, each direction stored with its contraction index contiguous:
-  // F~1 at [v][k][j][i], F~2 at [v][k][i][j], F~3 at [v][j][i][k]
+  // contravariant fluxes F~1, F~2, F~3, each in node order [v][k][j][i]
   T* sF = reinterpret_cast<T*>(smem_raw);        // [EPB][3][5][NN]
   T* sS = sF + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
-  T* sD = sS + EPB * 30 * NP2;                   // [NP][NP] Dhat
 
   const T* c = Prec<T>::c(m);
   const int tid = threadIdx.x;
@@ -145,7 +183,6 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
   const long long base = e * 5 * NN + nd;
   const T gamma = c[MC_GAMMA];
 
-  if (tid < NP2) sD[tid] = Prec<T>::dhat(m.basis)[(tid / NP) * SM_MAXNP + (tid % NP)];
   T u[5], g[5];
   if (active) {
 #pragma unroll
@@ -157,7 +194,6 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
     const int blk = e >= m.Es;
     const Prim<T> q = primitives(u, gamma);
     T f[5];
-    const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
     T* Fe = sF + le * 15 * NN;
     const T a0 = c[MC_METRIC + 3 * blk], a1 = c[MC_METRIC + 3 * blk + 1], a2 = c[MC_METRIC + 3 * blk + 2];
     T gn[PHYS ? 15 : 1], fv[5];
@@ -180,7 +216,7 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
       for (int v = 0; v < 5; ++v) f[v] -= fv[v];
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN + j + NP * (i + NP * k)] = a1 * f[v];
+    for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN + nd] = a1 * f[v];
     axis_flux<T, 0>(u, q, T(0), f);                             // xi^3 -> x
     if (PHYS) {
       viscous_flux_axis(u, gn, 0, c, fv);
@@ -188,7 +224,7 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
       for (int v = 0; v < 5; ++v) f[v] -= fv[v];
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN + k + NP * (i + NP * j)] = a2 * f[v];
+    for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN + nd] = a2 * f[v];
   }
 
   // ---- face fluxes: one work item per (element, face, face node) ----
@@ -285,47 +321,15 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
   // ---- volume integral (sum factorisation) + surface integral ----
   const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
   T acc[5];
-#if SM_ELEM_LINES
-  // every contraction line (direction, variable, line) once, in place
   __syncthreads();
   contract_lines_inplace<N, T>(sF, tid);
   __syncthreads();
   if (!active) return;
   {
-    const T* F1 = sF + le * 15 * NN + nd;
-    const T* F2 = sF + le * 15 * NN + 5 * NN + j + NP * (i + NP * k);
-    const T* F3 = sF + le * 15 * NN + 10 * NN + k + NP * (i + NP * j);
+    const T* Fe = sF + le * 15 * NN + nd;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = F1[v * NN] + F2[v * NN] + F3[v * NN];
+    for (int v = 0; v < 5; ++v) acc[v] = Fe[v * NN] + Fe[(5 + v) * NN] + Fe[(10 + v) * NN];
   }
-#else
-  __syncthreads();
-  if (!active) return;
-  {
-    T d1[NP], d2[NP], d3[NP];
-    load_line<T, NP>(sD + i * NP, d1);
-    load_line<T, NP>(sD + j * NP, d2);
-    load_line<T, NP>(sD + k * NP, d3);
-    const T* F1 = sF + le * 15 * NN + NP * (j + NP * k);
-    const T* F2 = sF + le * 15 * NN + 5 * NN + NP * (i + NP * k);
-    const T* F3 = sF + le * 15 * NN + 10 * NN + NP * (i + NP * j);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      T r[NP];
-      T a = T(0);
-      load_line<T, NP>(F1 + v * NN, r);
-#pragma unroll
-      for (int l = 0; l < NP; ++l) a += d1[l] * r[l];
-      load_line<T, NP>(F2 + v * NN, r);
-#pragma unroll
-      for (int l = 0; l < NP; ++l) a += d2[l] * r[l];
-      load_line<T, NP>(F3 + v * NN, r);
-#pragma unroll
-      for (int l = 0; l < NP; ++l) a += d3[l] * r[l];
-      acc[v] = a;
-    }
-  }
-#endif
   const T iw0 = c[MC_IW0];
   const T* Se = sS + le * 30 * NP2;
   if (i == 0 || i == N) {

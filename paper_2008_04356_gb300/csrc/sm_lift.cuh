@@ -36,8 +36,8 @@ __device__ __forceinline__ void lift_block(const MeshDev& m, const StageParams* 
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       Fe[v * NN + nd] = a0 * Q[v];
-      Fe[(5 + v) * NN + j + NP * (i + NP * k)] = a1 * Q[v];
-      Fe[(10 + v) * NN + k + NP * (i + NP * j)] = a2 * Q[v];
+      Fe[(5 + v) * NN + nd] = a1 * Q[v];
+      Fe[(10 + v) * NN + nd] = a2 * Q[v];
     }
   }
   for (int w = tid; w < EPB * 6 * NP2; w += THREADS) {
@@ -115,8 +115,8 @@ __device__ __forceinline__ void lift_block(const MeshDev& m, const StageParams* 
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     T gy = Fe[v * NN + nd];
-    T gz = Fe[(5 + v) * NN + j + NP * (i + NP * k)];
-    T gx = Fe[(10 + v) * NN + k + NP * (i + NP * j)];
+    T gz = Fe[(5 + v) * NN + nd];
+    T gx = Fe[(10 + v) * NN + nd];
     if (i == 0) gy += iw0 * Se[(0 * 5 + v) * NP2 + j + NP * k];
     if (i == N) gy += iw0 * Se[(1 * 5 + v) * NP2 + j + NP * k];
     if (j == 0) gz += iw0 * Se[(2 * 5 + v) * NP2 + i + NP * k];
