@@ -50,22 +50,71 @@ dg_element_batch_kernel(const BatchSolveDev* __restrict__ bs, const int* __restr
   }
 }
 
+// Interface tiles of every solve of the group: odd N takes the register-fused tile (TF 8 or
+// 16) in persistent CTAs that prefetch the next tile; even N the staged tile.
+template <int N, int TF> struct BatchIfCfg {
+  static constexpr bool FUSED = N % 2 == 1;
+  static constexpr int TFF = TF < 8 ? 8 : TF;
+  static constexpr int THREADS = FUSED ? IfFusedCfg<(FUSED ? N : 1), TFF>::THREADS : IfCfg<N>::THREADS;
+  static constexpr int MINB = FUSED ? IfFusedCfg<(FUSED ? N : 1), TFF>::MINB : IfCfg<N>::MINB;
+  static constexpr size_t smem = FUSED ? IfFusedCfg<(FUSED ? N : 1), TFF>::smem_bytes : IfCfg<N>::template smem_bytes<float, TF>();
+  static constexpr int TILE = FUSED ? TFF : TF;
+};
+
 template <int N, int RIEM, int TF>
-__global__ void __launch_bounds__(IfCfg<N>::THREADS, IfCfg<N>::MINB)
+__global__ void __launch_bounds__(BatchIfCfg<N, TF>::THREADS, BatchIfCfg<N, TF>::MINB)
 sliding_interface_batch_kernel(const BatchSolveDev* __restrict__ bs, const int* __restrict__ offs, int nsolve, int stage) {
+  using B = BatchIfCfg<N, TF>;
+  constexpr int TL = B::TILE;
   __shared__ int s_off[SM_MAX_BATCH + 1];
-  for (int i = threadIdx.x; i <= nsolve; i += blockDim.x) s_off[i] = offs[i];
+  const int tid = threadIdx.x;
+  for (int i = tid; i <= nsolve; i += blockDim.x) s_off[i] = offs[i];
   __syncthreads();
   const int total = s_off[nsolve];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int s = find_solve(s_off, nsolve, item);
-    const BatchSolveDev& b = bs[s];
-    const int local = item - s_off[s];
-    const int ntx = (b.m.ny + TF - 1) / TF;
-    const int c = b.cur ^ (stage & 1);
-    interface_tile<N, float, RIEM, TF>(b.m, b.sp, (const float*)b.U[c], (float*)b.Fs, (float*)b.Fm, local % ntx,
-                                       local / ntx, nullptr, (const float*)b.Ts, (const float*)b.Tm);
-    __syncthreads();
+  if constexpr (B::FUSED) {
+    using C = IfFusedCfg<N, TL>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* sBuf = reinterpret_cast<float*>(smem_raw);   // [NBUF][TBUF] trace buffers
+    float* sF = sBuf + C::NBUF * C::TBUF;
+    float* sO = sF + C::SFSZ;
+    // a work item's solve, its buffers at this stage and its tile coordinates
+    auto locate = [&](int item, int* ty, int* tz) -> const BatchSolveDev& {
+      const int s = find_solve(s_off, nsolve, item);
+      const BatchSolveDev& b = bs[s];
+      const int ntx = (b.m.ny + TL - 1) / TL;
+      divmod_small(item - s_off[s], ntx, 1.0f / (float)ntx, tz, ty);
+      return b;
+    };
+    fused_pipeline<N, TL>(
+        blockIdx.x, gridDim.x, total, sBuf,
+        [&](int item, float* dst) {
+          int ty, tz;
+          const BatchSolveDev& b = locate(item, &ty, &tz);
+          const int c = b.cur ^ (stage & 1);
+          fused_tile_stage<N, TL>(b.m, b.sp, (const float*)b.U[c], (const float*)b.Ts, (const float*)b.Tm, ty, tz,
+                                  dst, tid);
+        },
+        [&](int item, const float* sB) {
+          int ty, tz;
+          const BatchSolveDev& b = locate(item, &ty, &tz);
+          fused_tile_compute<N, RIEM, TL>(b.m, b.sp, (float*)b.Fs, (float*)b.Fm, ty, tz, sB, sF, sO, tid);
+        },
+        [&](int item) {
+          int ty, tz;
+          const BatchSolveDev& b = locate(item, &ty, &tz);
+          fused_tile_store<N, TL>(b.m, b.sp, (float*)b.Fs, (float*)b.Fm, ty, tz, sO, tid);
+        });
+  } else {
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+      const int s = find_solve(s_off, nsolve, item);
+      const BatchSolveDev& b = bs[s];
+      const int local = item - s_off[s];
+      const int ntx = (b.m.ny + TL - 1) / TL;
+      const int c = b.cur ^ (stage & 1);
+      interface_tile<N, float, RIEM, TL>(b.m, b.sp, (const float*)b.U[c], (float*)b.Fs, (float*)b.Fm, local % ntx,
+                                         local / ntx, nullptr, (const float*)b.Ts, (const float*)b.Tm);
+      __syncthreads();
+    }
   }
 }
 
@@ -80,8 +129,8 @@ cudaError_t launch_el(const BatchSolveDev* bs, const int* offs, int nsolve, int 
 
 template <int N, int RIEM, int TF>
 cudaError_t launch_if(const BatchSolveDev* bs, const int* offs, int nsolve, int grid, int stage, cudaStream_t st) {
-  using C = IfCfg<N>;
-  sliding_interface_batch_kernel<N, RIEM, TF><<<grid, C::THREADS, C::template smem_bytes<float, TF>(), st>>>(
+  using C = BatchIfCfg<N, TF>;
+  sliding_interface_batch_kernel<N, RIEM, TF><<<grid, C::THREADS, C::smem, st>>>(
       bs, offs, nsolve, stage);
   return cudaGetLastError();
 }
@@ -107,7 +156,7 @@ cudaError_t launch_if_tf(int tf, const BatchSolveDev* bs, const int* offs, int n
 template <int N, int RIEM, int TF>
 cudaError_t prep_if() {
   return cudaFuncSetAttribute(sliding_interface_batch_kernel<N, RIEM, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)IfCfg<N>::template smem_bytes<float, TF>());
+                              (int)BatchIfCfg<N, TF>::smem);
 }
 
 template <int N, int RIEM, int MODE>
@@ -177,6 +226,8 @@ cudaError_t prepare_batch(int N) {
   SM_BATCH_SWITCH(N, SM_PREP_CALL)
 #undef SM_PREP_CALL
 }
+
+int batch_interface_tile(int N, int tf) { return (N % 2 == 1 && tf < 8) ? 8 : tf; }
 
 int batch_elements_per_block(int N) {
   switch (N) {

@@ -31,10 +31,17 @@ struct StageParams {
   double t;            // stage time
   double delta;        // displacement of the moving block
   long long n;         // integer face offset
+  int n_mod;           // n mod n_par in [0, n_par): the partner shift of the interface kernels
+  int pad_;
   double s;            // sub-face fraction
   double sig_s, sig_m;
   double mat[8][SM_MAXNP * SM_MAXNP];
   float mat_f[8][SM_MAXNP * SM_MAXNP];
+  // the FP32 operators as the float pairs the FP32 interface kernel reads, four tables of
+  // sm_pair_stride(np) floats: table g = 0, 1 forward pairs of mortar i_sub = g,
+  // [i][j] = (Ps_g[j][i], Pm_(3-g)[j][i]); table g = 2, 3 back pairs of side g - 2,
+  // [j][i] = (B_lo[i][j], B_hi[i][j]); rows of sm_pair_row(np) pairs
+  alignas(16) float pair_f[4 * 144];
   // cylindrical interface: cos, sin of the rotor angle phi = -delta, and of the angles
   // w Theta - phi that carry a stator face seen through w periodic wraps into the rotor's
   // frame, for w = w0 and w0 + 1 (w0 = floor((-n-1) / n_par), the smallest wrap count)
@@ -44,6 +51,11 @@ struct StageParams {
   float rot_f[2];
   float arot_f[2][2];
 };
+
+// Layout of StageParams::pair_f: pairs per row (even) and floats per table (16 mod 32, so
+// that two tables read by one warp fall in different banks).
+__host__ __device__ constexpr int sm_pair_row(int np) { return np + (np & 1); }
+__host__ __device__ constexpr int sm_pair_stride(int np) { return ((2 * sm_pair_row(np) * np + 31) / 32) * 32 + 16; }
 
 // Per-precision constants of the discrete operator, precomputed on the host so that the
 // kernels do no FP64 arithmetic in FP32 mode.

@@ -960,7 +960,8 @@ long long group_elems(const sm_batch& b, const sm_batch::Group& g) {
 }
 
 // interface work-item offsets for tile width tf
-cudaError_t upload_if_offsets(sm_batch::Group& g, const sm_batch& b, int tf) {
+cudaError_t upload_if_offsets(sm_batch::Group& g, const sm_batch& b, int tf_req) {
+  const int tf = batch_interface_tile(g.N, tf_req);
   std::vector<int> offs(g.members.size() + 1, 0);
   for (size_t q = 0; q < g.members.size(); ++q) {
     const MeshDev& m = b.solvers[g.members[q]]->m;
@@ -1111,6 +1112,7 @@ static int batch_autotune(sm_batch* b, void* stream, bool only_missing) {
     int best_tf = g.tf, best_gif = g.grid_if;
     float best_if = 1e30f;
     for (int tf : {4, 8, 16}) {
+      if (batch_interface_tile(g.N, tf) != tf) continue;   // the same kernel as a wider tile
       if ((err = upload_if_offsets(g, *b, tf)) != cudaSuccess) break;
       for (int per_sm : {2, 4, 8, 16, 0}) {
         const int grid = per_sm ? std::min(g.total_if, b->sms * per_sm) : g.total_if;

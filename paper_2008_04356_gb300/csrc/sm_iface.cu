@@ -1,7 +1,25 @@
-// Single-solve launch of the fused sliding-interface kernel (body in sm_iface.cuh).
+// Single-solve launch of the fused sliding-interface kernel (bodies in sm_iface.cuh): the
+// register-fused tile for FP32 states at odd N, the staged tile otherwise.
 #include "sm_iface.cuh"
 
 namespace {
+
+// persistent grid of the FP32 interface kernel: CTAs per SM x SMs of the current device
+int fused_sms() {
+  static int sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (sms[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    sms[dev] = v;
+  }
+  return sms[dev];
+}
+// resident CTAs per SM of the FP32 interface kernel <N, RIEM, TF> (occupancy calculator,
+// once per instantiation; the shared-memory attribute is set by prepare_interface first)
+template <int N, int RIEM, int TF>
+int fused_ctas_per_sm();
 
 template <int N, typename T, int RIEM>
 __global__ void __launch_bounds__(IfCfg<N>::THREADS, sizeof(T) == 4 ? IfCfg<N>::MINB : 1)
@@ -10,24 +28,67 @@ sliding_interface_kernel(const MeshDev m, const StageParams* __restrict__ sp, co
   interface_tile<N, T, RIEM, IfCfg<N>::TF>(m, sp, U, Fs, Fm, blockIdx.x, blockIdx.y, nullptr, Ts, Tm);
 }
 
+// FP32, odd N: the register-fused tile
+template <int N, int RIEM, int TF>
+__global__ void __launch_bounds__(IfFusedCfg<N, TF>::THREADS, IfFusedCfg<N, TF>::MINB)
+sliding_interface_fused_kernel(const MeshDev m, const StageParams* __restrict__ sp, const float* __restrict__ U,
+                               float* __restrict__ Fs, float* __restrict__ Fm, const float* __restrict__ Ts,
+                               const float* __restrict__ Tm) {
+  interface_fused_loop<N, RIEM, TF>(m, sp, U, Fs, Fm, Ts, Tm);
+}
+
+template <int N, int RIEM, int TF>
+int fused_ctas_per_sm() {
+  static int n = 0;
+  if (n == 0) {
+    using F = IfFusedCfg<N, TF>;
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sliding_interface_fused_kernel<N, RIEM, TF>, F::THREADS,
+                                                      F::smem_bytes) != cudaSuccess || v <= 0)
+      v = 1;
+    n = v;
+  }
+  return n;
+}
+
 template <int N, typename T, int RIEM>
 cudaError_t launch_if_t(const MeshDev& m, const StageParams* sp, const void* U, void* Fs, void* Fm, cudaStream_t st,
                         const void* Ts, const void* Tm) {
-  using C = IfCfg<N>;
-  dim3 grid((m.ny + C::TF - 1) / C::TF, m.nz);
-  sliding_interface_kernel<N, T, RIEM><<<grid, C::THREADS, C::template smem_bytes<T>(), st>>>(
-      m, sp, (const T*)U, (T*)Fs, (T*)Fm, (const T*)Ts, (const T*)Tm);
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 4 && N % 2 == 1) {
+    using F = IfFusedCfg<N, IfFusedTF<N>::TF>;
+    const long long tiles = (long long)((m.ny + F::TF - 1) / F::TF) * m.nz;
+    if (tiles <= 0) return cudaSuccess;
+    const long long cap = (long long)fused_ctas_per_sm<N, RIEM, F::TF>() * fused_sms();
+    const long long grid = tiles < cap ? tiles : cap;
+    sliding_interface_fused_kernel<N, RIEM, F::TF><<<(unsigned)grid, F::THREADS, F::smem_bytes, st>>>(
+        m, sp, (const float*)U, (float*)Fs, (float*)Fm, (const float*)Ts, (const float*)Tm);
+    return cudaGetLastError();
+  } else {
+    using C = IfCfg<N>;
+    dim3 grid((m.ny + C::TF - 1) / C::TF, m.nz);
+    sliding_interface_kernel<N, T, RIEM><<<grid, C::THREADS, C::template smem_bytes<T>(), st>>>(
+        m, sp, (const T*)U, (T*)Fs, (T*)Fm, (const T*)Ts, (const T*)Tm);
+    return cudaGetLastError();
+  }
 }
 
 template <int N, typename T>
 cudaError_t prepare_if_t() {
-  using C = IfCfg<N>;
-  cudaError_t e0 = cudaFuncSetAttribute(sliding_interface_kernel<N, T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)C::template smem_bytes<T>());
-  cudaError_t e1 = cudaFuncSetAttribute(sliding_interface_kernel<N, T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)C::template smem_bytes<T>());
-  return e0 != cudaSuccess ? e0 : e1;
+  if constexpr (sizeof(T) == 4 && N % 2 == 1) {
+    using F = IfFusedCfg<N, IfFusedTF<N>::TF>;
+    cudaError_t f0 = cudaFuncSetAttribute(sliding_interface_fused_kernel<N, 0, F::TF>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem_bytes);
+    cudaError_t f1 = cudaFuncSetAttribute(sliding_interface_fused_kernel<N, 1, F::TF>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem_bytes);
+    return f0 != cudaSuccess ? f0 : f1;
+  } else {
+    using C = IfCfg<N>;
+    cudaError_t e0 = cudaFuncSetAttribute(sliding_interface_kernel<N, T, 0>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::template smem_bytes<T>());
+    cudaError_t e1 = cudaFuncSetAttribute(sliding_interface_kernel<N, T, 1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::template smem_bytes<T>());
+    return e0 != cudaSuccess ? e0 : e1;
+  }
 }
 
 template <int N>

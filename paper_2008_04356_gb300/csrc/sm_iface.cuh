@@ -90,8 +90,7 @@ __device__ __forceinline__ void interface_tile_euler(const MeshDev& m, const Sta
   const int ny = m.ny;
   const int TFe = min(TF, ny - i0);
   const int nmort = 2 * TFe + 1;
-  long long nl = sp->n % ny;
-  const int nmod = (int)(nl < 0 ? nl + ny : nl);
+  const int nmod = sp->n_mod;
 
   for (int w = tid; w < 8 * NP2; w += THREADS) {
     const int k = w / NP2, r = w - k * NP2;
@@ -189,6 +188,336 @@ __device__ __forceinline__ void interface_tile_euler(const MeshDev& m, const Sta
   }
 }
 
+// Register-fused Euler tile (FP32 state, N odd): the three steps of Sec. 3.3 with few
+// shared-memory round trips, in persistent CTAs that prefetch the traces of the next two
+// tiles with 16-byte cp.async while they compute the current one.  Per tile (TF static faces of one
+// perpendicular line plus one halo face per side):
+//   A. two threads per (mortar, row q), each for half of the row's NP mortar nodes: both
+//      sides' traces of all five variables are projected onto those nodes (Eq.
+//      projection_domain_mortar) into registers, as float pairs (static, moving) updated by
+//      packed FMAs, and the Riemann flux of each node follows at once, times the surface
+//      element;
+//   B. two threads per (side, face, row q), each for half of the row's face nodes: the
+//      face's two mortar flux rows are projected back (Eq. projection_mortar_domain; pairs
+//      (lower, upper mortar) summed at the end) into shared output blocks, which the CTA
+//      then copies to the face flux arrays with coalesced 16-byte stores.
+// A mortar's arithmetic does not depend on the tile it sits in (the halo mortar is computed
+// by both neighbouring tiles with the same operations), so results are independent of TF.
+// Lanes of a warp: in A 16 consecutive mortars x the two halves of one row (both halves
+// read the same trace values), in B 8 faces x 2 sides x 2 halves of one row; face blocks
+// at 4 mod 32 words, mortar blocks at 2 mod 32 and the operator tables 16 apart keep the
+// accesses of a warp in distinct banks.
+template <int N, int TFV> struct IfFusedCfg {
+  static_assert(N % 2 == 1, "the fused interface tile takes odd N (16-byte face blocks)");
+  static_assert(TFV % 8 == 0, "the fused interface tile takes TF = 8 k");
+  static constexpr int NP = N + 1, NP2 = NP * NP, NN = NP * NP * NP;
+  static constexpr int TF = TFV;
+  static constexpr int NM = 2 * TF + 1;
+  static constexpr int H0 = NP / 2;                              // node halves of a row
+  static constexpr int NBA = 2 * TF / 16;                        // 16-mortar blocks (A)
+  static constexpr int NBB = TF / 8;                             // 8-face blocks (B)
+  static constexpr int ITEMS_A = 32 * NBA * NP + 2 * NP;         // + the halo mortar
+  static constexpr int ITEMS_B = 32 * NBB * NP;
+  static constexpr int THREADS = ((ITEMS_A + 31) / 32) * 32;
+  // resident CTAs per SM asked of the register allocator (about 80 registers a thread)
+  static constexpr int MINB = 65536 / (THREADS * 80) > 0 ? 65536 / (THREADS * 80) : 1;
+  static constexpr int TB = 5 * NP2;                             // one face's block (floats)
+  static constexpr int FS = TB + (36 - TB % 32) % 32;            // = 4 mod 32, 16-byte rows
+  static constexpr int MS = TB + (34 - TB % 32) % 32;            // = 2 mod 32
+  static constexpr int MR = sm_pair_row(NP);
+  static constexpr int MT = sm_pair_stride(NP);
+  static constexpr int TBUF = 4 * MT + 2 * (TF + 1) * FS;        // one prefetch buffer (floats)
+  static constexpr int SFSZ = ((NM * MS + 3) / 4) * 4;           // mortar fluxes
+  static constexpr int OSZ = 2 * TF * FS;                        // output blocks
+  static constexpr int NBUF = 3;                                 // trace buffers: 2 tiles ahead
+  static constexpr size_t smem_floats = (size_t)NBUF * TBUF + SFSZ + OSZ;
+  static constexpr size_t smem_bytes = sizeof(float) * smem_floats;
+};
+// default tile width of the single-solve FP32 launch (the batch autotuner picks 8 or 16)
+template <int N> struct IfFusedTF { static constexpr int TF = 8; };
+
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+// Issues the asynchronous copies of one tile into buffer sB: the operator pair tables and the
+// traces of static faces i0 + r and moving faces i0 - n - 1 + r (mod n_par), r = 0..TFe,
+// from the compact arrays Ts / Tm or, when they are NULL, from the element node layers of U
+// (xi^3 = +1 static, xi^3 = -1 moving).
+template <int N, int TF>
+__device__ __forceinline__ void fused_tile_stage(const MeshDev& m, const StageParams* __restrict__ sp,
+                                                 const float* __restrict__ U, const float* __restrict__ Ts,
+                                                 const float* __restrict__ Tm, const int tile_x, const int iz,
+                                                 float* sB, const int tid) {
+  using C = IfFusedCfg<N, TF>;
+  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, THREADS = C::THREADS;
+  constexpr int FS = C::FS, MT = C::MT, TB = C::TB;
+  const int ny = m.ny;
+  const int i0 = tile_x * TF;
+  const int TFe = min(TF, ny - i0);
+  const int nmod = sp->n_mod;
+  for (int w = tid; w < MT; w += THREADS) cp_async_16(sB + 4 * w, sp->pair_f + 4 * w);
+  float* sT = sB + 4 * MT;
+  const int nslot = 2 * (TFe + 1);
+  if (Ts) {
+    // compact traces: a face's 5 (N+1)^2 values are contiguous, TB / 4 chunks of 16 bytes;
+    // thread = (chunk, slot group)
+    constexpr int NC = TB / 4;
+    constexpr int G = THREADS / NC;
+    if (tid < G * NC) {
+      const int c = tid % NC;
+      for (int slot = tid / NC; slot < nslot; slot += G) {
+        const int side = slot > TFe, r = slot - side * (TFe + 1);
+        int f = side ? i0 - nmod - 1 + r : i0 + r;
+        f = f < 0 ? f + ny : (f >= ny ? f - ny : f);
+        cp_async_16(sT + (side * (TF + 1) + r) * FS + 4 * c, (side ? Tm : Ts) + ((long long)iz * ny + f) * TB + 4 * c);
+      }
+    }
+  } else {
+    constexpr int NV = NP2 / 2;
+    for (int w = tid; w < nslot * 5 * NV; w += THREADS) {
+      const int k = w % NV;
+      const int rest = w / NV;
+      const int v = rest % 5;
+      const int sr = rest / 5;
+      const int side = sr >= TFe + 1, r = sr - side * (TFe + 1);
+      int f = side ? i0 - nmod - 1 + r : i0 + r;
+      f = f < 0 ? f + ny : (f >= ny ? f - ny : f);
+      const float* src = U + encode_elem(m, side, side ? 0 : m.nxs - 1, f, iz) * 5 * NN + (side ? 0 : NP2 * N) +
+                         (long long)v * NN + 2 * k;
+      cp_async_8(sT + (side * (TF + 1) + r) * FS + v * NP2 + 2 * k, src);
+    }
+  }
+}
+
+// Phase A for the NH mortar nodes j0 .. j0+NH-1 of row q of mortar mi.
+template <int N, int RIEM, int TF, int NH>
+__device__ __forceinline__ void fused_mortar_nodes(const float* sB, float* sF, const int mi, const int q,
+                                                   const int j0, const float sJ, const float gamma) {
+  using C = IfFusedCfg<N, TF>;
+  constexpr int NP = C::NP, NP2 = C::NP2, FS = C::FS, MS = C::MS, MR = C::MR, MT = C::MT;
+  const int isub = mi & 1, rs = mi >> 1, rm = rs + isub;
+  const float* sT = sB + 4 * MT;
+  const float* ts = sT + rs * FS + q * NP;
+  const float* tm = sT + (TF + 1 + rm) * FS + q * NP;
+  // the static lower mortar meets the moving face's upper part and vice versa
+  const float2* PF = reinterpret_cast<const float2*>(sB + isub * MT) + j0;
+  float2 acc[5][NH];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int j = 0; j < NH; ++j) acc[v][j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    float2 pp[NH];
+#pragma unroll
+    for (int j = 0; j < NH; ++j) pp[j] = PF[i * MR + j];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const float2 ab = make_float2(ts[v * NP2 + i], tm[v * NP2 + i]);
+#pragma unroll
+      for (int j = 0; j < NH; ++j) acc[v][j] = __ffma2_rn(pp[j], ab, acc[v][j]);
+    }
+  }
+  float* out = sF + mi * MS + q * NP + j0;
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    float QL[5], QR[5], F[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { QL[v] = acc[v][j].x; QR[v] = acc[v][j].y; }
+    riemann_axis<float, 0, RIEM>(QL, QR, 0.f, gamma, F);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v * NP2 + j] = F[v] * sJ;
+  }
+}
+
+// Phase B for the NH face nodes i0n .. i0n+NH-1 of row q of face r on one side, into the
+// face's shared output block o (the row's first node).
+template <int N, int TF, int NH>
+__device__ __forceinline__ void fused_face_nodes(const float* sB, const float* sF, float* o, const int r,
+                                                 const int side, const int q, const int i0n) {
+  using C = IfFusedCfg<N, TF>;
+  constexpr int NP = C::NP, NP2 = C::NP2, MS = C::MS, MR = C::MR, MT = C::MT;
+  const float* flo = sF + (2 * r + side) * MS + q * NP;
+  const float* fhi = flo + MS;
+  const float2* PB = reinterpret_cast<const float2*>(sB + (2 + side) * MT) + i0n;
+  float2 acc[5][NH];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int i = 0; i < NH; ++i) acc[v][i] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    float2 bb[NH];
+#pragma unroll
+    for (int i = 0; i < NH; ++i) bb[i] = PB[j * MR + i];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const float2 ab = make_float2(flo[v * NP2 + j], fhi[v * NP2 + j]);
+#pragma unroll
+      for (int i = 0; i < NH; ++i) acc[v][i] = __ffma2_rn(bb[i], ab, acc[v][i]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int i = 0; i < NH; ++i) {
+      const float x = acc[v][i].x + acc[v][i].y;
+      o[v * NP2 + i0n + i] = side ? -x : x;
+    }
+}
+
+// Phases A and B of one tile whose buffer sB has landed (see fused_tile_stage), into the
+// output blocks sO; ends with a barrier, after which sB and sF are free.
+template <int N, int RIEM, int TF>
+__device__ __forceinline__ void fused_tile_compute(const MeshDev& m, const StageParams* __restrict__ sp,
+                                                   float* __restrict__ Fs, float* __restrict__ Fm, const int tile_x,
+                                                   const int iz, const float* sB, float* sF, float* sO, const int tid) {
+  using C = IfFusedCfg<N, TF>;
+  constexpr int NP = C::NP, NP2 = C::NP2, H0 = C::H0, FS = C::FS, TB = C::TB;
+  const int ny = m.ny;
+  const int i0 = tile_x * TF;
+  const int TFe = min(TF, ny - i0);
+  const int nme = 2 * TFe + 1;
+  const int nmod = sp->n_mod;
+
+  // A. projections of both sides and the mortar Riemann fluxes (static outward normal +x)
+  const float sJ = m.cf[MC_SJ_IF];
+  const float gamma = m.cf[MC_GAMMA];
+  if (tid < C::ITEMS_A) {
+    int mi, q, h;
+    if (tid < 32 * C::NBA * NP) {
+      const int rest = tid >> 5;
+      mi = 16 * (rest / NP) + (tid & 15);
+      q = rest % NP;
+      h = (tid >> 4) & 1;
+    } else {
+      const int hw = tid - 32 * C::NBA * NP;   // the halo mortar 2 TF
+      mi = 2 * TF;
+      q = hw % NP;
+      h = hw / NP;
+    }
+    // both halves in one call (H0 = H1): the two half-warps run the same instructions
+    if (mi < nme) fused_mortar_nodes<N, RIEM, TF, H0>(sB, sF, mi, q, h * H0, sJ, gamma);
+  }
+  __syncthreads();
+
+  // B. back-projection: static face i0 + r from mortars (2r, 2r+1); moving face i0 - n + r
+  // from mortars 2r+1 (its lower part) and 2r+2 (its upper part), with the opposite sign
+  if (tid < C::ITEMS_B) {
+    const int rest = tid >> 5;
+    const int r = 8 * (rest / NP) + (tid & 7);
+    const int q = rest % NP;
+    const int side = (tid >> 3) & 1, h = (tid >> 4) & 1;
+    if (r < TFe) fused_face_nodes<N, TF, H0>(sB, sF, sO + (side * TF + r) * FS + q * NP, r, side, q, h * H0);
+  }
+  __syncthreads();
+}
+
+// Copies the tile's face flux blocks from sO to the face flux arrays (16-byte stores).
+template <int N, int TF>
+__device__ __forceinline__ void fused_tile_store(const MeshDev& m, const StageParams* __restrict__ sp,
+                                                 float* __restrict__ Fs, float* __restrict__ Fm, const int tile_x,
+                                                 const int iz, const float* sO, const int tid) {
+  using C = IfFusedCfg<N, TF>;
+  constexpr int FS = C::FS, TB = C::TB, THREADS = C::THREADS, NC = TB / 4;
+  const int ny = m.ny;
+  const int i0 = tile_x * TF;
+  const int TFe = min(TF, ny - i0);
+  const int nmod = sp->n_mod;
+  for (int w = tid; w < 2 * TFe * NC; w += THREADS) {
+    const int slot = w / NC, c = w - slot * NC;
+    const int side = slot >= TFe, r = slot - side * TFe;
+    int f = side ? i0 - nmod + r : i0 + r;
+    f = f < 0 ? f + ny : (f >= ny ? f - ny : f);
+    const float4 x = *reinterpret_cast<const float4*>(sO + (side * TF + r) * FS + 4 * c);
+    *reinterpret_cast<float4*>((side ? Fm : Fs) + ((long long)iz * ny + f) * TB + 4 * c) = x;
+  }
+}
+
+// Persistent tile pipeline: tiles first, first + stride, ... < total, with the traces of the
+// next NBUF - 1 tiles in flight while a tile computes.  stage(item, buffer) issues a tile's
+// copies; run(item, buffer) computes it (ending with a barrier) and store(item) writes it.
+template <int N, int TF, class Stage, class Run, class Store>
+__device__ __forceinline__ void fused_pipeline(const int first, const int stride, const int total, float* sBuf,
+                                               Stage stage, Run run, Store store) {
+  using C = IfFusedCfg<N, TF>;
+  constexpr int NBUF = C::NBUF;
+#pragma unroll
+  for (int k = 0; k < NBUF - 1; ++k) {
+    const int it = first + k * stride;
+    if (it < total) stage(it, sBuf + k * C::TBUF);
+    cp_async_commit();
+  }
+  // tile first + k stride sits in buffer k mod NBUF
+  int slot = 0;
+  for (int t = first; t < total; t += stride) {
+    // the buffer of the previous tile (free: its computation ended with a barrier) receives
+    // tile t + (NBUF-1) stride; then this tile's group is the oldest of NBUF pending ones
+    const int tp = t + (NBUF - 1) * stride;
+    if (tp < total) stage(tp, sBuf + (slot == 0 ? NBUF - 1 : slot - 1) * C::TBUF);
+    cp_async_commit();
+    cp_async_wait<NBUF - 1>();
+    __syncthreads();
+    run(t, sBuf + slot * C::TBUF);
+    store(t);
+    slot = slot + 1 == NBUF ? 0 : slot + 1;
+  }
+  cp_async_wait<0>();
+}
+
+// q = t / n, r = t - q n for 0 <= t < 2^24 and n >= 1 from a float estimate (inv = 1 / n),
+// corrected by one step either way: cheaper than an integer division by a runtime value.
+__device__ __forceinline__ void divmod_small(const int t, const int n, const float inv, int* q, int* r) {
+  int qq = __float2int_rz((float)t * inv);
+  int rr = t - qq * n;
+  if (rr < 0) { --qq; rr += n; }
+  else if (rr >= n) { ++qq; rr -= n; }
+  *q = qq;
+  *r = rr;
+}
+
+// The tiles of one solve: (n_par / TF) x n_perp, tile index = tile_x + ntx iz.
+template <int N, int RIEM, int TF>
+__device__ __forceinline__ void interface_fused_loop(const MeshDev& m, const StageParams* __restrict__ sp,
+                                                     const float* __restrict__ U, float* __restrict__ Fs,
+                                                     float* __restrict__ Fm, const float* __restrict__ Ts,
+                                                     const float* __restrict__ Tm) {
+  using C = IfFusedCfg<N, TF>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sBuf = reinterpret_cast<float*>(smem_raw);   // [NBUF][TBUF] trace buffers
+  float* sF = sBuf + C::NBUF * C::TBUF;               // [NM][MS] mortar fluxes
+  float* sO = sF + C::SFSZ;                           // [2][TF][FS] output blocks
+  const int tid = threadIdx.x;
+  const int ntx = (m.ny + TF - 1) / TF;
+  const float inv = 1.0f / (float)ntx;
+  int rx = 0, rz = 0;   // coordinates of the tile being computed
+  fused_pipeline<N, TF>(
+      blockIdx.x, gridDim.x, ntx * m.nz, sBuf,
+      [&](int t, float* dst) {
+        int x, z;
+        divmod_small(t, ntx, inv, &z, &x);
+        fused_tile_stage<N, TF>(m, sp, U, Ts, Tm, x, z, dst, tid);
+      },
+      [&](int t, const float* sB) {
+        divmod_small(t, ntx, inv, &rz, &rx);
+        fused_tile_compute<N, RIEM, TF>(m, sp, Fs, Fm, rx, rz, sB, sF, sO, tid);
+      },
+      [&](int t) { fused_tile_store<N, TF>(m, sp, Fs, Fm, rx, rz, sO, tid); });
+}
+
 // Interface tile modes: Euler flux, Navier-Stokes flux (BR1 viscous mean of both sides'
 // projected gradients on each mortar, Sec. 3.2), lifting (mortar mean of both sides'
 // projected primitive traces, the BR1 face value of the gradient computation).
@@ -215,8 +544,7 @@ __device__ __forceinline__ void interface_tile_staged(const MeshDev& m, const St
   const int i0 = tile_x * TF;
   const int ny = m.ny;
   const int TFe = min(TF, ny - i0);
-  long long nl = sp->n % ny;
-  const int nmod = (int)(nl < 0 ? nl + ny : nl);
+  const int nmod = sp->n_mod;
 
   for (int w = tid; w < 8 * NP2; w += THREADS) {
     const int k = w / NP2, r = w - k * NP2;

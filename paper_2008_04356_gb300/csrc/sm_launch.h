@@ -126,3 +126,5 @@ cudaError_t launch_batch_element(int N, int riemann, int mode, const BatchSolveD
 cudaError_t launch_batch_flip(BatchSolveDev* d_bs, int nsolve, cudaStream_t st);
 cudaError_t prepare_batch(int N);
 int batch_elements_per_block(int N);
+// tile width (static faces per work item) the batched interface kernel uses for a requested tf
+int batch_interface_tile(int N, int tf);

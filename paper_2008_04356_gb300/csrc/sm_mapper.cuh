@@ -91,6 +91,10 @@ __device__ __forceinline__ void stage_params_body(const MeshDev& m, int np, Stag
     sp->t = t;
     sp->delta = delta;
     sp->n = n;
+    {
+      const long long r = n % m.ny;
+      sp->n_mod = (int)(r < 0 ? r + m.ny : r);
+    }
     sp->s = s;
     sp->sig_s = __dsub_rn(two_s, 1.0);
     sp->sig_m = __dsub_rn(1.0, two_s);
@@ -129,6 +133,18 @@ __device__ __forceinline__ void stage_params_body(const MeshDev& m, int np, Stag
       sp->mat_f[slot][ij] = (float)v;
     }
     __syncthreads();
+  }
+  // the FP32 pair tables (zero in the padding)
+  const int mr = sm_pair_row(np), mt = sm_pair_stride(np);
+  for (int r = threadIdx.x; r < 4 * mt; r += blockDim.x) {
+    const int g = r / mt, rem = r - g * mt, pr = rem >> 1, h = rem & 1;
+    const int row = pr / mr, col = pr - row * mr;
+    float v = 0.f;
+    if (row < np && col < np) {
+      const int k = g == 0 ? (h ? 3 : 0) : (g == 1 ? (h ? 2 : 1) : 4 + 2 * (g - 2) + h);
+      v = sp->mat_f[k][col * np + row];
+    }
+    sp->pair_f[r] = v;
   }
 }
 
