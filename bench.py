@@ -111,6 +111,15 @@ def source_sha(paths):
 
 ELEMENT_SOURCES = ["paper_2008_04356_gb300/csrc/sm_element.cuh", "paper_2008_04356_gb300/csrc/sm_common.cuh"]
 
+# FP64 operations the plain FP64 path executes per DOF-update (N = 5, Rusanov), averaged over
+# the five stages of a step: DFMA x 2 + DADD + DMUL counted with ncu on the element kernel
+# (422 per DOF in a stage, 412 in the first stage, which reads no RK register), plus the
+# interface kernel's share (16 per DOF of the 2 x 4 x 256 x 8 capture, 4 cells per face along x).
+FP64_FLOP_PER_DOF = (4 * 422.4 + 412.4) / 5 + 16.1
+# FP64 peak of one GB300: 152 SMs x 2 DFMA per clock x 2 flop x 2.07 GHz (the nominal
+# 1.25 TFLOP/s; a dependent-chain DFMA probe measured 1.0 TFLOP/s at about 1990 MHz)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
 
 def measured_peaks():
     try:
@@ -450,6 +459,7 @@ def main():
     torch.cuda.synchronize()
     ms64 = max_over_ranks(f0.elapsed_time(f1))
     value64 = world * p64.ndof * 5 * args.fp64_steps / (ms64 * 1e-3)
+    gflops64 = value64 / world * FP64_FLOP_PER_DOF / 1e9
     s64.close()
     del s64
 
@@ -479,12 +489,17 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": p.nelem, "N": p.N, "dof": p.ndof,
                    "sliding_faces_per_side": p.n_faces, "state_bytes": p.ndof * 5 * 4,
-                   "riemann": "rusanov", "l2": "inputs larger than L2 (2.26 GB state per buffer)",
+                   "riemann": "rusanov",
+                   "l2": "inputs %s L2 (%.2f GB state per buffer, L2 129 MB)" % (
+                       "larger than" if p.ndof * 5 * 4 > 129e6 else "NOT larger than", p.ndof * 5 * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "dt": dt, "final_t": d["t"]},
         "interface_face_updates_per_s": face_rate,
         "fp64_plain": {"value": value64, "unit": UNIT, "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps,
-                       "fp32_over_fp64": value / value64},
+                       "fp32_over_fp64": value / value64,
+                       "roofline": {"bound": "alu", "achieved": gflops64, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                                    "frac": gflops64 / FP64_PEAK_GFLOPS, "flop_per_dof_update": FP64_FLOP_PER_DOF,
+                                    "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "kernel": "dg_element_kernel<N=5, float, Rusanov, stage>",
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": elem_bytes,
