@@ -108,6 +108,25 @@ def test_interface_fp64(sm, N, riemann):
         sol.close()
 
 
+@pytest.mark.parametrize("riemann", [synth.RUSANOV, synth.ROE_HH])
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 7])
+def test_interface_fp32(sm, N, riemann):
+    """FP32 interface fluxes (register-fused tile at odd N, staged tile at even N) against
+    the oracle: tiles of 8 faces with a ragged last tile (11, 17, 40), a single short tile
+    (4), one face (1), partner offsets that wrap both ways, and the conforming instant."""
+    for ny, delta0, t in ((11, 0.3337, 0.21), (4, 0.0, 0.0), (17, -2.71, 0.05), (1, 0.4, 0.0), (40, 5.123, 0.3)):
+        p = ragged_box(N, riemann, ny=ny, delta0=delta0, prec=synth.FP32)
+        o = O.Oracle(p)
+        U = synth.random_state(p, seed=N * 10 + ny).astype(np.float32)
+        Fs_ref, Fm_ref = o.interface_fluxes(U.astype(np.float64), t)
+        sol = sm.Solver(p)
+        Fs, Fm = sol.interface(to_dev(U, torch.float32), t)
+        torch.cuda.synchronize()
+        assert rel_l2(Fs.cpu().numpy(), Fs_ref) < FP32_TOL, (ny, "static")
+        assert rel_l2(Fm.cpu().numpy(), Fm_ref) < FP32_TOL, (ny, "moving")
+        sol.close()
+
+
 # ------------------------------------------------------------------ full right-hand side
 @pytest.mark.parametrize("riemann", [synth.RUSANOV, synth.ROE_HH])
 @pytest.mark.parametrize("N", range(1, 8))
@@ -211,6 +230,43 @@ def test_step_fp32_vs_oracle(sm):
     sol.step(dt, 100)
     Ug, _ = sol.get_state()
     assert rel_l2(Ug.cpu().numpy(), Uo) < FP32_TOL
+
+
+@pytest.mark.parametrize("N", [3, 5, 7])
+def test_step_fp32_ragged_tiles(sm, N):
+    """FP32 steps through the compact interface traces (the stepping path of the interface
+    kernel): 37 faces along the sliding direction (4 full tiles and a ragged one), moving
+    block crossing several faces, against the oracle."""
+    p = ragged_box(N, synth.RUSANOV, ny=37, nz=2, delta0=1.93, v=0.9, prec=synth.FP32)
+    o = O.Oracle(p)
+    U0 = o.init_state()
+    dt = synth.cfl_dt(p)
+    Uo, Go = U0.copy(), np.zeros_like(U0)
+    o.step(Uo, Go, 0.0, dt, 6)
+    sol = sm.Solver(p)
+    sol.set_state(U0.astype(np.float32), 0.0)
+    sol.step(dt, 6)
+    Ug, _ = sol.get_state()
+    assert rel_l2(Ug.cpu().numpy(), Uo) < FP32_TOL
+    sol.close()
+
+
+def test_step_fp32_interface_ring_wraps(sm):
+    """More interface tiles than resident CTAs (2 x 4 x 256 x 32 elements, N = 5: 1,024
+    tiles of 8 faces), so every CTA of the persistent FP32 interface kernel cycles its
+    three trace buffers; one RK step against the oracle."""
+    p = synth.config_interface_heavy(seed=3, precision=synth.FP32, nz=32)
+    o = O.Oracle(p)
+    U0 = o.init_state()
+    dt = synth.cfl_dt(p)
+    Uo, Go = U0.copy(), np.zeros_like(U0)
+    o.step(Uo, Go, 0.0, dt, 1)
+    sol = sm.Solver(p)
+    sol.set_state(U0.astype(np.float32), 0.0)
+    sol.step(dt, 1)
+    Ug, _ = sol.get_state()
+    assert rel_l2(Ug.cpu().numpy(), Uo) < FP32_TOL
+    sol.close()
 
 
 def test_init_state_matches_oracle(sm):
