@@ -102,6 +102,37 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+class Replicas:
+    """Bookkeeping of N independent replicas of the workload, one per rank (the path does not
+    shard: no collective on the data path).  Only the timing needs the ranks: a barrier
+    around the timed region and the maximum of the per-rank times, over NCCL on GPUs or
+    gloo on CPUs; the whole-job value is N x the units one rank processes / that maximum."""
+
+    def __init__(self, world: int, device=None):
+        self.world = world
+        self.device = device
+
+    def barrier(self):
+        import torch
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        if self.device is not None and self.device.type == "cuda":
+            torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def value(self, units_per_rank: float, seconds: float) -> float:
+        return self.world * units_per_rank / seconds
+
+
 def source_sha(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -313,7 +344,11 @@ def run_cylinder(args, rank, world, local):
     curvilinear kernels (interface lifting, lifting, viscous interface flux, element)."""
     import torch
     from paper_2008_04356_gb300 import build as B, slidemesh, synth
+    import torch.distributed as dist
     torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rep = Replicas(world, torch.device("cuda", local))
     B.build_library()
     stream = torch.cuda.current_stream()
     prec = synth.FP64 if args.precision == "fp64" else synth.FP32
@@ -323,18 +358,19 @@ def run_cylinder(args, rank, world, local):
     sol.init_state()
     dt = synth.cfl_dt(p)
     sol.step(dt, args.warmup)
-    torch.cuda.synchronize()
+    rep.barrier()
     clocks = ClockSampler(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
+    rep.barrier()
     e0.record(stream)
     sol.step(dt, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    rep.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    value = world * p.ndof * 5 * args.steps / (ms * 1e-3)
+    ms = rep.max(e0.elapsed_time(e1))
+    value = rep.value(p.ndof * 5 * args.steps, ms * 1e-3)
     kms, kcnt = sol.step_profiled(dt, args.profile_steps)
     sb = 8 if prec == synth.FP64 else 4
     # element kernel per DOF-update: U in/out, G in (4 of 5 stages)/out, 13 geometry values,
@@ -346,6 +382,9 @@ def run_cylinder(args, rank, world, local):
     achieved = elem_bytes / (elem_ms * 1e-3) / 1e9
     d = sol.diag()
     if rank != 0:
+        sol.close()
+        if world > 1:
+            dist.destroy_process_group()
         return
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -355,8 +394,8 @@ def run_cylinder(args, rank, world, local):
                    "sliding_faces_per_side": p.n_faces, "riemann": "rusanov", "mu": p.mu,
                    "l2": "inputs larger than L2 (%.2f GB state + %.2f GB geometry)" % (
                        p.ndof * 5 * sb / 1e9, p.ndof * 13 * sb / 1e9),
-                   "parallelism": "single GPU", "dt": dt, "final_t": d["t"]},
-        "interface_face_updates_per_s": p.n_faces * 5 * args.steps / (ms * 1e-3),
+                   "parallelism": "replicas" if world > 1 else "single GPU", "dt": dt, "final_t": d["t"]},
+        "interface_face_updates_per_s": rep.value(p.n_faces * 5 * args.steps, ms * 1e-3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "kernel": "curved_element_kernel<N=7, %s, Rusanov, stage, NS>" % (
                          "double" if prec == synth.FP64 else "float"),
@@ -371,6 +410,8 @@ def run_cylinder(args, rank, world, local):
     }
     sol.close()
     print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():
@@ -399,17 +440,8 @@ def main():
     B.build_library()
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    rep = Replicas(world, torch.device("cuda", local))
+    barrier, max_over_ranks = rep.barrier, rep.max
 
     p = synth.config_interface_heavy(seed=1 + rank, precision=synth.FP32, nz=args.nz)
     sol = slidemesh.Solver(p)
@@ -428,9 +460,8 @@ def main():
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
-    dof_updates = world * p.ndof * 5 * args.steps
-    value = dof_updates / (ms * 1e-3)
-    face_rate = world * p.n_faces * 5 * args.steps / (ms * 1e-3)
+    value = rep.value(p.ndof * 5 * args.steps, ms * 1e-3)
+    face_rate = rep.value(p.n_faces * 5 * args.steps, ms * 1e-3)
     d = sol.diag()
 
     # per-kernel device times of the same stage sequence (event pairs around each launch)
