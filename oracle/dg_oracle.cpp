@@ -414,6 +414,44 @@ void orc_viscous_flux(const double* U, const double* g, double mu, double Pr, do
   }
 }
 
+/* Two-point volume fluxes of the split-form DGSEM (Sec. 3.1: the split formulation of
+ * Pirozzoli).  Reading: Pirozzoli's split of the convective terms d(rho w phi)/dx_n with
+ * phi in {1, v, H}, the advecting velocity w = v.n - v^g.n being the velocity relative to
+ * the moving grid (the ALE form of Sec. 2), written in two-point form as products of
+ * arithmetic means {{a}} = (a_L + a_R) / 2:
+ *   F#_rho = {{rho}} {{w}},   F#_rho v = F#_rho {{v}} + {{p}} n,   F#_rho e = F#_rho {{H}} + {{p}} v^g.n,
+ * with the total enthalpy H = (rho e + p) / rho.  For U_L = U_R this is the ALE flux of
+ * Eq. fluxes_written_out, F.n - (v^g.n) U, because rho H v^g.n - p v^g.n = rho e v^g.n.
+ * kind 1 is the central flux (F(U_L) + F(U_R)) / 2, with which the split form equals the
+ * weak form (summation-by-parts property of the LGL derivative). */
+void orc_two_point_flux(int kind, const double* UL, const double* UR, const double* n, double vgn,
+                        double gamma, double* F) {
+  if (kind == 1) {
+    double FL[5], FR[5];
+    orc_euler_flux(UL, n, vgn, gamma, FL);
+    orc_euler_flux(UR, n, vgn, gamma, FR);
+    for (int k = 0; k < 5; ++k) F[k] = 0.5 * (FL[k] + FR[k]);
+    return;
+  }
+  const double* S[2] = {UL, UR};
+  double rho[2], vel[2][3], p[2], H[2];
+  for (int s = 0; s < 2; ++s) {
+    rho[s] = S[s][0];
+    for (int a = 0; a < 3; ++a) vel[s][a] = S[s][1 + a] / rho[s];
+    double q2 = vel[s][0] * vel[s][0] + vel[s][1] * vel[s][1] + vel[s][2] * vel[s][2];
+    p[s] = (gamma - 1.0) * (S[s][4] - 0.5 * rho[s] * q2);
+    H[s] = (S[s][4] + p[s]) / rho[s];
+  }
+  double rho_m = 0.5 * (rho[0] + rho[1]), p_m = 0.5 * (p[0] + p[1]), H_m = 0.5 * (H[0] + H[1]);
+  double v_m[3];
+  for (int a = 0; a < 3; ++a) v_m[a] = 0.5 * (vel[0][a] + vel[1][a]);
+  double w_m = v_m[0] * n[0] + v_m[1] * n[1] + v_m[2] * n[2] - vgn;
+  double f_rho = rho_m * w_m;
+  F[0] = f_rho;
+  for (int a = 0; a < 3; ++a) F[1 + a] = f_rho * v_m[a] + p_m * n[a];
+  F[4] = f_rho * H_m + p_m * vgn;
+}
+
 /* Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients, the scheme
  * Sec. 3.1 names for time integration (values are not printed in the paper):
  *   G = A_k G + dt R(U, t + c_k dt);  U = U + B_k G. */
@@ -849,12 +887,66 @@ void face_flux_out(const Oracle& o, const Interface* I, const double* U, const d
     }
 }
 
+/* Split-form DGSEM residual of one element (Sec. 3.1, the split formulation with
+ * Pirozzoli's flux), on a Cartesian element, where the contravariant two-point flux of
+ * direction xi^{d+1} is |Ja^d| F#(U_a, U_b) along that direction's physical axis.  Strong
+ * form, the volume term carried by the two-point flux:
+ *   J dU/dt = - sum_d sum_l 2 D_il |Ja^d| F#^d(U_node, U_l)        (l along xi^{d+1})
+ *             - sum_faces ell(+-1)/w (F* . N - F(U_node) . N) sJ ,
+ * the surface term being the Riemann flux minus the node's own flux. */
+void split_element_residual(const Oracle& o, const Interface* I, const double* U, double t, long long e,
+                            const std::vector<double>* Fs, const std::vector<double>* Fm, double* Ut_e) {
+  ElemId id = elem_id(o, e);
+  int np = o.np, nn = o.nn, nq = np * np;
+  int kind = o.p.volume == 2 ? 1 : 0;
+  for (int k = 0; k < np; ++k)
+    for (int j = 0; j < np; ++j)
+      for (int i = 0; i < np; ++i) {
+        int node = i + np * (j + np * k);
+        double u[5], ul[5], f[5], n[3], acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * nn + node];
+        for (int d = 0; d < 3; ++d) {
+          unit_normal(d, n);
+          double vgn = grid_vel(o, id.blk, d), a = metric(o, id.blk, d);
+          int row = d == 0 ? i : (d == 1 ? j : k);
+          for (int l = 0; l < np; ++l) {
+            int nl = d == 0 ? l + np * (j + np * k) : (d == 1 ? i + np * (l + np * k) : i + np * (j + np * l));
+            for (int v = 0; v < 5; ++v) ul[v] = U[(e * 5 + v) * nn + nl];
+            orc_two_point_flux(kind, u, ul, n, vgn, o.p.gamma, f);
+            for (int v = 0; v < 5; ++v) acc[v] += 2.0 * o.D[row * np + l] * a * f[v];
+          }
+        }
+        for (int v = 0; v < 5; ++v) Ut_e[v * nn + node] = -acc[v];
+      }
+  std::vector<double> Fout(5 * nq);
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side) {
+      face_flux_out(o, I, U, nullptr, t, e, d, side, Fs, Fm, Fout.data());
+      double wend = o.w[side == 0 ? 0 : o.N], sJ = metric(o, id.blk, d), sg = side == 1 ? 1.0 : -1.0;
+      double n[3], u[5], f[5];
+      unit_normal(d, n);
+      for (int b = 0; b < np; ++b)
+        for (int a = 0; a < np; ++a) {
+          int node = face_node_to_vol(o, d, side, a, b);
+          for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * nn + node];
+          orc_euler_flux(u, n, grid_vel(o, id.blk, d), o.p.gamma, f);
+          for (int v = 0; v < 5; ++v) Ut_e[v * nn + node] -= (Fout[v * nq + a + np * b] - sg * sJ * f[v]) / wend;
+        }
+    }
+  double invJ = 1.0 / jacobian(o, id.blk);
+  for (int k = 0; k < 5 * nn; ++k) Ut_e[k] *= invJ;
+}
+
 /* Weak-form DGSEM residual of one element (Eq. weak_formulation with LGL collocation):
  *   J dU/dt = - [ sum_l Dhat_il F~1_ljk + sum_l Dhat_jl F~2_ilk + sum_l Dhat_kl F~3_ijl ]
  *             - sum_faces ell(+-1)/w * (F* . N) sJ ,
  * with Dhat_il = -(w_l / w_i) D_li and contravariant fluxes F~d = |Ja^d| (F - v^g U) . e. */
 void element_residual(const Oracle& o, const Interface* I, const double* U, const double* grad, double t, long long e,
                       const std::vector<double>* Fs, const std::vector<double>* Fm, double* Ut_e) {
+  if (o.p.volume != 0) {
+    split_element_residual(o, I, U, t, e, Fs, Fm, Ut_e);
+    return;
+  }
   ElemId id = elem_id(o, e);
   int np = o.np, nn = o.nn, nq = np * np;
   std::vector<double> Ft(3 * 5 * nn);
@@ -1036,9 +1128,10 @@ extern "C" {
 static bool curved(void* h) { return *(int*)h == 1; }
 
 void* orc_create(const orc_problem* p) {
-  if (p->geom != 0) return orc_curved_create(p);
+  if (p->geom != 0) return p->volume != 0 ? nullptr : orc_curved_create(p);
   if (p->N < 1 || p->N > 15) return nullptr;
   if (p->nel_s[1] != p->nel_m[1] || p->nel_s[2] != p->nel_m[2]) return nullptr;
+  if (p->volume < 0 || p->volume > 2 || (p->volume != 0 && p->physics != 0)) return nullptr;
   Oracle* o = new Oracle();
   o->p = *p;
   o->N = p->N; o->np = p->N + 1; o->nn = o->np * o->np * o->np;

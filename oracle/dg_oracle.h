@@ -41,6 +41,10 @@ typedef struct {
   int geom;              /* 0 plane interface (Cartesian operator); 1 cylindrical interface
                             (curvilinear operator); 2 plane interface through the
                             curvilinear operator (general metrics) */
+  int volume;            /* volume integral (Sec. 3.1): 0 weak form; 1 split form with
+                            Pirozzoli's two-point flux; 2 split form with the central
+                            two-point flux (equal to the weak form by summation by parts).
+                            The split forms take geom 0 and Euler physics. */
 } orc_problem;
 
 /* geom 1, the cylindrical sliding interface of Sec. 3.3 (a rotor inside the circle):
@@ -73,6 +77,9 @@ void orc_mortar_mats(int N, double sigma, double* P_lo, double* P_hi, double* B_
 void orc_euler_flux(const double* U, const double* n, double vgn, double gamma, double* F);
 void orc_riemann(int kind, const double* UL, const double* UR, const double* n, double vgn,
                  double gamma, double* F);
+/* two-point volume flux of the split form (kind 0 Pirozzoli, 1 central), Sec. 3.1 */
+void orc_two_point_flux(int kind, const double* UL, const double* UR, const double* n, double vgn,
+                        double gamma, double* F);
 
 /* ---- low-storage RK (Carpenter & Kennedy (5,4), Sec. 3.1) ---- */
 void orc_lsrk_coeffs(double* A, double* B, double* c);

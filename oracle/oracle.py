@@ -30,7 +30,7 @@ class OrcProblem(C.Structure):
                 ("riemann", C.c_int), ("interface_conforming", C.c_int), ("flow", C.c_int),
                 ("fpar", C.c_double * 16), ("modes", C.c_double * 160),
                 ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double),
-                ("geom", C.c_int)]
+                ("geom", C.c_int), ("volume", C.c_int)]
 
 
 _LIB = None
@@ -52,6 +52,7 @@ def lib():
         L.orc_mortar_mats.argtypes = [C.c_int, C.c_double, _dp, _dp, _dp, _dp]
         L.orc_euler_flux.argtypes = [_dp, _dp, C.c_double, C.c_double, _dp]
         L.orc_riemann.argtypes = [C.c_int, _dp, _dp, _dp, C.c_double, C.c_double, _dp]
+        L.orc_two_point_flux.argtypes = [C.c_int, _dp, _dp, _dp, C.c_double, C.c_double, _dp]
         L.orc_lsrk_coeffs.argtypes = [_dp, _dp, _dp]
         L.orc_create.argtypes = [C.POINTER(OrcProblem)]
         L.orc_create.restype = C.c_void_p
@@ -158,6 +159,16 @@ def riemann(kind, UL, UR, n, vgn=0.0, gamma=1.4):
     return F
 
 
+def two_point_flux(kind, UL, UR, n, vgn=0.0, gamma=1.4):
+    """Split-form volume flux F#(UL, UR) along n: kind 0 Pirozzoli, 1 central."""
+    UL = np.ascontiguousarray(UL, dtype=np.float64)
+    UR = np.ascontiguousarray(UR, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    F = np.zeros(5)
+    lib().orc_two_point_flux(int(kind), _p(UL), _p(UR), _p(n), float(vgn), float(gamma), _p(F))
+    return F
+
+
 def viscous_flux(U, grad15, mu, Pr, Rgas, gamma=1.4):
     U = np.ascontiguousarray(U, dtype=np.float64)
     g = np.ascontiguousarray(grad15, dtype=np.float64)
@@ -194,6 +205,7 @@ def to_orc_problem(p) -> OrcProblem:
     s.physics = int(p.physics)
     s.mu, s.Pr, s.Rgas = float(p.mu), float(p.Pr), float(p.Rgas)
     s.geom = int(getattr(p, "geom", 0))
+    s.volume = int(getattr(p, "volume", 0))
     return s
 
 

@@ -26,6 +26,7 @@ GEOM_PLANE, GEOM_CYLINDER, GEOM_PLANE_CURVILINEAR = 0, 1, 2
 EULER, NAVIER_STOKES = 0, 1
 RUSANOV, ROE_HH = 0, 1
 FP64, FP32 = 0, 1
+VOLUME_WEAK, VOLUME_SPLIT = 0, 1       # weak-form DGSEM; split form with Pirozzoli's flux
 
 
 def splitmix64(counters: np.ndarray) -> np.ndarray:
@@ -82,6 +83,7 @@ class Problem:
     Pr: float = 0.72
     Rgas: float = 1.0
     geom: int = GEOM_PLANE
+    volume: int = VOLUME_WEAK
 
     @property
     def np_(self) -> int:
