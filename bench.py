@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=256, help="elements along z (256 = the full workload)")
     ap.add_argument("--workload", choices=["interface-heavy", "serving", "cylinder"], default="interface-heavy")
+    ap.add_argument("--volume", choices=["weak", "split"], default="weak",
+                    help="volume integral of the interface-heavy headline: weak form, or the split form")
+    ap.add_argument("--riemann", choices=["rusanov", "roe"], default=None,
+                    help="Riemann solver of the headline (default: Rusanov for the weak form, Roe/HH for the split form)")
+    ap.add_argument("--split-steps", type=int, default=20,
+                    help="timed steps of the split-form (Pirozzoli, Roe/HH) solve beside the weak-form headline; 0: skip")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32", help="cylinder workload state precision")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--serve-steps", type=int, default=100)
@@ -172,7 +178,7 @@ def ncu_traffic():
     return rec.get("dram_bytes_per_launch_full_workload")
 
 
-def cpu_baseline(seconds: float):
+def cpu_baseline(seconds: float, volume: int = 0, riemann: int = 0):
     """The FP64 oracle, as it stands, on the host cores: whole RK steps of the same workload
     with fewer elements along z (bounded sample)."""
     import numpy as np
@@ -180,6 +186,7 @@ def cpu_baseline(seconds: float):
     from paper_2008_04356_gb300 import synth
     nz = 4
     p = synth.config_interface_heavy(seed=1, precision=synth.FP64, nz=nz)
+    p.volume, p.riemann = volume, riemann
     o = O.Oracle(p)
     U = o.init_state()
     G = np.zeros_like(U)
@@ -206,7 +213,11 @@ def run_reference(args, rank):
     from oracle import oracle as O
     from paper_2008_04356_gb300 import synth
     # size the sample so that (warmup + steps) whole RK steps take about two minutes
+    volume = synth.VOLUME_SPLIT if args.volume == "split" else synth.VOLUME_WEAK
+    riemann = synth.ROE_HH if (args.riemann or ("roe" if args.volume == "split" else "rusanov")) == "roe" \
+        else synth.RUSANOV
     probe = synth.config_interface_heavy(seed=1, precision=synth.FP64, nz=1)
+    probe.volume, probe.riemann = volume, riemann
     o = O.Oracle(probe)
     U = o.init_state()
     G = np.zeros_like(U)
@@ -217,6 +228,7 @@ def run_reference(args, rank):
     budget = 120.0 / max(1, args.steps + args.warmup)
     nz = int(max(1, min(256, budget / max(per_nz, 1e-6))))
     p = synth.config_interface_heavy(seed=1, precision=synth.FP64, nz=nz)
+    p.volume, p.riemann = volume, riemann
     o = O.Oracle(p)
     U = o.init_state()
     G = np.zeros_like(U)
@@ -444,6 +456,11 @@ def main():
     barrier, max_over_ranks = rep.barrier, rep.max
 
     p = synth.config_interface_heavy(seed=1 + rank, precision=synth.FP32, nz=args.nz)
+    p.volume = synth.VOLUME_SPLIT if args.volume == "split" else synth.VOLUME_WEAK
+    riem = args.riemann or ("roe" if args.volume == "split" else "rusanov")
+    p.riemann = synth.ROE_HH if riem == "roe" else synth.RUSANOV
+    kname = "%s<N=5, float, %s, stage>" % ("dg_element_split_kernel" if args.volume == "split" else "dg_element_kernel",
+                                          "Roe/HH" if riem == "roe" else "Rusanov")
     sol = slidemesh.Solver(p)
     sol.init_state()
     dt = synth.cfl_dt(p)
@@ -479,6 +496,7 @@ def main():
 
     # FP64 plain path, same workload, one solve
     p64 = synth.config_interface_heavy(seed=1 + rank, precision=synth.FP64, nz=args.nz)
+    p64.volume, p64.riemann = p.volume, p.riemann
     s64 = slidemesh.Solver(p64)
     s64.init_state()
     s64.step(dt, 1)
@@ -493,6 +511,38 @@ def main():
     gflops64 = value64 / world * FP64_FLOP_PER_DOF / 1e9
     s64.close()
     del s64
+
+    # the split-form volume integral with Roe/HH (the paper's scheme), same workload, FP32
+    split = None
+    if args.volume == "weak" and args.split_steps > 0:
+        ps = synth.config_interface_heavy(seed=1 + rank, precision=synth.FP32, nz=args.nz)
+        ps.volume, ps.riemann = synth.VOLUME_SPLIT, synth.ROE_HH
+        ss = slidemesh.Solver(ps)
+        ss.init_state()
+        ss.step(dt, 3)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        ss.step(dt, args.split_steps)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        mss = max_over_ranks(g0.elapsed_time(g1))
+        skms, skcnt = ss.step_profiled(dt, max(2, args.profile_steps // 2))
+        sel_ms = skms[2] / skcnt[2]
+        sach = elem_bytes / (sel_ms * 1e-3) / 1e9
+        split = {"value": rep.value(ps.ndof * 5 * args.split_steps, mss * 1e-3), "unit": UNIT,
+                 "steps": args.split_steps, "ms_per_step": mss / args.split_steps,
+                 "volume": "split form, Pirozzoli two-point flux", "riemann": "roe_hh",
+                 "roofline": {"bound": "hbm", "achieved": sach, "peak": hbm, "unit": "GB/s", "frac": sach / hbm,
+                              "kernel": "dg_element_split_kernel<N=5, float, Roe/HH, stage>",
+                              "peak_source": peak_kind, "algorithmic_bytes_per_launch": elem_bytes,
+                              "avg_launch_ms": sel_ms},
+                 "kernels": {"stage_params": {"launches": skcnt[0], "ms": skms[0]},
+                             "sliding_interface": {"launches": skcnt[1], "ms": skms[1]},
+                             "dg_element_split": {"launches": skcnt[2], "ms": skms[2], "avg_ms": sel_ms}},
+                 "diag_finite": ss.diag()["status"] == 0}
+        ss.close()
+        del ss
 
     # end to end through the C-ABI with host buffers: state in (pinned), one step, state out
     Uh, _ = sol.get_state(out=torch.empty(sol.shape(), dtype=torch.float32, pin_memory=True))
@@ -520,7 +570,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": p.nelem, "N": p.N, "dof": p.ndof,
                    "sliding_faces_per_side": p.n_faces, "state_bytes": p.ndof * 5 * 4,
-                   "riemann": "rusanov",
+                   "riemann": "roe_hh" if riem == "roe" else "rusanov",
+                   "volume": "split form, Pirozzoli two-point flux" if args.volume == "split" else "weak form",
                    "l2": "inputs %s L2 (%.2f GB state per buffer, L2 129 MB)" % (
                        "larger than" if p.ndof * 5 * 4 > 129e6 else "NOT larger than", p.ndof * 5 * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -532,7 +583,8 @@ def main():
                                     "frac": gflops64 / FP64_PEAK_GFLOPS, "flop_per_dof_update": FP64_FLOP_PER_DOF,
                                     "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic, "kernel": "dg_element_kernel<N=5, float, Rusanov, stage>",
+                     "traffic": traffic if args.volume == "weak" and riem == "rusanov" else None,
+                     "kernel": kname,
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": elem_bytes,
                      "avg_launch_ms": elem_ms},
         "kernels": {"stage_params": {"launches": kcnt[0], "ms": kms[0]},
@@ -545,8 +597,10 @@ def main():
         "clocks": clk,
         "diag": {"n_delta": d["n_delta"], "s_delta": d["s_delta"], "finite": d["status"] == 0},
     }
+    if split is not None:
+        line["split_form"] = split
     if not args.no_cpu_baseline and world >= 1:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, p.volume, p.riemann)
     sol.close()
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -49,6 +49,16 @@ enum { SM_FP64 = 0, SM_FP32 = 1 };
 enum { SM_RUSANOV = 0, SM_ROE_HH = 1 };
 enum { SM_GEOM_PLANE = 0, SM_GEOM_CYLINDER = 1, SM_GEOM_PLANE_CURVILINEAR = 2 };
 enum { SM_EULER = 0, SM_NAVIER_STOKES = 1 };
+/* Volume integral of the element operator (Sec. 3.1):
+ *  SM_VOLUME_WEAK   weak-form DGSEM, sum-factorised flux divergence with Dhat = -M^-1 D^T M;
+ *  SM_VOLUME_SPLIT  split form with Pirozzoli's two-point flux (the scheme of all of the
+ *                   paper's computations, used there with SM_ROE_HH): strong form, volume
+ *                   term sum_l (2 D - M^-1 B)_il F#(U_i, U_l) per direction with
+ *                   F#_rho = {{rho}}{{w}}, F#_rho v = F#_rho {{v}} + {{p}} n,
+ *                   F#_rho e = F#_rho {{H}} + {{p}} v^g.n, {{a}} the arithmetic mean,
+ *                   w = v.n - v^g.n the velocity relative to the grid, H the total enthalpy.
+ *                   Plane geometry (SM_GEOM_PLANE) and Euler physics only. */
+enum { SM_VOLUME_WEAK = 0, SM_VOLUME_SPLIT = 1 };
 /* Flows used as initial data (sm_init_state) and as the weak Dirichlet state at x = x0, x2
  * (SM_FLOW_SHEAR_X: rho = fpar0, p = fpar1, velocity (0, 0, fpar2 + fpar3 x + fpar4 x^2)):
  *  SM_FLOW_CONSTANT      primitive (rho, v1, v2, v3, p) = fpar[0..4]
@@ -97,6 +107,7 @@ typedef struct {
   double modes[5][8][4];
   int physics;             /* SM_EULER | SM_NAVIER_STOKES (BR1 lifting, Sec. 3.1) */
   double mu, Pr, Rgas;     /* dynamic viscosity, Prandtl number, gas constant */
+  int volume;              /* SM_VOLUME_WEAK | SM_VOLUME_SPLIT */
 } sm_mesh_desc;
 
 /* Motion of the moving block: displacement Delta(t) = delta0 + v t along +y (Sec. 4.3,

@@ -20,6 +20,7 @@ struct BasisDev {
   double Dhat[SM_MAXNP * SM_MAXNP];
   float Dhat_f[SM_MAXNP * SM_MAXNP];
   float x_f[SM_MAXNP], w_f[SM_MAXNP];
+  double Dsplit[SM_MAXNP * SM_MAXNP];   // split form: 2 D - M^-1 B (zero diagonal)
 };
 
 // Per-stage interface configuration (Sec. 4.3) and mortar operators (Sec. 3.2), written by

@@ -151,83 +151,20 @@ __device__ __forceinline__ void contract_lines_inplace(T* sF, int tid) {
   }
 }
 
-// The work of one CTA: elements e0 .. e0+EPB-1 of one solve.  Shared by the single-solve
-// kernel below and the batched persistent kernel.
-//
-// One barrier per element: before it, every thread computes its node's contravariant
-// fluxes into shared memory and one face-node Riemann flux (own and neighbour traces both
-// read from the state in global memory, the neighbour codes from the topology table), so
-// no thread needs another thread's result until the volume/surface phase after it.
-// PHYS 1 (Navier-Stokes) adds the viscous fluxes of the BR1-lifted gradients Gr
-// ([E][15][NN], component 5 d + c = d(primitive c)/dx_d): F^c - F^v in the volume and the
-// mean of both sides' viscous fluxes on conforming and boundary faces (Sec. 2, 3.1).
-template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
-__device__ __forceinline__ void element_block(const MeshDev& m, const StageParams* __restrict__ sp,
-                                              const T* __restrict__ U, T* __restrict__ out, T* __restrict__ G,
-                                              const T* __restrict__ Fs, const T* __restrict__ Fm, const T rkA,
-                                              const T rkB, const T dt, const long long e0,
-                                              const T* __restrict__ Gr = nullptr, T* __restrict__ Ts = nullptr,
-                                              T* __restrict__ Tm = nullptr) {
+// Face fluxes of the CTA's EPB elements (elements e0 ..), one work item per (element, face,
+// face node), into sS[EPB][6][5][NP^2] as outward fluxes times the surface element: conforming
+// and weak Dirichlet faces by the Riemann solver in canonical orientation (left = minus-side
+// element, normal +axis), sliding faces copied from the interface kernel's face fluxes.
+// Reads global memory only, so it runs before the CTA's first barrier.
+template <int N, typename T, int RIEM, int PHYS>
+__device__ __forceinline__ void element_face_fluxes(const MeshDev& m, const StageParams* __restrict__ sp,
+                                                    const T* __restrict__ U, const T* __restrict__ Fs,
+                                                    const T* __restrict__ Fm, const T* __restrict__ Gr,
+                                                    const long long e0, T* sS, const int tid) {
   using C = ElemCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // contravariant fluxes F~1, F~2, F~3, each in node order [v][k][j][i]
-  T* sF = reinterpret_cast<T*>(smem_raw);        // [EPB][3][5][NN]
-  T* sS = sF + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
-
   const T* c = Prec<T>::c(m);
-  const int tid = threadIdx.x;
-  const int le = tid / NN, nd = tid - le * NN;
-  const long long e = e0 + le;
-  const bool active = e < m.E;
-  const long long base = e * 5 * NN + nd;
   const T gamma = c[MC_GAMMA];
-
-  T u[5], g[5];
-  if (active) {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) u[v] = U[base + v * NN];
-    if (MODE == ELEM_STAGE) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) g[v] = G[base + v * NN];
-    }
-    const int blk = e >= m.Es;
-    const Prim<T> q = primitives(u, gamma);
-    T f[5];
-    T* Fe = sF + le * 15 * NN;
-    const T a0 = c[MC_METRIC + 3 * blk], a1 = c[MC_METRIC + 3 * blk + 1], a2 = c[MC_METRIC + 3 * blk + 2];
-    T gn[PHYS ? 15 : 1], fv[5];
-    if (PHYS) {
-#pragma unroll
-      for (int kk = 0; kk < 15; ++kk) gn[kk] = Gr[(e * 15 + kk) * NN + nd];
-    }
-    axis_flux<T, 1>(u, q, blk ? c[MC_VG] : T(0), f);          // xi^1 -> y (grid velocity)
-    if (PHYS) {
-      viscous_flux_axis(u, gn, 1, c, fv);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) f[v] -= fv[v];
-    }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[v * NN + nd] = a0 * f[v];
-    axis_flux<T, 2>(u, q, T(0), f);                             // xi^2 -> z
-    if (PHYS) {
-      viscous_flux_axis(u, gn, 2, c, fv);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) f[v] -= fv[v];
-    }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN + nd] = a1 * f[v];
-    axis_flux<T, 0>(u, q, T(0), f);                             // xi^3 -> x
-    if (PHYS) {
-      viscous_flux_axis(u, gn, 0, c, fv);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) f[v] -= fv[v];
-    }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN + nd] = a2 * f[v];
-  }
-
-  // ---- face fluxes: one work item per (element, face, face node) ----
   for (int w = tid; w < EPB * 6 * NP2; w += THREADS) {
     const int l2 = w / (6 * NP2);
     const int r = w - l2 * 6 * NP2;
@@ -317,21 +254,24 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
 #pragma unroll
     for (int v = 0; v < 5; ++v) sS[((l2 * 6 + fc) * 5 + v) * NP2 + ab] = Fo[v];
   }
+}
 
-  // ---- volume integral (sum factorisation) + surface integral ----
+// Surface integral at the element's face nodes, the 1/J scaling and (stage modes) the
+// low-storage RK update of node nd of element e, given the node's volume term acc:
+//   dU/dt = -(1/J) [ acc + (1/w_0) (outward face flux) ],
+//   G = A_k G + dt dU/dt,  U = U + B_k G  (ELEM_STAGE_FIRST: A_k G = 0),
+// and the interface node layers of the updated state for the next stage's interface kernel.
+template <int N, typename T, int MODE>
+__device__ __forceinline__ void element_surface_update(const MeshDev& m, const T* Se, T (&acc)[5], const int nd,
+                                                       const long long e, const long long base, const T (&u)[5],
+                                                       const T (&g)[5], T* __restrict__ out, T* __restrict__ G,
+                                                       const T rkA, const T rkB, const T dt, T* __restrict__ Ts,
+                                                       T* __restrict__ Tm) {
+  using C = ElemCfg<N>;
+  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN;
+  const T* c = Prec<T>::c(m);
   const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
-  T acc[5];
-  __syncthreads();
-  contract_lines_inplace<N, T>(sF, tid);
-  __syncthreads();
-  if (!active) return;
-  {
-    const T* Fe = sF + le * 15 * NN + nd;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = Fe[v * NN] + Fe[(5 + v) * NN] + Fe[(10 + v) * NN];
-  }
   const T iw0 = c[MC_IW0];
-  const T* Se = sS + le * 30 * NP2;
   if (i == 0 || i == N) {
     const T* s = Se + (i == 0 ? 0 : 1) * 5 * NP2 + j + NP * k;
 #pragma unroll
@@ -372,6 +312,98 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
       }
     }
   }
+}
+
+// The work of one CTA: elements e0 .. e0+EPB-1 of one solve.  Shared by the single-solve
+// kernel below and the batched persistent kernel.
+//
+// One barrier per element: before it, every thread computes its node's contravariant
+// fluxes into shared memory and one face-node Riemann flux (own and neighbour traces both
+// read from the state in global memory, the neighbour codes from the topology table), so
+// no thread needs another thread's result until the volume/surface phase after it.
+// PHYS 1 (Navier-Stokes) adds the viscous fluxes of the BR1-lifted gradients Gr
+// ([E][15][NN], component 5 d + c = d(primitive c)/dx_d): F^c - F^v in the volume and the
+// mean of both sides' viscous fluxes on conforming and boundary faces (Sec. 2, 3.1).
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
+__device__ __forceinline__ void element_block(const MeshDev& m, const StageParams* __restrict__ sp,
+                                              const T* __restrict__ U, T* __restrict__ out, T* __restrict__ G,
+                                              const T* __restrict__ Fs, const T* __restrict__ Fm, const T rkA,
+                                              const T rkB, const T dt, const long long e0,
+                                              const T* __restrict__ Gr = nullptr, T* __restrict__ Ts = nullptr,
+                                              T* __restrict__ Tm = nullptr) {
+  using C = ElemCfg<N>;
+  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // contravariant fluxes F~1, F~2, F~3, each in node order [v][k][j][i]
+  T* sF = reinterpret_cast<T*>(smem_raw);        // [EPB][3][5][NN]
+  T* sS = sF + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
+
+  const T* c = Prec<T>::c(m);
+  const int tid = threadIdx.x;
+  const int le = tid / NN, nd = tid - le * NN;
+  const long long e = e0 + le;
+  const bool active = e < m.E;
+  const long long base = e * 5 * NN + nd;
+  const T gamma = c[MC_GAMMA];
+
+  T u[5], g[5];
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = U[base + v * NN];
+    if (MODE == ELEM_STAGE) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) g[v] = G[base + v * NN];
+    }
+    const int blk = e >= m.Es;
+    const Prim<T> q = primitives(u, gamma);
+    T f[5];
+    T* Fe = sF + le * 15 * NN;
+    const T a0 = c[MC_METRIC + 3 * blk], a1 = c[MC_METRIC + 3 * blk + 1], a2 = c[MC_METRIC + 3 * blk + 2];
+    T gn[PHYS ? 15 : 1], fv[5];
+    if (PHYS) {
+#pragma unroll
+      for (int kk = 0; kk < 15; ++kk) gn[kk] = Gr[(e * 15 + kk) * NN + nd];
+    }
+    axis_flux<T, 1>(u, q, blk ? c[MC_VG] : T(0), f);          // xi^1 -> y (grid velocity)
+    if (PHYS) {
+      viscous_flux_axis(u, gn, 1, c, fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= fv[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fe[v * NN + nd] = a0 * f[v];
+    axis_flux<T, 2>(u, q, T(0), f);                             // xi^2 -> z
+    if (PHYS) {
+      viscous_flux_axis(u, gn, 2, c, fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= fv[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN + nd] = a1 * f[v];
+    axis_flux<T, 0>(u, q, T(0), f);                             // xi^3 -> x
+    if (PHYS) {
+      viscous_flux_axis(u, gn, 0, c, fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= fv[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN + nd] = a2 * f[v];
+  }
+
+  element_face_fluxes<N, T, RIEM, PHYS>(m, sp, U, Fs, Fm, Gr, e0, sS, tid);
+
+  // ---- volume integral (sum factorisation) + surface integral ----
+  T acc[5];
+  __syncthreads();
+  contract_lines_inplace<N, T>(sF, tid);
+  __syncthreads();
+  if (!active) return;
+  {
+    const T* Fe = sF + le * 15 * NN + nd;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] = Fe[v * NN] + Fe[(5 + v) * NN] + Fe[(10 + v) * NN];
+  }
+  element_surface_update<N, T, MODE>(m, sS + le * 30 * NP2, acc, nd, e, base, u, g, out, G, rkA, rkB, dt, Ts, Tm);
 }
 
 template <int N, typename T, int RIEM, int MODE, int PHYS = 0>

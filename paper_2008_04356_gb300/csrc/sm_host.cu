@@ -144,6 +144,10 @@ void lgl_basis(int N, BasisDev& b) {
       b.Dhat[i * SM_MAXNP + l] = dh;
       b.Dhat_f[i * SM_MAXNP + l] = (float)dh;
     }
+  // split form: Ds = 2 D - M^-1 B with the LGL weights, zero on the diagonal (D_ii = 0 at the
+  // interior nodes of the symmetric LGL set, 2 D_00 = -1/w_0 and 2 D_NN = 1/w_N at the ends)
+  for (int i = 0; i < np; ++i)
+    for (int l = 0; l < np; ++l) b.Dsplit[i * SM_MAXNP + l] = i == l ? 0.0 : 2.0 * D[i][l];
   for (int j = 0; j < np; ++j) {
     b.x_f[j] = (float)b.x[j];
     b.w_f[j] = (float)b.w[j];
@@ -312,16 +316,20 @@ cudaError_t ensure_dhat_constants() {
   if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_dhat_mu);
   if (g_dhat_done[dev]) return cudaSuccess;
-  static float f[7][SM_MAXNP * SM_MAXNP];
-  static double d[7][SM_MAXNP * SM_MAXNP];
+  static float f[7][SM_MAXNP * SM_MAXNP], fs[7][SM_MAXNP * SM_MAXNP];
+  static double d[7][SM_MAXNP * SM_MAXNP], ds[7][SM_MAXNP * SM_MAXNP];
   for (int n = 1; n <= 7; ++n) {
     BasisDev b;
     lgl_basis(n, b);
     for (int k = 0; k < SM_MAXNP * SM_MAXNP; ++k) {
       d[n - 1][k] = b.Dhat[k];
       f[n - 1][k] = b.Dhat_f[k];
+      ds[n - 1][k] = b.Dsplit[k];
+      fs[n - 1][k] = (float)b.Dsplit[k];
     }
   }
+  if ((e = upload_dsplit_f32(&fs[0][0], &ds[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dsplit_f64(&fs[0][0], &ds[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_batch(&f[0][0], &d[0][0])) != cudaSuccess) return e;
@@ -446,6 +454,9 @@ cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a0, cudaStream_t
     return s->prec == SM_FP64 ? launch_element_ns_f64(s->N, s->desc.riemann, mode, a, st)
                               : launch_element_ns_f32(s->N, s->desc.riemann, mode, a, st);
   }
+  if (s->desc.volume == SM_VOLUME_SPLIT)
+    return s->prec == SM_FP64 ? launch_element_split_f64(s->N, s->desc.riemann, mode, a, st)
+                              : launch_element_split_f32(s->N, s->desc.riemann, mode, a, st);
   return s->prec == SM_FP64 ? launch_element_f64(s->N, s->desc.riemann, mode, a, st)
                             : launch_element_f32(s->N, s->desc.riemann, mode, a, st);
 }
@@ -526,6 +537,9 @@ int valid_desc(const sm_mesh_desc* d) {
   if (d->physics != SM_EULER && d->physics != SM_NAVIER_STOKES) return fail(SM_ERR_ARG, "unknown physics");
   if (d->physics == SM_NAVIER_STOKES && !(d->mu >= 0.0 && d->Pr > 0.0 && d->Rgas > 0.0))
     return fail(SM_ERR_ARG, "Navier-Stokes needs mu >= 0, Pr > 0, Rgas > 0");
+  if (d->volume != SM_VOLUME_WEAK && d->volume != SM_VOLUME_SPLIT) return fail(SM_ERR_ARG, "unknown volume integral");
+  if (d->volume == SM_VOLUME_SPLIT && (d->geom != SM_GEOM_PLANE || d->physics != SM_EULER))
+    return fail(SM_ERR_UNSUPPORTED, "the split-form volume integral takes the plane interface and Euler physics");
   long long E = (long long)(d->nel_static[0] + d->nel_moving[0]) * d->nel_static[1] * d->nel_static[2];
   if (E > (1LL << 31)) return fail(SM_ERR_ARG, "too many elements");
   return SM_OK;
@@ -668,6 +682,9 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   else if ((e = cudaMemset(s->t_d, 0, sizeof(double))) != cudaSuccess) what = "clear t";
   else if ((e = cudaMemset(s->sp, 0, sizeof(StageParams))) != cudaSuccess) what = "clear stage params";
   else if ((e = (s->prec == SM_FP64 ? prepare_element_f64(s->N) : prepare_element_f32(s->N))) != cudaSuccess) what = "element kernel attributes";
+  else if (desc->volume == SM_VOLUME_SPLIT &&
+           (e = (s->prec == SM_FP64 ? prepare_element_split_f64(s->N) : prepare_element_split_f32(s->N))) != cudaSuccess)
+    what = "split-form kernel attributes";
   else if ((e = ensure_dhat_constants()) != cudaSuccess) what = "derivative constants";
   else if ((e = prepare_interface(s->N, s->prec)) != cudaSuccess) what = "interface kernel attributes";
   else if (desc->geom != SM_GEOM_PLANE &&
@@ -1012,6 +1029,7 @@ extern "C" int sm_batch_create(sm_solver* const* solvers, const double* dt, int 
     if (solvers[i]->prec != SM_FP32) return fail(SM_ERR_UNSUPPORTED, "batched kernels are FP32; step FP64 solvers with sm_step");
     if (solvers[i]->desc.physics != SM_EULER) return fail(SM_ERR_UNSUPPORTED, "batched kernels are Euler; step Navier-Stokes solvers with sm_step");
     if (solvers[i]->desc.geom != SM_GEOM_PLANE) return fail(SM_ERR_UNSUPPORTED, "batched kernels are for the plane interface");
+    if (solvers[i]->desc.volume != SM_VOLUME_WEAK) return fail(SM_ERR_UNSUPPORTED, "batched kernels take the weak-form volume integral");
   }
   sm_batch* b = new (std::nothrow) sm_batch();
   if (!b) return fail(SM_ERR_OOM, "host allocation");
@@ -1265,6 +1283,7 @@ extern "C" int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, 
   if (rc != SM_OK) return rc;
   if (desc->physics != SM_EULER) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes the Euler operator only");
   if (desc->geom != SM_GEOM_PLANE) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes the plane interface only");
+  if (desc->volume != SM_VOLUME_WEAK) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes the weak-form operator only");
   if (!motion || !dU || !dUt) return fail(SM_ERR_ARG, "NULL argument");
   if (dU == dUt) return fail(SM_ERR_ARG, "dU and dUt must not overlap");
   if (motion->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");

@@ -60,6 +60,16 @@ cudaError_t launch_element_f64(int N, int riemann, int mode, const ElemArgs& a, 
 cudaError_t prepare_element_f32(int N);
 cudaError_t prepare_element_f64(int N);
 
+// sm_elem_split_f32.cu / sm_elem_split_f64.cu: the split-form volume integral (Pirozzoli's
+// two-point flux) with the same faces, surface integral and RK update
+cudaError_t launch_element_split_f32(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t launch_element_split_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t prepare_element_split_f32(int N);
+cudaError_t prepare_element_split_f64(int N);
+// constant-memory Ds = 2 D - M^-1 B tables of the split kernels ([7][64], N = 1..7)
+cudaError_t upload_dsplit_f32(const float* f, const double* d);
+cudaError_t upload_dsplit_f64(const float* f, const double* d);
+
 // constant-memory Dhat tables of the element kernels ([7][64], N = 1..7), one copy per unit
 cudaError_t upload_dhat_f32(const float* f, const double* d);
 cudaError_t upload_dhat_f64(const float* f, const double* d);

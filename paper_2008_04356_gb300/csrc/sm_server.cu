@@ -49,7 +49,7 @@ size_t request_bytes(const sm_mesh_desc& d) {
 
 // FP32 Euler solves on the plane interface share the batched kernels; the others step alone
 bool batchable(const sm_mesh_desc& d) {
-  return d.precision == SM_FP32 && d.physics == SM_EULER && d.geom == SM_GEOM_PLANE;
+  return d.precision == SM_FP32 && d.physics == SM_EULER && d.geom == SM_GEOM_PLANE && d.volume == SM_VOLUME_WEAK;
 }
 
 }  // namespace

@@ -26,7 +26,8 @@ class SmMeshDesc(C.Structure):
                 ("y1", C.c_double), ("z0", C.c_double), ("z1", C.c_double), ("gamma", C.c_double),
                 ("riemann", C.c_int), ("precision", C.c_int), ("interface_conforming", C.c_int),
                 ("flow", C.c_int), ("fpar", C.c_double * 16), ("modes", C.c_double * 160),
-                ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double)]
+                ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double),
+                ("volume", C.c_int)]
 
 
 class SmMotion(C.Structure):
@@ -147,6 +148,7 @@ def mesh_desc(p: synth.Problem) -> SmMeshDesc:
     for k, m in enumerate(p.modes_array().ravel()):
         d.modes[k] = m
     d.physics, d.mu, d.Pr, d.Rgas = int(p.physics), float(p.mu), float(p.Pr), float(p.Rgas)
+    d.volume = int(getattr(p, "volume", 0))
     return d
 
 
