@@ -20,11 +20,11 @@
 //
 // One thread per volume node loads its state and stores the halved primitives
 // (rho, v1, v2, v3, p, H) / 2 in shared memory, so that a mean is one addition; the face
-// fluxes are computed as in the weak-form kernel.  After a barrier one thread per
-// contraction line (direction, line) holds the line's primitives in registers, evaluates
-// the NP (NP - 1) / 2 pair fluxes once and accumulates both ends; after a second barrier
-// every node sums its three directions with the metric terms and applies the surface
-// integral and the RK update.
+// fluxes are computed as in the weak-form kernel.  After a barrier two threads per
+// contraction line (direction, line), one per group of conserved variables, hold the
+// line's primitives in registers, evaluate the NP (NP - 1) / 2 pair fluxes once and
+// accumulate both ends; after a second barrier every node sums its three directions with
+// the metric terms and applies the surface integral and the RK update.
 #pragma once
 
 #include "sm_element.cuh"
@@ -33,8 +33,14 @@ template <int N> struct SplitCfg {
   using C = ElemCfg<N>;
   static constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
   static constexpr int LINES = EPB * 3 * NP2;
-  // FP32 launch bound: resident CTAs per SM asked of the register allocator
-  static constexpr int MINB = N <= 2 ? 2 : (N == 7 ? 1 : (N == 6 ? 2 : 3));
+  // FP32 launch bound: resident CTAs per SM asked of the register allocator (N = 5: 56
+  // registers, 5 CTAs of 216 threads; measured 4 % (Roe/HH) to 8 % (Rusanov) faster than 72
+  // registers and 4 CTAs)
+#ifdef SM_SPLIT_MINB_OVERRIDE
+  static constexpr int MINB = SM_SPLIT_MINB_OVERRIDE;
+#else
+  static constexpr int MINB = N <= 2 ? 2 : (N == 7 ? 1 : (N == 6 ? 2 : (N == 5 ? 5 : 3)));
+#endif
   template <typename T> static constexpr size_t smem_bytes() {
     return sizeof(T) * (size_t)(EPB * 6 * NN + EPB * 15 * NN + EPB * 30 * NP2);
   }
@@ -55,71 +61,96 @@ template <typename T> __device__ __forceinline__ T dsplit_c(int n, int idx);
 template <> __device__ __forceinline__ float dsplit_c<float>(int n, int idx) { return c_dsplit_f[n - 1][idx]; }
 template <> __device__ __forceinline__ double dsplit_c<double>(int n, int idx) { return c_dsplit_d[n - 1][idx]; }
 
-// The two-point volume integral of every contraction line of the CTA's elements.
+// One half of the two-point volume integral of a contraction line: ROLE 0 the mass, normal
+// and first tangential momentum components, ROLE 1 the second tangential momentum and the
+// energy.  Each half evaluates the parts of the pair fluxes it needs, so a line's two halves
+// run on two threads with about half the registers of one thread doing the whole line.
 //   sQ [EPB][6][NN]: halved primitives (rho, v1, v2, v3, p, H) / 2 in node order;
 //   sV [EPB][3][5][NN]: per direction d, sum_l Ds_al F#(U_a, U_l) (physical momentum order,
 //   without the metric factor |Ja^d|).
-// Lines of direction d: xi^1 (i) lines are contiguous, xi^2 (j) lines have stride NP and
-// xi^3 (k) lines stride NP^2.  Velocity slots are read in the order (normal, tangential,
-// tangential) of the direction's physical axis, so one code path serves all directions.
+// Line (l2, d, q): xi^1 (i) lines are contiguous, xi^2 (j) lines have stride NP and xi^3 (k)
+// lines stride NP^2.  Velocity slots are read in the order (normal, tangential, tangential)
+// of the direction's physical axis, so one code path serves all directions.
+template <int N, typename T, int ROLE>
+__device__ __forceinline__ void split_line_half(const MeshDev& m, const T* sQ, T* sV, const long long e0,
+                                                const int w) {
+  constexpr int NP = N + 1, NP2 = NP * NP, NN = NP2 * NP;
+  constexpr int NV = ROLE == 0 ? 3 : 2;
+  const int l2 = w / (3 * NP2);
+  const int r = w - l2 * 3 * NP2;
+  const int d = r / NP2, q = r - d * NP2;
+  if (e0 + l2 >= m.E) return;
+  const int blk = e0 + l2 >= m.Es;
+  const int base = d == 0 ? NP * q : (d == 1 ? (q % NP) + NP2 * (q / NP) : q);
+  const int stride = d == 0 ? 1 : (d == 1 ? NP : NP2);
+  const int ax = d == 0 ? 1 : (d == 1 ? 2 : 0);      // physical axis of xi^{d+1}
+  const int sn = 1 + ax, st1 = 1 + (ax + 1) % 3, st2 = 1 + (ax + 2) % 3;
+  // grid velocity along the axis: the moving block translates along y = xi^1
+  const T vg = (d == 0 && blk) ? Prec<T>::c(m)[MC_VG] : T(0);
+  const T* Q = sQ + l2 * 6 * NN + base;
+  // ROLE 0 reads (rho, v_n, p, v_t1); ROLE 1 reads (rho, v_n, p, v_t2, H)
+  T rh[NP], un[NP], pp[NP], xa[NP], xb[NP];
+  const int sa = ROLE == 0 ? st1 : st2;
+#pragma unroll
+  for (int l = 0; l < NP; ++l) {
+    rh[l] = Q[l * stride];
+    un[l] = Q[sn * NN + l * stride];
+    pp[l] = Q[4 * NN + l * stride];
+    xa[l] = Q[sa * NN + l * stride];
+    if (ROLE == 1) xb[l] = Q[5 * NN + l * stride];
+  }
+  T acc[NP][NV];
+#pragma unroll
+  for (int a = 0; a < NP; ++a)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[a][v] = T(0);
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int l = a + 1; l < NP; ++l) {
+      const T nm = un[a] + un[l], pm = pp[a] + pp[l];
+      const T fr = (rh[a] + rh[l]) * (nm - vg);
+      T f[NV];
+      if (ROLE == 0) {
+        f[0] = fr;
+        f[1] = fr * nm + pm;
+        f[2] = fr * (xa[a] + xa[l]);
+      } else {
+        f[0] = fr * (xa[a] + xa[l]);
+        f[1] = fr * (xb[a] + xb[l]) + pm * vg;
+      }
+      const T dal = dsplit_c<T>(N, a * SM_MAXNP + l), dla = dsplit_c<T>(N, l * SM_MAXNP + a);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        acc[a][v] += dal * f[v];
+        acc[l][v] += dla * f[v];
+      }
+    }
+  }
+  T* V = sV + (l2 * 3 + d) * 5 * NN + base;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    if (ROLE == 0) {
+      V[a * stride] = acc[a][0];
+      V[sn * NN + a * stride] = acc[a][1];
+      V[st1 * NN + a * stride] = acc[a][2];
+    } else {
+      V[st2 * NN + a * stride] = acc[a][0];
+      V[4 * NN + a * stride] = acc[a][1];
+    }
+  }
+}
+
+// The two-point volume integral of every contraction line of the CTA's elements: work items
+// 0 .. LINES-1 are the first halves of the lines, LINES .. 2 LINES-1 the second halves (the
+// two roles meet in at most one warp).
 template <int N, typename T>
 __device__ __forceinline__ void split_volume_lines(const MeshDev& m, const T* sQ, T* sV, const long long e0,
                                                    const int tid) {
   using C = SplitCfg<N>;
-  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN;
-  const T* c = Prec<T>::c(m);
-  for (int w = tid; w < C::LINES; w += C::THREADS) {
-    const int l2 = w / (3 * NP2);
-    const int r = w - l2 * 3 * NP2;
-    const int d = r / NP2, q = r - d * NP2;
-    if (e0 + l2 >= m.E) continue;
-    const int blk = e0 + l2 >= m.Es;
-    const int base = d == 0 ? NP * q : (d == 1 ? (q % NP) + NP2 * (q / NP) : q);
-    const int stride = d == 0 ? 1 : (d == 1 ? NP : NP2);
-    const int ax = d == 0 ? 1 : (d == 1 ? 2 : 0);      // physical axis of xi^{d+1}
-    const int sn = 1 + ax, st1 = 1 + (ax + 1) % 3, st2 = 1 + (ax + 2) % 3;
-    // grid velocity along the axis: the moving block translates along y = xi^1
-    const T vg = (d == 0 && blk) ? c[MC_VG] : T(0);
-    const T* Q = sQ + l2 * 6 * NN + base;
-    T rh[NP], un[NP], ut1[NP], ut2[NP], pp[NP], hh[NP];
-#pragma unroll
-    for (int l = 0; l < NP; ++l) {
-      rh[l] = Q[l * stride];
-      un[l] = Q[sn * NN + l * stride];
-      ut1[l] = Q[st1 * NN + l * stride];
-      ut2[l] = Q[st2 * NN + l * stride];
-      pp[l] = Q[4 * NN + l * stride];
-      hh[l] = Q[5 * NN + l * stride];
-    }
-    T acc[NP][5];
-#pragma unroll
-    for (int a = 0; a < NP; ++a)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) acc[a][v] = T(0);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-#pragma unroll
-      for (int l = a + 1; l < NP; ++l) {
-        const T rm = rh[a] + rh[l], nm = un[a] + un[l], pm = pp[a] + pp[l];
-        const T fr = rm * (nm - vg);
-        const T f1 = fr * nm + pm;
-        const T f2 = fr * (ut1[a] + ut1[l]);
-        const T f3 = fr * (ut2[a] + ut2[l]);
-        const T f4 = fr * (hh[a] + hh[l]) + pm * vg;
-        const T dal = dsplit_c<T>(N, a * SM_MAXNP + l), dla = dsplit_c<T>(N, l * SM_MAXNP + a);
-        acc[a][0] += dal * fr; acc[a][1] += dal * f1; acc[a][2] += dal * f2; acc[a][3] += dal * f3; acc[a][4] += dal * f4;
-        acc[l][0] += dla * fr; acc[l][1] += dla * f1; acc[l][2] += dla * f2; acc[l][3] += dla * f3; acc[l][4] += dla * f4;
-      }
-    }
-    T* V = sV + (l2 * 3 + d) * 5 * NN + base;
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      V[a * stride] = acc[a][0];
-      V[sn * NN + a * stride] = acc[a][1];
-      V[st1 * NN + a * stride] = acc[a][2];
-      V[st2 * NN + a * stride] = acc[a][3];
-      V[4 * NN + a * stride] = acc[a][4];
-    }
+  for (int w = tid; w < 2 * C::LINES; w += C::THREADS) {
+    if (w < C::LINES) split_line_half<N, T, 0>(m, sQ, sV, e0, w);
+    else split_line_half<N, T, 1>(m, sQ, sV, e0, w - C::LINES);
   }
 }
 
