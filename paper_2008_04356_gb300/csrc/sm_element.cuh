@@ -151,6 +151,26 @@ __device__ __forceinline__ void contract_lines_inplace(T* sF, int tid) {
   }
 }
 
+// Exterior state of a weak Dirichlet face (x = x0 or x = x2) at face node vn of element e2:
+// the boundary flow at the node's position at the stage time (the moving block shifted by
+// the displacement).  pos_ix / pos_f: the element's x index and iz * ny + iy.
+template <int N, typename T>
+__device__ __forceinline__ void dirichlet_exterior(const MeshDev& m, const StageParams* __restrict__ sp,
+                                                   const int blk2, const int pos_ix, const int pos_f, const int vn,
+                                                   T (&uout)[5]) {
+  constexpr int NP = N + 1, NP2 = NP * NP;
+  const T* c = Prec<T>::c(m);
+  const int iy = pos_f % m.ny, iz = pos_f / m.ny;
+  const T* xi = Prec<T>::x(m.basis);
+  const int i = vn % NP, j = (vn / NP) % NP, k = vn / NP2;
+  const T hx = c[MC_H + blk2];
+  T X[3];
+  X[0] = c[MC_X + blk2] + (T)pos_ix * hx + (xi[k] + T(1)) * T(0.5) * hx;
+  X[1] = c[MC_X + 2] + (T)iy * c[MC_H + 2] + (xi[i] + T(1)) * T(0.5) * c[MC_H + 2] + (blk2 ? (T)sp->delta : T(0));
+  X[2] = c[MC_X + 3] + (T)iz * c[MC_H + 3] + (xi[j] + T(1)) * T(0.5) * c[MC_H + 3];
+  boundary_state<T>(m, X, (T)sp->t, uout);
+}
+
 // Face fluxes of the CTA's EPB elements (elements e0 ..), one work item per (element, face,
 // face node), into sS[EPB][6][5][NP^2] as outward fluxes times the surface element: conforming
 // and weak Dirichlet faces by the Riemann solver in canonical orientation (left = minus-side
@@ -209,15 +229,7 @@ __device__ __forceinline__ void element_face_fluxes(const MeshDev& m, const Stag
       } else {
         // weak Dirichlet face (x = x0 or x = x2): node position at the stage time
         if (tp) { pos_ix = tp[6] >> 1; pos_f = tp[7]; }
-        const int iy = pos_f % m.ny, iz = pos_f / m.ny;
-        const T* xi = Prec<T>::x(m.basis);
-        const int i = vn % NP, j = (vn / NP) % NP, k = vn / NP2;
-        const T hx = c[MC_H + blk2];
-        T X[3];
-        X[0] = c[MC_X + blk2] + (T)pos_ix * hx + (xi[k] + T(1)) * T(0.5) * hx;
-        X[1] = c[MC_X + 2] + (T)iy * c[MC_H + 2] + (xi[i] + T(1)) * T(0.5) * c[MC_H + 2] + (blk2 ? (T)sp->delta : T(0));
-        X[2] = c[MC_X + 3] + (T)iz * c[MC_H + 3] + (xi[j] + T(1)) * T(0.5) * c[MC_H + 3];
-        boundary_state<T>(m, X, (T)sp->t, uout);
+        dirichlet_exterior<N, T>(m, sp, blk2, pos_ix, pos_f, vn, uout);
       }
       // canonical orientation: left = minus-side element, normal +axis
       const int ax = d == 0 ? 1 : (d == 1 ? 2 : 0);
@@ -304,9 +316,18 @@ __device__ __forceinline__ void element_surface_update(const MeshDev& m, const T
     // the interface node layers of the updated state, for the next stage's interface kernel
     const int blk = e >= m.Es;
     if (Ts && k == (blk ? 0 : N)) {
-      const ElemPos p = decode_elem(m, e);
-      if (p.ix == (blk ? 0 : m.nxs - 1)) {
-        T* dst = (blk ? Tm : Ts) + ((long long)p.iz * m.ny + p.iy) * 5 * NP2 + i + NP * j;
+      int ix, f;
+      if (m.topo) {
+        const int* tp = reinterpret_cast<const int*>(m.topo) + 8 * e;
+        ix = tp[6] >> 1;
+        f = tp[7];
+      } else {
+        const ElemPos p = decode_elem(m, e);
+        ix = p.ix;
+        f = p.iz * m.ny + p.iy;
+      }
+      if (ix == (blk ? 0 : m.nxs - 1)) {
+        T* dst = (blk ? Tm : Ts) + (long long)f * 5 * NP2 + i + NP * j;
 #pragma unroll
         for (int v = 0; v < 5; ++v) dst[v * NP2] = un[v];
       }
@@ -334,7 +355,8 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
   using C = ElemCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // contravariant fluxes F~1, F~2, F~3, each in node order [v][k][j][i]
+  // physical fluxes along the axes of xi^1, xi^2, xi^3 (the contravariant fluxes without
+  // their constant metric factors), each in node order [v][k][j][i]
   T* sF = reinterpret_cast<T*>(smem_raw);        // [EPB][3][5][NN]
   T* sS = sF + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
 
@@ -358,7 +380,6 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
     const Prim<T> q = primitives(u, gamma);
     T f[5];
     T* Fe = sF + le * 15 * NN;
-    const T a0 = c[MC_METRIC + 3 * blk], a1 = c[MC_METRIC + 3 * blk + 1], a2 = c[MC_METRIC + 3 * blk + 2];
     T gn[PHYS ? 15 : 1], fv[5];
     if (PHYS) {
 #pragma unroll
@@ -371,7 +392,7 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
       for (int v = 0; v < 5; ++v) f[v] -= fv[v];
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[v * NN + nd] = a0 * f[v];
+    for (int v = 0; v < 5; ++v) Fe[v * NN + nd] = f[v];
     axis_flux<T, 2>(u, q, T(0), f);                             // xi^2 -> z
     if (PHYS) {
       viscous_flux_axis(u, gn, 2, c, fv);
@@ -379,7 +400,7 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
       for (int v = 0; v < 5; ++v) f[v] -= fv[v];
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN + nd] = a1 * f[v];
+    for (int v = 0; v < 5; ++v) Fe[(5 + v) * NN + nd] = f[v];
     axis_flux<T, 0>(u, q, T(0), f);                             // xi^3 -> x
     if (PHYS) {
       viscous_flux_axis(u, gn, 0, c, fv);
@@ -387,7 +408,7 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
       for (int v = 0; v < 5; ++v) f[v] -= fv[v];
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN + nd] = a2 * f[v];
+    for (int v = 0; v < 5; ++v) Fe[(10 + v) * NN + nd] = f[v];
   }
 
   element_face_fluxes<N, T, RIEM, PHYS>(m, sp, U, Fs, Fm, Gr, e0, sS, tid);
@@ -399,9 +420,12 @@ __device__ __forceinline__ void element_block(const MeshDev& m, const StageParam
   __syncthreads();
   if (!active) return;
   {
+    // the metric terms |Ja^d| (constant per block) scale the contracted fluxes
+    const int blk = e >= m.Es;
+    const T a0 = c[MC_METRIC + 3 * blk], a1 = c[MC_METRIC + 3 * blk + 1], a2 = c[MC_METRIC + 3 * blk + 2];
     const T* Fe = sF + le * 15 * NN + nd;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = Fe[v * NN] + Fe[(5 + v) * NN] + Fe[(10 + v) * NN];
+    for (int v = 0; v < 5; ++v) acc[v] = a0 * Fe[v * NN] + a1 * Fe[(5 + v) * NN] + a2 * Fe[(10 + v) * NN];
   }
   element_surface_update<N, T, MODE>(m, sS + le * 30 * NP2, acc, nd, e, base, u, g, out, G, rkA, rkB, dt, Ts, Tm);
 }
