@@ -677,12 +677,15 @@ void interface_config(const Oracle& o, double t, Interface& I) {
 
 int wrap(long long i, int n) { long long r = i % n; if (r < 0) r += n; return (int)r; }
 
-/* Face trace on the interface: static face (i, iperp) is the xi^3 = +1 face of static
- * element (nx-1, i, iperp); moving face (i~, iperp) is the xi^3 = -1 face of moving
- * element (0, i~, iperp).  tr[(v*np + q)*np + p], p along xi^1 (sliding), q along xi^2. */
-void interface_trace(const Oracle& o, const double* U, int blk, int ipar, int iperp, double* tr) {
-  int ix = blk == 0 ? o.p.nel_s[0] - 1 : 0;
-  int side = blk == 0 ? 1 : 0;
+/* Face trace on interface ifc.  Interface 0 (x = x1): static face (i, iperp) is the
+ * xi^3 = +1 face of static element (nx-1, i, iperp), moving face (i~, iperp) the xi^3 = -1
+ * face of moving element (0, i~, iperp).  Interface 1 (x = x0 = x2, periodic x): static face
+ * the xi^3 = -1 face of static element (0, i, iperp), moving face the xi^3 = +1 face of
+ * moving element (nx-1, i~, iperp).  tr[(v*np + q)*np + p], p along xi^1 (sliding), q along
+ * xi^2. */
+void interface_trace(const Oracle& o, const double* U, int blk, int ipar, int iperp, double* tr, int ifc = 0) {
+  int ix = ifc == 0 ? (blk == 0 ? o.p.nel_s[0] - 1 : 0) : (blk == 0 ? 0 : o.p.nel_m[0] - 1);
+  int side = (blk == 0) == (ifc == 0) ? 1 : 0;
   long long e = elem_index(o, blk, ix, ipar, iperp);
   for (int v = 0; v < 5; ++v)
     for (int q = 0; q < o.np; ++q)
@@ -721,20 +724,22 @@ void project_to_mortar(const Oracle& o, const double* P, const double* tr, doubl
       }
 }
 
-/* Steps 2-4 for one mortar (ipar, iperp, isub) (mortar index triple of Sec. 4.3):
- * primary (static) and replica (moving) states on the mortar, then the Riemann flux with
- * the static face's outward normal (+x), scaled by the static face's surface element. */
+/* Steps 2-4 for one mortar (ipar, iperp, isub) of interface ifc (mortar index of Sec. 4.3,
+ * with the interface as the outermost key): primary (static) and replica (moving) states on
+ * the mortar, then the Riemann flux along the static face's outward normal (+x on interface
+ * 0, -x on interface 1), scaled by the static face's surface element.  Both interfaces see
+ * the same displacement, hence the same partners (Eq. indices) and operators. */
 void mortar_flux(const Oracle& o, const Interface& I, const double* U, const double* grad, int ipar, int iperp,
-                 int isub, double* Fm) {
+                 int isub, double* Fm, int ifc = 0) {
   int nq = o.np * o.np;
   std::vector<double> tr(15 * nq), QL(5 * nq), QR(5 * nq), GL(15 * nq), GR(15 * nq);
   const double* Ps = isub == 0 ? I.Ps_lo.data() : I.Ps_hi.data();
   /* the static lower mortar is the upper part of the moving face, and vice versa */
   const double* Pm = isub == 0 ? I.Pm_hi.data() : I.Pm_lo.data();
   int it = wrap((long long)ipar - I.n + isub - 1, o.ny);          /* Eq. indices */
-  interface_trace(o, U, 0, ipar, iperp, tr.data());
+  interface_trace(o, U, 0, ipar, iperp, tr.data(), ifc);
   project_to_mortar(o, Ps, tr.data(), QL.data());
-  interface_trace(o, U, 1, it, iperp, tr.data());
+  interface_trace(o, U, 1, it, iperp, tr.data(), ifc);
   project_to_mortar(o, Pm, tr.data(), QR.data());
   if (grad) {   /* gradients projected onto the mortars like the solution (Sec. 3.2) */
     interface_grad_trace(o, grad, 0, ipar, iperp, tr.data());
@@ -747,7 +752,13 @@ void mortar_flux(const Oracle& o, const Interface& I, const double* U, const dou
     for (int j = 0; j < o.np; ++j) {
       double ul[5], ur[5], f[5];
       for (int v = 0; v < 5; ++v) { ul[v] = QL[(v * o.np + q) * o.np + j]; ur[v] = QR[(v * o.np + q) * o.np + j]; }
-      orc_riemann(o.p.riemann, ul, ur, n, 0.0, o.p.gamma, f);
+      if (ifc == 0) orc_riemann(o.p.riemann, ul, ur, n, 0.0, o.p.gamma, f);
+      else {
+        /* x = x0 = x2: the moving state is on the minus side; the flux in canonical
+         * orientation (minus side left, normal +x), negated for the static outward normal */
+        orc_riemann(o.p.riemann, ur, ul, n, 0.0, o.p.gamma, f);
+        for (int v = 0; v < 5; ++v) f[v] = -f[v];
+      }
       if (grad) {   /* BR1: mean of both sides' viscous fluxes */
         double gl[15], gr[15], fl[5], fr[5];
         for (int k = 0; k < 15; ++k) { gl[k] = GL[(k * o.np + q) * o.np + j]; gr[k] = GR[(k * o.np + q) * o.np + j]; }
@@ -794,25 +805,25 @@ void project_to_face(const Oracle& o, const double* B_lo, const double* F_lo, co
       }
 }
 
-/* Outward flux (times surface element) on static face (ipar, iperp). */
+/* Outward flux (times surface element) on static face (ipar, iperp) of interface ifc. */
 void static_face_flux(const Oracle& o, const Interface& I, const double* U, const double* grad, int ipar, int iperp,
-                      double* F) {
+                      double* F, int ifc = 0) {
   int nq = o.np * o.np;
   std::vector<double> F0(5 * nq), F1(5 * nq);
-  mortar_flux(o, I, U, grad, ipar, iperp, 0, F0.data());
-  mortar_flux(o, I, U, grad, ipar, iperp, 1, F1.data());
+  mortar_flux(o, I, U, grad, ipar, iperp, 0, F0.data(), ifc);
+  mortar_flux(o, I, U, grad, ipar, iperp, 1, F1.data(), ifc);
   project_to_face(o, I.Bs_lo.data(), F0.data(), I.Bs_hi.data(), F1.data(), 1.0, F);
 }
 
-/* Outward flux on moving face (it, iperp): its lower part (xi~ <= sigma~) is mortar
- * (it + n, 1), its upper part mortar (it + n + 1, 0); the moving side's outward normal
- * is -x, hence the sign. */
+/* Outward flux on moving face (it, iperp) of interface ifc: its lower part (xi~ <= sigma~)
+ * is mortar (it + n, 1), its upper part mortar (it + n + 1, 0); the moving side's outward
+ * normal is opposite to the static side's, hence the sign. */
 void moving_face_flux(const Oracle& o, const Interface& I, const double* U, const double* grad, int it, int iperp,
-                      double* F) {
+                      double* F, int ifc = 0) {
   int nq = o.np * o.np;
   std::vector<double> Flo(5 * nq), Fhi(5 * nq);
-  mortar_flux(o, I, U, grad, wrap((long long)it + I.n, o.ny), iperp, 1, Flo.data());
-  mortar_flux(o, I, U, grad, wrap((long long)it + I.n + 1, o.ny), iperp, 0, Fhi.data());
+  mortar_flux(o, I, U, grad, wrap((long long)it + I.n, o.ny), iperp, 1, Flo.data(), ifc);
+  mortar_flux(o, I, U, grad, wrap((long long)it + I.n + 1, o.ny), iperp, 0, Fhi.data(), ifc);
   project_to_face(o, I.Bm_lo.data(), Flo.data(), I.Bm_hi.data(), Fhi.data(), -1.0, F);
 }
 
@@ -833,25 +844,35 @@ void face_flux_out(const Oracle& o, const Interface* I, const double* U, const d
   unit_normal(d, n);
   /* classify the neighbour */
   long long nb = -1; int nb_blk = id.blk; int kind = 0;  /* 0 conforming, 1 boundary, 2 interface */
+  int ifc = 0;                                           /* interface 0 (x = x1) or 1 (x = x0 = x2) */
   if (d == 0) nb = elem_index(o, id.blk, id.ix, wrap(id.iy + (side ? 1 : -1), o.ny), id.iz);
   else if (d == 1) nb = elem_index(o, id.blk, id.ix, id.iy, wrap(id.iz + (side ? 1 : -1), o.nz));
   else {
     int jx = id.ix + (side ? 1 : -1);
+    bool outer = (id.blk == 0 && side == 0) || (id.blk == 1 && side == 1);
     if (jx >= 0 && jx < nx) nb = elem_index(o, id.blk, jx, id.iy, id.iz);
-    else if ((id.blk == 0 && side == 0) || (id.blk == 1 && side == 1)) kind = 1;
+    else if (outer && !o.p.periodic_x) kind = 1;
     else if (o.p.interface_conforming) {
+      /* the other block's element across the interface: across x = x1 the static
+       * element nx-1 meets moving element 0; across x = x0 = x2 static element 0 meets
+       * moving element nx-1 */
       nb_blk = 1 - id.blk;
-      nb = elem_index(o, nb_blk, nb_blk == 0 ? o.p.nel_s[0] - 1 : 0, id.iy, id.iz);
-    } else kind = 2;
+      int nb_ix = nb_blk == 0 ? (outer ? 0 : o.p.nel_s[0] - 1) : (outer ? o.p.nel_m[0] - 1 : 0);
+      nb = elem_index(o, nb_blk, nb_ix, id.iy, id.iz);
+    } else {
+      kind = 2;
+      ifc = outer ? 1 : 0;
+    }
   }
   if (kind == 2) {
     const std::vector<double>* src = id.blk == 0 ? Fsl_static : Fsl_moving;
     if (src) {
-      const double* F = src->data() + ((long long)id.iz * o.ny + id.iy) * 5 * nq;
+      long long nf = (long long)o.ny * o.nz;
+      const double* F = src->data() + ((long long)ifc * nf + (long long)id.iz * o.ny + id.iy) * 5 * nq;
       for (int v = 0; v < 5; ++v)
         for (int ab = 0; ab < nq; ++ab) Fout[v * nq + ab] = F[v * nq + ab];
-    } else if (id.blk == 0) static_face_flux(o, *I, U, grad, id.iy, id.iz, Fout);
-    else moving_face_flux(o, *I, U, grad, id.iy, id.iz, Fout);
+    } else if (id.blk == 0) static_face_flux(o, *I, U, grad, id.iy, id.iz, Fout, ifc);
+    else moving_face_flux(o, *I, U, grad, id.iy, id.iz, Fout, ifc);
     return;
   }
   for (int b = 0; b < np; ++b)
@@ -999,24 +1020,29 @@ void all_interface_fluxes(const Oracle& o, const Interface& I, const double* U, 
                           std::vector<double>& Fs, std::vector<double>& Fm) {
   int nq = o.np * o.np;
   long long nf = (long long)o.ny * o.nz;
-  std::vector<double> Fsm(nf * 2 * 5 * nq);
+  int nifc = o.p.periodic_x ? 2 : 1;           /* interface 0 first, then interface 1 */
+  std::vector<double> Fsm(nifc * nf * 2 * 5 * nq);
   #pragma omp parallel for schedule(dynamic)
-  for (long long f = 0; f < nf; ++f) {
+  for (long long g = 0; g < nifc * nf; ++g) {
+    int ifc = (int)(g / nf);
+    long long f = g - ifc * nf;
     int ipar = (int)(f % o.ny), iperp = (int)(f / o.ny);
     for (int isub = 0; isub < 2; ++isub)
-      mortar_flux(o, I, U, grad, ipar, iperp, isub, Fsm.data() + (f * 2 + isub) * 5 * nq);
+      mortar_flux(o, I, U, grad, ipar, iperp, isub, Fsm.data() + (g * 2 + isub) * 5 * nq, ifc);
   }
-  Fs.assign(nf * 5 * nq, 0.0);
-  Fm.assign(nf * 5 * nq, 0.0);
+  Fs.assign(nifc * nf * 5 * nq, 0.0);
+  Fm.assign(nifc * nf * 5 * nq, 0.0);
   #pragma omp parallel for schedule(dynamic)
-  for (long long f = 0; f < nf; ++f) {
+  for (long long g = 0; g < nifc * nf; ++g) {
+    int ifc = (int)(g / nf);
+    long long f = g - ifc * nf;
     int ipar = (int)(f % o.ny), iperp = (int)(f / o.ny);
-    long long row = (long long)iperp * o.ny;
-    project_to_face(o, I.Bs_lo.data(), Fsm.data() + (f * 2 + 0) * 5 * nq, I.Bs_hi.data(),
-                    Fsm.data() + (f * 2 + 1) * 5 * nq, 1.0, Fs.data() + f * 5 * nq);
+    long long row = ifc * nf + (long long)iperp * o.ny;
+    project_to_face(o, I.Bs_lo.data(), Fsm.data() + (g * 2 + 0) * 5 * nq, I.Bs_hi.data(),
+                    Fsm.data() + (g * 2 + 1) * 5 * nq, 1.0, Fs.data() + g * 5 * nq);
     long long flo = row + wrap((long long)ipar + I.n, o.ny), fhi = row + wrap((long long)ipar + I.n + 1, o.ny);
     project_to_face(o, I.Bm_lo.data(), Fsm.data() + (flo * 2 + 1) * 5 * nq, I.Bm_hi.data(),
-                    Fsm.data() + (fhi * 2 + 0) * 5 * nq, -1.0, Fm.data() + f * 5 * nq);
+                    Fsm.data() + (fhi * 2 + 0) * 5 * nq, -1.0, Fm.data() + g * 5 * nq);
   }
 }
 
@@ -1128,10 +1154,11 @@ extern "C" {
 static bool curved(void* h) { return *(int*)h == 1; }
 
 void* orc_create(const orc_problem* p) {
-  if (p->geom != 0) return p->volume != 0 ? nullptr : orc_curved_create(p);
+  if (p->geom != 0) return (p->volume != 0 || p->periodic_x) ? nullptr : orc_curved_create(p);
   if (p->N < 1 || p->N > 15) return nullptr;
   if (p->nel_s[1] != p->nel_m[1] || p->nel_s[2] != p->nel_m[2]) return nullptr;
   if (p->volume < 0 || p->volume > 2 || (p->volume != 0 && p->physics != 0)) return nullptr;
+  if (p->periodic_x && p->physics != 0) return nullptr;
   Oracle* o = new Oracle();
   o->p = *p;
   o->N = p->N; o->np = p->N + 1; o->nn = o->np * o->np * o->np;
@@ -1263,6 +1290,7 @@ void orc_interface_fluxes(void* h, const double* U, double t, double* F_static, 
   if (o.ns) { grad.assign(o.E * 15 * o.nn, 0.0); compute_lifting(o, I, U, t, grad.data()); }
   std::vector<double> Fs, Fm;
   all_interface_fluxes(o, I, U, o.ns ? grad.data() : nullptr, Fs, Fm);
+  /* interface 0 (x = x1) first; with periodic x, interface 1 (x = x0 = x2) follows */
   std::memcpy(F_static, Fs.data(), sizeof(double) * Fs.size());
   std::memcpy(F_moving, Fm.data(), sizeof(double) * Fm.size());
 }

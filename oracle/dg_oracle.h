@@ -45,6 +45,9 @@ typedef struct {
                             Pirozzoli's two-point flux; 2 split form with the central
                             two-point flux (equal to the weak form by summation by parts).
                             The split forms take geom 0 and Euler physics. */
+  int periodic_x;        /* 1: x periodic with period x2 - x0, so that the moving block's face
+                            x = x2 meets the static block's face x = x0 in a second sliding
+                            interface (several interfaces, Sec. 4.3); geom 0, Euler physics */
 } orc_problem;
 
 /* geom 1, the cylindrical sliding interface of Sec. 3.3 (a rotor inside the circle):

@@ -30,7 +30,7 @@ class OrcProblem(C.Structure):
                 ("riemann", C.c_int), ("interface_conforming", C.c_int), ("flow", C.c_int),
                 ("fpar", C.c_double * 16), ("modes", C.c_double * 160),
                 ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double),
-                ("geom", C.c_int), ("volume", C.c_int)]
+                ("geom", C.c_int), ("volume", C.c_int), ("periodic_x", C.c_int)]
 
 
 _LIB = None
@@ -206,6 +206,7 @@ def to_orc_problem(p) -> OrcProblem:
     s.mu, s.Pr, s.Rgas = float(p.mu), float(p.Pr), float(p.Rgas)
     s.geom = int(getattr(p, "geom", 0))
     s.volume = int(getattr(p, "volume", 0))
+    s.periodic_x = int(getattr(p, "periodic_x", 0))
     return s
 
 
@@ -264,9 +265,13 @@ class Oracle:
         return Ut
 
     def interface_fluxes(self, U, t):
+        """Face fluxes of both sides, (nz, ny, 5, np, np) each; with periodic x the two
+        interfaces, (2, nz, ny, 5, np, np): x = x1 first, then x = x0 = x2."""
         U = np.ascontiguousarray(U, dtype=np.float64)
         p = self.problem
         shp = (p.nel_s[2], p.nel_s[1], 5, self.np_, self.np_)
+        if getattr(p, "periodic_x", 0):
+            shp = (2,) + shp
         Fs, Fm = np.zeros(shp), np.zeros(shp)
         lib().orc_interface_fluxes(self.h, _p(U), float(t), _p(Fs), _p(Fm))
         return Fs, Fm

@@ -58,6 +58,9 @@ class Problem:
     the rotor, inside), [y0, y1] the periodic angular sector, v the rotor's angular speed and
     delta0 its initial angle; walls r = x0, x2 are slip walls.  GEOM_PLANE_CURVILINEAR: the
     plane box through the curvilinear operator (general metrics).
+
+    periodic_x = 1 closes the box in x (period x2 - x0): the moving block's face x = x2 meets
+    the static block's face x = x0 in a second sliding interface (no Dirichlet faces).
     """
     N: int = 3
     nel_s: tuple = (4, 4, 2)
@@ -84,6 +87,7 @@ class Problem:
     Rgas: float = 1.0
     geom: int = GEOM_PLANE
     volume: int = VOLUME_WEAK
+    periodic_x: int = 0          # 1: x periodic, a second sliding interface at x0 = x2
 
     @property
     def np_(self) -> int:
