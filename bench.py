@@ -53,6 +53,8 @@ def parse():
                     help="volume integral of the interface-heavy headline: weak form, or the split form")
     ap.add_argument("--riemann", choices=["rusanov", "roe"], default=None,
                     help="Riemann solver of the headline (default: Rusanov for the weak form, Roe/HH for the split form)")
+    ap.add_argument("--two-steps", type=int, default=20,
+                    help="timed steps of the two-interface solve (the workload closed in x) beside the headline; 0: skip")
     ap.add_argument("--split-steps", type=int, default=20,
                     help="timed steps of the split-form (Pirozzoli, Roe/HH) solve beside the weak-form headline; 0: skip")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32", help="cylinder workload state precision")
@@ -544,6 +546,37 @@ def main():
         ss.close()
         del ss
 
+    # two sliding interfaces: the same workload closed in x (periodic x), so the moving block's
+    # face x2 meets the static face x0 as well: 2 x 65,536 interface face pairs per stage
+    two = None
+    if args.volume == "weak" and args.two_steps > 0:
+        pp = synth.config_interface_heavy(seed=1 + rank, precision=synth.FP32, nz=args.nz)
+        pp.periodic_x = 1
+        s2 = slidemesh.Solver(pp)
+        s2.init_state()
+        s2.step(dt, 3)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        s2.step(dt, args.two_steps)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = max_over_ranks(h0.elapsed_time(h1))
+        tkms, tkcnt = s2.step_profiled(dt, max(2, args.profile_steps // 2))
+        if_ms = tkms[1] / tkcnt[1] / 2.0
+        two = {"value": rep.value(pp.ndof * 5 * args.two_steps, ms2 * 1e-3), "unit": UNIT,
+               "interface_face_updates_per_s": rep.value(2 * pp.n_faces * 5 * args.two_steps, ms2 * 1e-3),
+               "steps": args.two_steps, "ms_per_step": ms2 / args.two_steps,
+               "interfaces": "x = x1 and x = x0 = x2 (periodic x), 2 x %d face pairs" % pp.n_faces,
+               "kernels": {"stage_params": {"launches": tkcnt[0], "ms": tkms[0]},
+                           "sliding_interface": {"launches": 2 * tkcnt[1], "ms": tkms[1], "avg_ms": if_ms,
+                                                 "achieved_gbs": iface_bytes / (if_ms * 1e-3) / 1e9,
+                                                 "frac_hbm": iface_bytes / (if_ms * 1e-3) / 1e9 / hbm},
+                           "dg_element": {"launches": tkcnt[2], "ms": tkms[2], "avg_ms": tkms[2] / tkcnt[2]}},
+               "diag_finite": s2.diag()["status"] == 0}
+        s2.close()
+        del s2
+
     # end to end through the C-ABI with host buffers: state in (pinned), one step, state out
     Uh, _ = sol.get_state(out=torch.empty(sol.shape(), dtype=torch.float32, pin_memory=True))
     Uo = torch.empty_like(Uh).pin_memory()
@@ -599,6 +632,8 @@ def main():
     }
     if split is not None:
         line["split_form"] = split
+    if two is not None:
+        line["two_interfaces"] = two
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, p.volume, p.riemann)
     sol.close()

@@ -108,6 +108,12 @@ typedef struct {
   int physics;             /* SM_EULER | SM_NAVIER_STOKES (BR1 lifting, Sec. 3.1) */
   double mu, Pr, Rgas;     /* dynamic viscosity, Prandtl number, gas constant */
   int volume;              /* SM_VOLUME_WEAK | SM_VOLUME_SPLIT */
+  int periodic_x;          /* 1: x periodic with period x2 - x0 (plane geometry, Euler): the
+                              moving block's face x = x2 meets the static block's face x = x0
+                              in a second sliding interface with the same displacement
+                              (several interfaces, Sec. 4.3); no Dirichlet faces remain.
+                              sm_interface and sm_diag's interface sums cover the interface
+                              x = x1 only.  Not for batches or sm_rhs_static. */
 } sm_mesh_desc;
 
 /* Motion of the moving block: displacement Delta(t) = delta0 + v t along +y (Sec. 4.3,

@@ -84,10 +84,12 @@ __global__ void finish_sum_kernel(const double* partial, int nblk, double* out5)
 
 // Interface traces of U: static face (iy, iz) is the xi^3 = +1 layer of static element
 // (nxs-1, iy, iz), moving face the xi^3 = -1 layer of moving element (0, iy, iz); output
-// [iz][iy][var][(N+1)^2] per side.
+// [iz][iy][var][(N+1)^2] per side.  ifc = 1, the second interface x = x0 = x2 of a periodic x
+// direction: the xi^3 = -1 layer of static element (0, iy, iz) and the xi^3 = +1 layer of
+// moving element (nxm-1, iy, iz), x-momentum negated (the mirrored problem).
 template <typename T>
 __global__ void gather_traces_kernel(const MeshDev m, int np, const T* __restrict__ U, T* __restrict__ Ts,
-                                     T* __restrict__ Tm) {
+                                     T* __restrict__ Tm, const int ifc) {
   const long long np2 = (long long)np * np, nn = np2 * np;
   const long long per_side = (long long)m.ny * m.nz * 5 * np2;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 2 * per_side;
@@ -98,19 +100,24 @@ __global__ void gather_traces_kernel(const MeshDev m, int np, const T* __restric
     const int r = (int)(w - f * 5 * np2);
     const int v = r / (int)np2, ab = r - v * (int)np2;
     const int iy = (int)(f % m.ny), iz = (int)(f / m.ny);
-    const long long e = encode_elem(m, side, side ? 0 : m.nxs - 1, iy, iz);
-    (side ? Tm : Ts)[w] = U[(e * 5 + v) * nn + (side ? 0 : np2 * (np - 1)) + ab];
+    const int ix = ifc == 0 ? (side ? 0 : m.nxs - 1) : (side ? m.nxm - 1 : 0);
+    const bool upper = (side == 0) == (ifc == 0);     // the element's xi^3 = +1 layer
+    const long long e = encode_elem(m, side, ix, iy, iz);
+    const T val = U[(e * 5 + v) * nn + (upper ? np2 * (np - 1) : 0) + ab];
+    (side ? Tm : Ts)[w] = (ifc == 1 && v == 1) ? -val : val;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_gather_traces(int N, int prec, const MeshDev& m, const void* U, void* Ts, void* Tm, cudaStream_t st) {
+cudaError_t launch_gather_traces(int N, int prec, const MeshDev& m, const void* U, void* Ts, void* Tm, cudaStream_t st,
+                                 int ifc) {
   const int np = N + 1;
   const long long total = 2LL * m.ny * m.nz * 5 * np * np;
   const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
-  if (prec == 0) gather_traces_kernel<double><<<grid, 256, 0, st>>>(m, np, (const double*)U, (double*)Ts, (double*)Tm);
-  else gather_traces_kernel<float><<<grid, 256, 0, st>>>(m, np, (const float*)U, (float*)Ts, (float*)Tm);
+  if (prec == 0)
+    gather_traces_kernel<double><<<grid, 256, 0, st>>>(m, np, (const double*)U, (double*)Ts, (double*)Tm, ifc);
+  else gather_traces_kernel<float><<<grid, 256, 0, st>>>(m, np, (const float*)U, (float*)Ts, (float*)Tm, ifc);
   return cudaGetLastError();
 }
 

@@ -98,7 +98,8 @@ struct MeshDev {
   float fparf[16];
   // Optional precomputed topology, two int4 per element: (nb0, nb1, nb2, nb3) and
   // (nb4, nb5, (ix << 1) | blk, iz * ny + iy), neighbour codes as in the element kernel
-  // (>= 0 element, -1 weak Dirichlet face, -2 sliding interface).  NULL: computed on the fly.
+  // (>= 0 element, -1 weak Dirichlet face, -2 sliding interface x = x1, -3 sliding
+  // interface x = x0 = x2).  NULL: computed on the fly.
   const int4* topo;
   // Curvilinear geometries: 0 plane interface (Cartesian kernels), 1 cylindrical interface
   // (rotor = block 0 inside, slip walls at the radial ends, periodic angular sector of
@@ -109,6 +110,17 @@ struct MeshDev {
   // J (slot 9), and the grid-velocity factors Ja^i . v^g / |v| of the moving block
   // (slots 10..12; the grid speed is MC_VG)
   const void* geo;
+  // Periodic x (plane geometry): the moving block's face x = x2 meets the static block's
+  // face x = x0 in a second sliding interface.  Its traces Ts2 / Tm2 and face fluxes Fs2 /
+  // Fm2 use the layout of the first interface's arrays and hold the x-mirrored problem
+  // (x-momentum negated), so that the first interface's kernel, whose static outward normal
+  // is +x, solves it unchanged; the element kernels mirror the fluxes back when they read
+  // them.  NULL pointers: one interface.
+  int periodic_x;
+  void* Ts2;
+  void* Tm2;
+  const void* Fs2;
+  const void* Fm2;
 };
 
 template <typename T> struct Prec;
@@ -178,7 +190,8 @@ __device__ __forceinline__ int face_vol_node(int d, int side, int a, int b) {
 }
 
 // Neighbour across face (d, side): kind 0 conforming (returns element), 1 weak Dirichlet
-// boundary (x = x0 of the static block, x = x2 of the moving block), 2 sliding interface.
+// boundary (x = x0 of the static block, x = x2 of the moving block), 2 sliding interface
+// x = x1, 3 the second sliding interface x = x0 = x2 (periodic x).
 __host__ __device__ __forceinline__ int face_neighbor(const MeshDev& m, const ElemPos& p, int d, int side, long long* nb) {
   if (d == 0) {
     int iy = p.iy + (side ? 1 : -1);
@@ -195,13 +208,16 @@ __host__ __device__ __forceinline__ int face_neighbor(const MeshDev& m, const El
   int nx = p.blk ? m.nxm : m.nxs;
   int jx = p.ix + (side ? 1 : -1);
   if (jx >= 0 && jx < nx) { *nb = encode_elem(m, p.blk, jx, p.iy, p.iz); return 0; }
-  if ((p.blk == 0 && side == 0) || (p.blk == 1 && side == 1)) return 1;
+  const bool outer = (p.blk == 0 && side == 0) || (p.blk == 1 && side == 1);
+  if (outer && !m.periodic_x) return 1;
   if (m.conforming) {
+    // across x = x1 static element nx-1 meets moving element 0; across x = x0 = x2 (periodic
+    // x) static element 0 meets moving element nx-1
     int ob = 1 - p.blk;
-    *nb = encode_elem(m, ob, ob == 0 ? m.nxs - 1 : 0, p.iy, p.iz);
+    *nb = encode_elem(m, ob, ob == 0 ? (outer ? 0 : m.nxs - 1) : (outer ? m.nxm - 1 : 0), p.iy, p.iz);
     return 0;
   }
-  return 2;
+  return outer ? 3 : 2;
 }
 
 // |Ja^d| (surface element of the xi^{d+1} faces) and the Jacobian of a Cartesian element.

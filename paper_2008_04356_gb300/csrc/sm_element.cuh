@@ -30,8 +30,8 @@ template <int N> struct ElemCfg {
 };
 
 // Neighbour codes of the per-CTA face table: >= 0 element index, -1 weak Dirichlet face,
-// -2 sliding interface face.
-enum { NB_BOUNDARY = -1, NB_INTERFACE = -2 };
+// -2 face of the sliding interface x = x1, -3 face of the sliding interface x = x0 = x2.
+enum { NB_BOUNDARY = -1, NB_INTERFACE = -2, NB_INTERFACE2 = -3 };
 
 // Contraction line of NP values starting at p (shared memory), read with vector loads when
 // the line length allows aligned pairs or quadruples.
@@ -207,7 +207,7 @@ __device__ __forceinline__ void element_face_fluxes(const MeshDev& m, const Stag
       const ElemPos p = decode_elem(m, e2);
       long long q = 0;
       const int kind = face_neighbor(m, p, d, side, &q);
-      nb = kind == 0 ? (int)q : (kind == 1 ? NB_BOUNDARY : NB_INTERFACE);
+      nb = kind == 0 ? (int)q : (kind == 1 ? NB_BOUNDARY : (kind == 2 ? NB_INTERFACE : NB_INTERFACE2));
       pos_ix = p.ix;
       pos_f = p.iz * m.ny + p.iy;
     }
@@ -217,6 +217,13 @@ __device__ __forceinline__ void element_face_fluxes(const MeshDev& m, const Stag
       const T* src = (blk2 ? Fm : Fs) + (long long)fi * 5 * NP2 + ab;
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fo[v] = src[v * NP2];
+    } else if (nb == NB_INTERFACE2) {
+      // second interface: fluxes of the x-mirrored problem, mirrored back
+      const int fi = tp ? tp[7] : pos_f;
+      const T* src = reinterpret_cast<const T*>(blk2 ? m.Fm2 : m.Fs2) + (long long)fi * 5 * NP2 + ab;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fo[v] = src[v * NP2];
+      Fo[1] = -Fo[1];
     } else {
       T uin[5], uout[5];
       const T* Ui = U + e2 * 5 * NN + vn;
@@ -330,6 +337,24 @@ __device__ __forceinline__ void element_surface_update(const MeshDev& m, const T
         T* dst = (blk ? Tm : Ts) + (long long)f * 5 * NP2 + i + NP * j;
 #pragma unroll
         for (int v = 0; v < 5; ++v) dst[v * NP2] = un[v];
+      }
+    }
+    // the second interface (periodic x): the opposite node layers, x-momentum mirrored
+    if (m.Ts2 && k == (blk ? N : 0)) {
+      int ix, f;
+      if (m.topo) {
+        const int* tp = reinterpret_cast<const int*>(m.topo) + 8 * e;
+        ix = tp[6] >> 1;
+        f = tp[7];
+      } else {
+        const ElemPos p = decode_elem(m, e);
+        ix = p.ix;
+        f = p.iz * m.ny + p.iy;
+      }
+      if (ix == (blk ? m.nxm - 1 : 0)) {
+        T* dst = reinterpret_cast<T*>(blk ? m.Tm2 : m.Ts2) + (long long)f * 5 * NP2 + i + NP * j;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dst[v * NP2] = v == 1 ? -un[v] : un[v];
       }
     }
   }

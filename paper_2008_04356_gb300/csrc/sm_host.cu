@@ -373,6 +373,10 @@ struct sm_solver {
   void* Lm = nullptr;           // ... moving side
   void* Ts = nullptr;           // interface traces of the current state (Euler, sliding interface)
   void* Tm = nullptr;
+  void* Ts2 = nullptr;          // periodic x: traces and face fluxes of the second interface
+  void* Tm2 = nullptr;          // (x-mirrored, see MeshDev)
+  void* Fs2 = nullptr;
+  void* Fm2 = nullptr;
   bool traces_ok = false;       // Ts / Tm hold the traces of U[cur]
   void* geo = nullptr;          // curvilinear geometry per node (MeshDev::geom != 0)
   int red_blocks = 0;
@@ -419,6 +423,16 @@ cudaError_t enqueue_flux_inputs(sm_solver* s, const void* dU, void* Fs, void* Fm
   if (sliding)
     e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st, from_traces ? s->Ts : nullptr,
                          from_traces ? s->Tm : nullptr);
+  if (e == cudaSuccess && sliding && s->m.Ts2) {
+    // the second interface (periodic x), solved as the x-mirrored first one from its traces
+    if (!from_traces) {
+      e = launch_gather_traces(s->N, s->prec, s->m, dU, s->m.Ts2, s->m.Tm2, st, 1);
+      s->traces_ok = false;           // Ts2 / Tm2 now hold the traces of dU
+      if (e != cudaSuccess) return e;
+    }
+    e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, const_cast<void*>(s->m.Fs2),
+                         const_cast<void*>(s->m.Fm2), st, s->m.Ts2, s->m.Tm2);
+  }
   return e;
 }
 
@@ -429,6 +443,7 @@ bool use_traces(const sm_solver* s) { return s->Ts != nullptr; }
 cudaError_t ensure_traces(sm_solver* s, cudaStream_t st) {
   if (!use_traces(s) || s->traces_ok) return cudaSuccess;
   cudaError_t e = launch_gather_traces(s->N, s->prec, s->m, s->U[s->cur], s->Ts, s->Tm, st);
+  if (e == cudaSuccess && s->m.Ts2) e = launch_gather_traces(s->N, s->prec, s->m, s->U[s->cur], s->m.Ts2, s->m.Tm2, st, 1);
   if (e == cudaSuccess) s->traces_ok = true;
   return e;
 }
@@ -506,7 +521,7 @@ void free_solver(sm_solver* s) {
   clear_graphs(s);
   if (s->cap) cudaStreamDestroy(s->cap);
   void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->t_d, s->red_d, s->topo_d,
-                  s->Gr, s->Ls, s->Lm, s->Ts, s->Tm, s->geo};
+                  s->Gr, s->Ls, s->Lm, s->Ts, s->Tm, s->Ts2, s->Tm2, s->Fs2, s->Fm2, s->geo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -540,6 +555,9 @@ int valid_desc(const sm_mesh_desc* d) {
   if (d->volume != SM_VOLUME_WEAK && d->volume != SM_VOLUME_SPLIT) return fail(SM_ERR_ARG, "unknown volume integral");
   if (d->volume == SM_VOLUME_SPLIT && (d->geom != SM_GEOM_PLANE || d->physics != SM_EULER))
     return fail(SM_ERR_UNSUPPORTED, "the split-form volume integral takes the plane interface and Euler physics");
+  if (d->periodic_x != 0 && d->periodic_x != 1) return fail(SM_ERR_ARG, "periodic_x must be 0 or 1");
+  if (d->periodic_x && (d->geom != SM_GEOM_PLANE || d->physics != SM_EULER))
+    return fail(SM_ERR_UNSUPPORTED, "the second sliding interface (periodic x) takes the plane geometry and Euler physics");
   long long E = (long long)(d->nel_static[0] + d->nel_moving[0]) * d->nel_static[1] * d->nel_static[2];
   if (E > (1LL << 31)) return fail(SM_ERR_ARG, "too many elements");
   return SM_OK;
@@ -639,12 +657,23 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   } else if (!desc->interface_conforming && desc->geom == SM_GEOM_PLANE) {
     SM_ALLOC(s->Ts, fbytes);
     SM_ALLOC(s->Tm, fbytes);
+    if (desc->periodic_x) {
+      SM_ALLOC(s->Ts2, fbytes);
+      SM_ALLOC(s->Tm2, fbytes);
+      SM_ALLOC(s->Fs2, fbytes);
+      SM_ALLOC(s->Fm2, fbytes);
+    }
   }
   if (desc->geom != SM_GEOM_PLANE) SM_ALLOC(s->geo, (size_t)m.E * 13 * s->nn * s->sb);
 #undef SM_ALLOC
   m.basis = s->basis_d;
   m.modes = s->modes_d;
   m.topo = s->topo_d;
+  m.periodic_x = desc->periodic_x;
+  m.Ts2 = s->Ts2;
+  m.Tm2 = s->Tm2;
+  m.Fs2 = s->Fs2;
+  m.Fm2 = s->Fm2;
   fill_constants(m, s->basis_h, desc->fpar);
   // static mesh topology: neighbour codes and packed position of every element
   std::vector<int4> topo(2 * (size_t)m.E);
@@ -654,7 +683,7 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
     for (int fc = 0; fc < 6; ++fc) {
       long long q = 0;
       int kind = face_neighbor(m, p, fc >> 1, fc & 1, &q);
-      nb[fc] = kind == 0 ? (int)q : (kind == 1 ? -1 : -2);
+      nb[fc] = kind == 0 ? (int)q : (kind == 1 ? -1 : (kind == 2 ? -2 : -3));
     }
     topo[2 * e] = make_int4(nb[0], nb[1], nb[2], nb[3]);
     topo[2 * e + 1] = make_int4(nb[4], nb[5], (p.ix << 1) | p.blk, p.iz * m.ny + p.iy);
@@ -1030,6 +1059,7 @@ extern "C" int sm_batch_create(sm_solver* const* solvers, const double* dt, int 
     if (solvers[i]->desc.physics != SM_EULER) return fail(SM_ERR_UNSUPPORTED, "batched kernels are Euler; step Navier-Stokes solvers with sm_step");
     if (solvers[i]->desc.geom != SM_GEOM_PLANE) return fail(SM_ERR_UNSUPPORTED, "batched kernels are for the plane interface");
     if (solvers[i]->desc.volume != SM_VOLUME_WEAK) return fail(SM_ERR_UNSUPPORTED, "batched kernels take the weak-form volume integral");
+    if (solvers[i]->desc.periodic_x) return fail(SM_ERR_UNSUPPORTED, "batched kernels take one sliding interface");
   }
   sm_batch* b = new (std::nothrow) sm_batch();
   if (!b) return fail(SM_ERR_OOM, "host allocation");
@@ -1284,6 +1314,7 @@ extern "C" int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, 
   if (desc->physics != SM_EULER) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes the Euler operator only");
   if (desc->geom != SM_GEOM_PLANE) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes the plane interface only");
   if (desc->volume != SM_VOLUME_WEAK) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes the weak-form operator only");
+  if (desc->periodic_x) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes one sliding interface only");
   if (!motion || !dU || !dUt) return fail(SM_ERR_ARG, "NULL argument");
   if (dU == dUt) return fail(SM_ERR_ARG, "dU and dUt must not overlap");
   if (motion->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");

@@ -97,8 +97,10 @@ cudaError_t prepare_interface_ns(int N, int prec);
 // the stage-mode element kernel or launch_gather_traces), or nullptr to read them from U.
 cudaError_t launch_interface(int N, int prec, int riemann, const MeshDev& m, const StageParams* sp, const void* U,
                              void* Fs, void* Fm, cudaStream_t st, const void* Ts = nullptr, const void* Tm = nullptr);
-// sm_aux.cu: the interface traces of U into Ts / Tm
-cudaError_t launch_gather_traces(int N, int prec, const MeshDev& m, const void* U, void* Ts, void* Tm, cudaStream_t st);
+// sm_aux.cu: the interface traces of U into Ts / Tm (ifc 1: the second interface of a
+// periodic x direction, x-momentum mirrored)
+cudaError_t launch_gather_traces(int N, int prec, const MeshDev& m, const void* U, void* Ts, void* Tm, cudaStream_t st,
+                                 int ifc = 0);
 cudaError_t prepare_interface(int N, int prec);
 
 // sm_aux.cu: initial data, reductions

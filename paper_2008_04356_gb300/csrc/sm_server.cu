@@ -44,12 +44,15 @@ size_t request_bytes(const sm_mesh_desc& d) {
   size_t b = 3 * E * nn * 5 * sb + 2 * faces * 5 * np * np * sb + 32 * E + (64 << 10);
   if (d.physics == SM_NAVIER_STOKES) b += E * nn * 15 * sb + 2 * faces * 5 * np * np * sb;   // gradients, lifting
   if (d.geom != SM_GEOM_PLANE) b += E * nn * 13 * sb;                                          // curvilinear geometry
+  if (d.physics == SM_EULER && d.geom == SM_GEOM_PLANE && !d.interface_conforming)             // traces (and a second
+    b += (d.periodic_x ? 6 : 2) * faces * 5 * np * np * sb;                                    // interface's arrays)
   return b;
 }
 
 // FP32 Euler solves on the plane interface share the batched kernels; the others step alone
 bool batchable(const sm_mesh_desc& d) {
-  return d.precision == SM_FP32 && d.physics == SM_EULER && d.geom == SM_GEOM_PLANE && d.volume == SM_VOLUME_WEAK;
+  return d.precision == SM_FP32 && d.physics == SM_EULER && d.geom == SM_GEOM_PLANE && d.volume == SM_VOLUME_WEAK &&
+         !d.periodic_x;
 }
 
 }  // namespace

@@ -27,7 +27,7 @@ class SmMeshDesc(C.Structure):
                 ("riemann", C.c_int), ("precision", C.c_int), ("interface_conforming", C.c_int),
                 ("flow", C.c_int), ("fpar", C.c_double * 16), ("modes", C.c_double * 160),
                 ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double),
-                ("volume", C.c_int)]
+                ("volume", C.c_int), ("periodic_x", C.c_int)]
 
 
 class SmMotion(C.Structure):
@@ -149,6 +149,7 @@ def mesh_desc(p: synth.Problem) -> SmMeshDesc:
         d.modes[k] = m
     d.physics, d.mu, d.Pr, d.Rgas = int(p.physics), float(p.mu), float(p.Pr), float(p.Rgas)
     d.volume = int(getattr(p, "volume", 0))
+    d.periodic_x = int(getattr(p, "periodic_x", 0))
     return d
 
 
