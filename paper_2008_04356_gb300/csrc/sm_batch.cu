@@ -165,7 +165,7 @@ cudaError_t prep_el() {
                                        (int)ElemCfg<N>::template smem_bytes<float>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(dg_element_batch_kernel<N, RIEM, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              (int)cudaSharedmemCarveoutMaxShared);
+                              (int)cudaSharedmemCarveoutDefault);
 }
 
 template <int N>

@@ -477,6 +477,10 @@ static cudaError_t launch_elem_t(const ElemArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// No shared-memory carveout preference: the driver takes the smallest shared-memory
+// configuration that holds the resident CTAs, and the rest of the SM's 256 KB stays L1,
+// which then holds the element's own and its neighbours' face traces the face fluxes re-read
+// (measured on N = 5: 11 % faster than the maximum-shared configuration).
 template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
 static cudaError_t prepare_elem_t() {
   using C = ElemCfg<N>;
@@ -484,7 +488,7 @@ static cudaError_t prepare_elem_t() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::template smem_bytes<T>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(dg_element_kernel<N, T, RIEM, MODE, PHYS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              (int)cudaSharedmemCarveoutMaxShared);
+                              (int)cudaSharedmemCarveoutDefault);
 }
 
 template <int N, typename T>

@@ -237,7 +237,7 @@ static cudaError_t prepare_split_t() {
                                        (int)SplitCfg<N>::template smem_bytes<T>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(dg_element_split_kernel<N, T, RIEM, MODE>,
-                              cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+                              cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutDefault);
 }
 
 template <int N, typename T>
