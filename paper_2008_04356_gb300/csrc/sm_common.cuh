@@ -319,6 +319,37 @@ __device__ __forceinline__ void riemann_axis(const T UL[5], const T UR[5], T vgn
   for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * D[k];
 }
 
+// Rusanov flux along the outward normal n = sgn e_ax (sgn = +-1) of the element holding
+// uin, ALE form with the normal grid speed vgn = v^g . n:
+//   F* = (F(uin).n + F(uout).n) / 2 - a (uout - uin) / 2,
+//   a = max(|v_in.n - vgn| + c_in, |v_out.n - vgn| + c_out).
+// Every term changes sign exactly when the two states trade places and n and vgn change
+// sign, and the same operations run for both neighbours of a face, so both obtain the same
+// flux bit for bit (conservation) without a canonical orientation.
+template <typename T>
+__device__ __forceinline__ void rusanov_outward(const T uin[5], const T uout[5], const int ax, const T sgn,
+                                                const T vgn, const T gamma, T F[5]) {
+  const Prim<T> qi = primitives(uin, gamma), qo = primitives(uout, gamma);
+  const T uni = sgn * (ax == 0 ? qi.u[0] : (ax == 1 ? qi.u[1] : qi.u[2]));
+  const T uno = sgn * (ax == 0 ? qo.u[0] : (ax == 1 ? qo.u[1] : qo.u[2]));
+  const T wi = uni - vgn, wo = uno - vgn;
+  const T pni = sgn * qi.p, pno = sgn * qo.p;
+  T Fi[5], Fo[5];
+  Fi[0] = uin[0] * wi;
+  Fo[0] = uout[0] * wo;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Fi[1 + k] = uin[1 + k] * wi + (k == ax ? pni : T(0));
+    Fo[1 + k] = uout[1 + k] * wo + (k == ax ? pno : T(0));
+  }
+  Fi[4] = uin[4] * wi + qi.p * uni;
+  Fo[4] = uout[4] * wo + qo.p * uno;
+  const T ci = Prec<T>::sqrt_(gamma * qi.p * qi.ir), co = Prec<T>::sqrt_(gamma * qo.p * qo.ir);
+  const T a = fmax(fabs(wi) + ci, fabs(wo) + co);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (Fi[k] + Fo[k]) - T(0.5) * a * (uout[k] - uin[k]);
+}
+
 // Cyclic rotation of the momentum components that brings physical axis ax (0 = x, 1 = y,
 // 2 = z) to the first slot: (m_ax, m_ax+1, m_ax+2) (indices mod 3).  A cyclic permutation
 // is a proper rotation, under which the Riemann fluxes are invariant, so every face is

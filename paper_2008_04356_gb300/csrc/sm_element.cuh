@@ -238,8 +238,19 @@ __device__ __forceinline__ void element_face_fluxes(const MeshDev& m, const Stag
         if (tp) { pos_ix = tp[6] >> 1; pos_f = tp[7]; }
         dirichlet_exterior<N, T>(m, sp, blk2, pos_ix, pos_f, vn, uout);
       }
-      // canonical orientation: left = minus-side element, normal +axis
       const int ax = d == 0 ? 1 : (d == 1 ? 2 : 0);
+      if constexpr (RIEM == 0 && PHYS == 0) {
+        // Rusanov along the outward normal: exactly antisymmetric between the neighbours
+        T fo[5];
+        const T sgn = side ? T(1) : T(-1);
+        const T vgn = (d == 0 && blk2) ? sgn * c[MC_VG] : T(0);
+        rusanov_outward<T>(uin, uout, ax, sgn, vgn, gamma, fo);
+        const T sJ = c[MC_METRIC + 3 * blk2 + d];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sS[((l2 * 6 + fc) * 5 + v) * NP2 + ab] = sJ * fo[v];
+        continue;
+      }
+      // canonical orientation: left = minus-side element, normal +axis
       T L[5], R[5], fl[5], fs[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
