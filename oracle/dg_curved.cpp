@@ -7,7 +7,12 @@
  *   geom 1: the cylindrical sliding interface of Sec. 3.3 (rotor inside the circle,
  *           stator outside, relative motion a rotation), the "rotation with a
  *           cylindrical radial interface" geometry of the paper's overview figure;
- *   geom 2: the plane two-block box of dg_oracle.cpp, written through general metrics.
+ *   geom 2: the plane two-block box of dg_oracle.cpp, written through general metrics;
+ *   geom 3: the plane annular interface normal to the rotation axis (the "rotation with a
+ *           plane annular axial interface" geometry of the paper's overview figure): rotor
+ *           z in [x0, x1] below the stator z in [x1, x2], both annular sectors with radii
+ *           [z0, z1] (xi^2 runs from r = z1 to r = z0, which keeps the map (theta, r, z)
+ *           right-handed); slip walls at both radii and at the axial ends.
  *
  * Readings (the paper does not print them):
  *   - metrics: conservative curl form of Kopriva (2006), antisymmetrised,
@@ -45,7 +50,8 @@ struct Curved {
   long long Es, Em, E;
   int ny, nz;                /* faces along xi^1 (sliding) and xi^2 (perpendicular) */
   double h1, h2, h3[2];      /* element sizes along xi^1, xi^2, xi^3 (per block) */
-  bool cyl, ns;
+  bool cyl, ns;              /* cyl: a rotor turning about z (geom 1 and 3) */
+  bool annular;              /* geom 3: reference axes (theta, r, z) instead of (theta, z, r) */
   double Theta;              /* periodic sector angle (geom 1) */
   std::vector<double> x, w, D, Dhat;
   double A[5], B[5], c[5];
@@ -185,7 +191,14 @@ void build_geometry(Curved& o) {
           double s2 = o.p.z0 + id.iz * o.h2 + (o.x[j] + 1.0) * 0.5 * o.h2;
           double s3 = lo3 + id.ix * o.h3[id.blk] + (o.x[k] + 1.0) * 0.5 * o.h3[id.blk];
           int nd = node(o, i, j, k);
-          if (o.cyl) {
+          if (o.annular) {          /* xi^1 -> theta, xi^2 -> -r (right-handed), xi^3 -> z */
+            double rr = o.p.z0 + o.p.z1 - s2;
+            X[nd] = rr * std::cos(s1);
+            X[nn + nd] = rr * std::sin(s1);
+            X[2 * nn + nd] = s3;
+            continue;
+          }
+          if (o.cyl) {              /* xi^1 -> theta, xi^2 -> z, xi^3 -> r */
             X[nd] = s3 * std::cos(s1);
             X[nn + nd] = s3 * std::sin(s1);
           } else {
@@ -201,9 +214,10 @@ void build_geometry(Curved& o) {
     {
       double s1 = o.p.y0 + (id.iy + 0.5) * o.h1, s2 = o.p.z0 + (id.iz + 0.5) * o.h2;
       double s3 = lo3 + (id.ix + 0.5) * o.h3[id.blk];
-      Xc[0] = o.cyl ? s3 * std::cos(s1) : s3;
-      Xc[1] = o.cyl ? s3 * std::sin(s1) : s1;
-      Xc[2] = s2;
+      double rc = o.p.z0 + o.p.z1 - s2;
+      Xc[0] = o.annular ? rc * std::cos(s1) : (o.cyl ? s3 * std::cos(s1) : s3);
+      Xc[1] = o.annular ? rc * std::sin(s1) : (o.cyl ? s3 * std::sin(s1) : s1);
+      Xc[2] = o.annular ? s3 : s2;
     }
     for (int n = 0; n < 3; ++n)
       for (int nd = 0; nd < nn; ++nd) X[n * nn + nd] -= Xc[n];
@@ -267,7 +281,9 @@ int neighbour(const Curved& o, const Id& id, int d, int side, long long* nb, dou
     return 0;
   }
   if (d == 1) {
-    *nb = elem_index(o, id.blk, id.ix, id.iy, wrap(id.iz + (side ? 1 : -1), o.nz));
+    int iz = id.iz + (side ? 1 : -1);
+    if (o.annular && (iz < 0 || iz >= o.nz)) return 1;   /* slip walls at the radii */
+    *nb = elem_index(o, id.blk, id.ix, id.iy, wrap(iz, o.nz));
     return 0;
   }
   int jx = id.ix + (side ? 1 : -1);
@@ -715,7 +731,9 @@ void* orc_curved_create(const orc_problem* p) {
   o->Es = (long long)p->nel_s[0] * o->ny * o->nz;
   o->Em = (long long)p->nel_m[0] * o->ny * o->nz;
   o->E = o->Es + o->Em;
-  o->cyl = p->geom == 1;
+  if (p->geom < 1 || p->geom > 3) { delete o; return nullptr; }
+  o->cyl = p->geom == 1 || p->geom == 3;
+  o->annular = p->geom == 3;
   o->ns = p->physics == 1;
   o->h1 = (p->y1 - p->y0) / o->ny;
   o->h2 = (p->z1 - p->z0) / o->nz;

@@ -40,7 +40,8 @@ typedef struct {
   double mu, Pr, Rgas;   /* viscosity, Prandtl number, gas constant (Navier-Stokes) */
   int geom;              /* 0 plane interface (Cartesian operator); 1 cylindrical interface
                             (curvilinear operator); 2 plane interface through the
-                            curvilinear operator (general metrics) */
+                            curvilinear operator (general metrics); 3 plane annular interface
+                            normal to the rotation axis (curvilinear operator) */
   int volume;            /* volume integral (Sec. 3.1): 0 weak form; 1 split form with
                             Pirozzoli's two-point flux; 2 split form with the central
                             two-point flux (equal to the weak form by summation by parts).
@@ -50,6 +51,12 @@ typedef struct {
                             interface (several interfaces, Sec. 4.3); geom 0, Euler physics */
 } orc_problem;
 
+/* geom 3, the plane annular interface of Sec. 3.3 normal to the rotation axis: x0 < x1 < x2
+ * are axial positions (block 0 = rotor, z in [x0, x1]; block 1 = stator, z in [x1, x2]),
+ * [y0, y1] the periodic angular sector, [z0, z1] the radii (z0 > 0); slip walls at both radii
+ * and at z = x0, x2; reference axes xi^1 -> theta (sliding), xi^2 -> r (from r = z1 down to
+ * r = z0: a right-handed map), xi^3 -> z.  Motion,
+ * flows and the periodic sector as for geom 1. */
 /* geom 1, the cylindrical sliding interface of Sec. 3.3 (a rotor inside the circle):
  * x0 < x1 < x2 are the radii (block 0 = rotor, r in [x0, x1]; block 1 = stator, r in
  * [x1, x2]), [y0, y1] the periodic angular sector (the state crosses its ends rotated by

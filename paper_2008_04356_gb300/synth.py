@@ -22,7 +22,7 @@ M2 = np.uint64(0x94D049BB133111EB)
 
 FLOW_CONSTANT, FLOW_ENTROPY_WAVE, FLOW_MODES, FLOW_POLY_X, FLOW_SHEAR_X = 0, 1, 2, 3, 4
 FLOW_AXIAL_PULSE, FLOW_RIGID_ROTATION = 5, 6
-GEOM_PLANE, GEOM_CYLINDER, GEOM_PLANE_CURVILINEAR = 0, 1, 2
+GEOM_PLANE, GEOM_CYLINDER, GEOM_PLANE_CURVILINEAR, GEOM_ANNULAR = 0, 1, 2, 3
 EULER, NAVIER_STOKES = 0, 1
 RUSANOV, ROE_HH = 0, 1
 FP64, FP32 = 0, 1
@@ -196,6 +196,26 @@ def config_cylinder(N: int = 3, nel=(3, 8, 2), omega: float = 0.4, phi0: float =
                    physics=physics, mu=mu, geom=GEOM_CYLINDER)
 
 
+def config_annular(N: int = 3, nel=(2, 8, 2), omega: float = 0.4, phi0: float = 0.0,
+                   z=(0.0, 0.25, 0.5), sector: float = math.pi / 4, r=(1.0, 1.5),
+                   flow: str = "pulse", precision: int = FP64) -> Problem:
+    """Plane annular sliding interface normal to the rotation axis: rotor z in [z0, z1]
+    below the stator z in [z1, z2], radii [r0, r1], angular sector [0, sector] periodic, slip
+    walls at both radii and at both axial ends; nel = (axial per block, angular, radial).
+    flow "pulse": fluid at rest (rho = 1, p = 1) with a Gaussian pressure pulse of 1e-2 on
+    the interface; "rotation": rigid rotation with the rotor's angular speed (a steady
+    solution); "rest": uniform state at rest."""
+    if flow == "pulse":
+        fl, fpar = FLOW_AXIAL_PULSE, (1.0, 1.0, 0.0, 1.0e-2, 0.5 * (r[0] + r[1]), 0.5 * sector, z[1], 0.08)
+    elif flow == "rotation":
+        fl, fpar = FLOW_RIGID_ROTATION, (1.0, 1.0, omega)
+    else:
+        fl, fpar = FLOW_CONSTANT, (1.0, 0.0, 0.0, 0.0, 1.0)
+    return Problem(N=N, nel_s=(nel[0], nel[1], nel[2]), nel_m=(nel[0], nel[1], nel[2]),
+                   x0=z[0], x1=z[1], x2=z[2], y0=0.0, y1=sector, z0=r[0], z1=r[1],
+                   v=omega, delta0=phi0, flow=fl, fpar=fpar, precision=precision, geom=GEOM_ANNULAR)
+
+
 def config_poly_x(N: int = 3, v: float = 0.5, coeffs=(1.0, 0.1, -0.05, 0.02),
                   vel=(0.3, 0.2, -0.1), p: float = 1.0) -> Problem:
     """State polynomial in x (degree <= 3) with constant velocity and pressure."""
@@ -222,7 +242,7 @@ def wave_speed_bounds(p: Problem):
     elif p.flow == FLOW_AXIAL_PULSE:
         rho_min, pmax, vel = f[0], f[1] + abs(f[3]), [0.0, 0.0, abs(f[2])]
     elif p.flow == FLOW_RIGID_ROTATION:
-        rmax = max(abs(p.x0), abs(p.x2))
+        rmax = max(abs(p.z0), abs(p.z1)) if p.geom == GEOM_ANNULAR else max(abs(p.x0), abs(p.x2))
         w = abs(f[2]) * rmax
         rho_min, pmax, vel = f[0], f[1] + 0.5 * f[0] * w * w, [w, w, 0.0]
     elif p.flow == FLOW_POLY_X:
@@ -240,6 +260,16 @@ def cfl_dt(p: Problem, cfl: float = 0.9) -> float:
     """dt = CFL / ((2N+1) * sum_d (|v_d - v^g_d| + c) / h_d), the largest over both blocks
     (grid velocity 0 in the static block, v along y in the moving one)."""
     vel, c = wave_speed_bounds(p)
+    if p.geom == GEOM_ANNULAR:
+        # angular (arc length at the inner radius), radial and axial sizes; the rotor's grid
+        # speed is at most omega r1
+        ha = p.z0 * (p.y1 - p.y0) / p.nel_s[1]
+        hr = (p.z1 - p.z0) / p.nel_s[2]
+        vmax = math.sqrt(vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)
+        rate = 0.0
+        for hz, vg in (((p.x1 - p.x0) / p.nel_s[0], abs(p.v) * p.z1), ((p.x2 - p.x1) / p.nel_m[0], 0.0)):
+            rate = max(rate, (vmax + c) / hz + (vmax + vg + c) / ha + (vmax + c) / hr)
+        return cfl / ((2 * p.N + 1) * rate)
     if p.geom == GEOM_CYLINDER:
         # radial, angular (arc length at the inner radius) and axial sizes; the rotor's grid
         # speed is omega r
