@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=256, help="elements along z (256 = the full workload)")
-    ap.add_argument("--workload", choices=["interface-heavy", "serving", "cylinder"], default="interface-heavy")
+    ap.add_argument("--workload", choices=["interface-heavy", "serving", "cylinder", "annular"], default="interface-heavy")
     ap.add_argument("--volume", choices=["weak", "split"], default="weak",
                     help="volume integral of the interface-heavy headline: weak form, or the split form")
     ap.add_argument("--riemann", choices=["rusanov", "roe"], default=None,
@@ -353,9 +353,16 @@ CYL_WORKLOAD = ("rotating cylindrical sliding interface, Navier-Stokes with BR1 
                 "omega=0.4, N=7 (18.9M DOF), Re=1e4, Pr=0.72, Mach 0.3 axial stream with a pressure pulse")
 
 
+ANN_WORKLOAD = ("rotating plane annular sliding interface normal to the axis, Euler: rotor z in [0,0.25] below "
+                "the stator z in [0.25,0.5], radii r in [1,1.5], theta in [0,pi/4] periodic, slip walls; rotor "
+                "and stator blocks of 24x48x16 curved hexes each (36,864 elements, 768 sliding faces per side), "
+                "rotor omega=0.4, N=7 (18.9M DOF), fluid at rest with a pressure pulse on the interface")
+
+
 def run_cylinder(args, rank, world, local):
-    """The rotating cylindrical interface with Navier-Stokes at N = 7: RK steps through the
-    curvilinear kernels (interface lifting, lifting, viscous interface flux, element)."""
+    """The rotating cylindrical interface with Navier-Stokes at N = 7 (or, --workload
+    annular, the plane annular interface with Euler): RK steps through the curvilinear
+    kernels (interface lifting, lifting, viscous interface flux, element)."""
     import torch
     from paper_2008_04356_gb300 import build as B, slidemesh, synth
     import torch.distributed as dist
@@ -366,8 +373,12 @@ def run_cylinder(args, rank, world, local):
     B.build_library()
     stream = torch.cuda.current_stream()
     prec = synth.FP64 if args.precision == "fp64" else synth.FP32
-    p = synth.config_cylinder(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec,
-                              physics=synth.NAVIER_STOKES)
+    annular = args.workload == "annular"
+    if annular:
+        p = synth.config_annular(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec)
+    else:
+        p = synth.config_cylinder(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec,
+                                  physics=synth.NAVIER_STOKES)
     sol = slidemesh.Solver(p)
     sol.init_state()
     dt = synth.cfl_dt(p)
@@ -388,8 +399,8 @@ def run_cylinder(args, rank, world, local):
     kms, kcnt = sol.step_profiled(dt, args.profile_steps)
     sb = 8 if prec == synth.FP64 else 4
     # element kernel per DOF-update: U in/out, G in (4 of 5 stages)/out, 13 geometry values,
-    # 15 gradients
-    elem_bytes = ((2 + 1 + 0.8) * 5 + 13 + 15) * sb * p.ndof
+    # 15 gradients (Navier-Stokes)
+    elem_bytes = ((2 + 1 + 0.8) * 5 + 13 + (0 if annular else 15)) * sb * p.ndof
     elem_ms = kms[2] / kcnt[2]
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -404,20 +415,20 @@ def run_cylinder(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32", "data": "synthetic",
-        "config": {"workload": CYL_WORKLOAD, "elements": p.nelem, "N": p.N, "dof": p.ndof,
+        "config": {"workload": ANN_WORKLOAD if annular else CYL_WORKLOAD, "elements": p.nelem, "N": p.N, "dof": p.ndof,
                    "sliding_faces_per_side": p.n_faces, "riemann": "rusanov", "mu": p.mu,
                    "l2": "inputs larger than L2 (%.2f GB state + %.2f GB geometry)" % (
                        p.ndof * 5 * sb / 1e9, p.ndof * 13 * sb / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU", "dt": dt, "final_t": d["t"]},
         "interface_face_updates_per_s": rep.value(p.n_faces * 5 * args.steps, ms * 1e-3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "curved_element_kernel<N=7, %s, Rusanov, stage, NS>" % (
-                         "double" if prec == synth.FP64 else "float"),
+                     "traffic": None, "kernel": "curved_element_kernel<N=7, %s, Rusanov, stage%s>" % (
+                         "double" if prec == synth.FP64 else "float", "" if annular else ", NS"),
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": elem_bytes, "avg_launch_ms": elem_ms},
         "kernels": {"stage_params": {"launches": kcnt[0], "ms": kms[0]},
                     "lifting_and_interface": {"launches": kcnt[1], "ms": kms[1], "avg_ms": kms[1] / max(kcnt[1], 1)},
                     "curved_element": {"launches": kcnt[2], "ms": kms[2], "avg_ms": elem_ms}},
-        "gpu_launches": 5 * 5 * args.steps,
+        "gpu_launches": (3 if annular else 5) * 5 * args.steps,
         "clocks": clk,
         "diag": {"n_delta": d["n_delta"], "s_delta": d["s_delta"], "finite": d["status"] == 0,
                  "totals": d["totals"]},
@@ -440,7 +451,7 @@ def main():
         if rank == 0:
             run_serving(args)
         return
-    if args.workload == "cylinder":
+    if args.workload in ("cylinder", "annular"):
         run_cylinder(args, rank, world, local)
         return
     import numpy as np

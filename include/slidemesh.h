@@ -47,7 +47,7 @@ typedef enum {
 
 enum { SM_FP64 = 0, SM_FP32 = 1 };
 enum { SM_RUSANOV = 0, SM_ROE_HH = 1 };
-enum { SM_GEOM_PLANE = 0, SM_GEOM_CYLINDER = 1, SM_GEOM_PLANE_CURVILINEAR = 2 };
+enum { SM_GEOM_PLANE = 0, SM_GEOM_CYLINDER = 1, SM_GEOM_PLANE_CURVILINEAR = 2, SM_GEOM_ANNULAR = 3 };
 enum { SM_EULER = 0, SM_NAVIER_STOKES = 1 };
 /* Volume integral of the element operator (Sec. 3.1):
  *  SM_VOLUME_WEAK   weak-form DGSEM, sum-factorised flux divergence with Dhat = -M^-1 D^T M;
@@ -90,7 +90,15 @@ enum { SM_FLOW_CONSTANT = 0, SM_FLOW_ENTROPY_WAVE = 1, SM_FLOW_MODES = 2, SM_FLO
  * [x1, x2]), [y0, y1] is the periodic angular sector (states crossing its ends turn by the
  * sector angle), [z0, z1] the periodic axial extent; r = x0 and r = x2 are slip walls.
  * Curved elements from the analytic map, metric terms in conservative curl form; Euler.
- * geom SM_GEOM_PLANE_CURVILINEAR: the plane box through the same curvilinear kernels. */
+ * geom SM_GEOM_PLANE_CURVILINEAR: the plane box through the same curvilinear kernels.
+ *
+ * geom SM_GEOM_ANNULAR: the plane annular sliding interface normal to the rotation axis (Sec.
+ * 3.3, the third rotating geometry of the paper's overview figure): x0 < x1 < x2 are axial
+ * positions (the static-block slot holds the rotor, z in [x0, x1]; the moving-block slot the
+ * stator, z in [x1, x2]), [y0, y1] is the periodic angular sector, [z0, z1] the radii
+ * (z0 > 0; element index iz runs from the outer radius inwards, which keeps the map right-
+ * handed); slip walls at both radii and at z = x0, x2.  Motion, flows and curved elements
+ * as for the cylinder; Euler or Navier-Stokes. */
 typedef struct {
   int N;                   /* polynomial degree, 1..7 */
   int geom;                /* SM_GEOM_PLANE */
@@ -117,7 +125,7 @@ typedef struct {
 } sm_mesh_desc;
 
 /* Motion of the moving block: displacement Delta(t) = delta0 + v t along +y (Sec. 4.3,
- * Fig. coordinates); omega must be 0.  Cylinder: the rotor turns about the z axis by the
+ * Fig. coordinates); omega must be 0.  Cylinder and annulus: the rotor turns about the z axis by the
  * angle delta0 + omega t (v must be 0); the stator's displacement seen from the rotor is
  * minus that angle, in units of the angular face size. */
 typedef struct {

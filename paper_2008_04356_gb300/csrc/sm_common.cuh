@@ -164,6 +164,11 @@ __device__ __forceinline__ float Prec<float>::fpar(const MeshDev& m, int k) { re
 // ---------------------------------------------------------------------------------------
 struct ElemPos { int blk, ix, iy, iz; };
 
+// Geometries with a rotor turning about the z axis: 1 the cylindrical interface, 3 the plane
+// annular interface normal to the axis (reference axes xi^1 -> theta, xi^2 -> r from the outer
+// radius z1 down to z0, xi^3 -> z).
+__host__ __device__ __forceinline__ bool rotating_geom(int geom) { return geom == 1 || geom == 3; }
+
 // Element counts stay below 2^31 (checked when a solver is created): 32-bit arithmetic.
 __host__ __device__ __forceinline__ ElemPos decode_elem(const MeshDev& m, long long e64) {
   ElemPos p;
@@ -201,6 +206,7 @@ __host__ __device__ __forceinline__ int face_neighbor(const MeshDev& m, const El
   }
   if (d == 1) {
     int iz = p.iz + (side ? 1 : -1);
+    if (m.geom == 3 && (iz < 0 || iz >= m.nz)) return 1;   // annular: slip walls at the radii
     iz = iz < 0 ? iz + m.nz : (iz >= m.nz ? iz - m.nz : iz);
     *nb = encode_elem(m, p.blk, p.ix, p.iy, iz);
     return 0;
@@ -587,15 +593,18 @@ __device__ __forceinline__ void node_position(const MeshDev& m, const ElemPos& p
   const double* xi = m.basis->x;
   double hx = p.blk ? m.hx1 : m.hx0;
   double xlo = p.blk ? m.x1 : m.x0;
-  if (m.geom == 1) {
-    const double r = xlo + p.ix * hx + (xi[k] + 1.0) * 0.5 * hx;
+  if (rotating_geom(m.geom)) {
+    const double s3 = xlo + p.ix * hx + (xi[k] + 1.0) * 0.5 * hx;
+    const double s2 = m.z0 + p.iz * m.hz + (xi[j] + 1.0) * 0.5 * m.hz;
     const double th = m.y0 + p.iy * m.hy + (xi[i] + 1.0) * 0.5 * m.hy;
+    // cylinder: r = s3, z = s2; annular: r = z0 + z1 - s2, z = s3
+    const double r = m.geom == 1 ? s3 : 2.0 * m.z0 + m.nz * m.hz - s2;
     const double a0 = r * cos(th), a1 = r * sin(th);
     double c = 1.0, s = 0.0;
     if (p.blk == 0) sincos(-delta, &s, &c);
     X[0] = c * a0 - s * a1;
     X[1] = s * a0 + c * a1;
-    X[2] = m.z0 + p.iz * m.hz + (xi[j] + 1.0) * 0.5 * m.hz;
+    X[2] = m.geom == 1 ? s2 : s3;
     return;
   }
   X[0] = xlo + p.ix * hx + (xi[k] + 1.0) * 0.5 * hx;

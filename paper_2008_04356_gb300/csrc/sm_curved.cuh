@@ -1,7 +1,8 @@
 // Curvilinear kernels: the DGSEM operator of Sec. 3.1 with per-node metric terms
-// (Eq. transformed_equation) and the sliding interface of Sec. 3.3 on a curved
-// (cylindrical) interface, for the rotating geometry of the paper's overview figure
-// (rotor inside the circle, stator outside).
+// (Eq. transformed_equation) and the sliding interface of Sec. 3.3 for the rotating
+// geometries of the paper's overview figure: the cylindrical interface (rotor inside the
+// circle, stator outside; geom 1) and the plane annular interface normal to the axis (rotor
+// below, stator above; geom 3), both with a periodic angular sector and slip walls.
 //
 // Frames.  The state is stored in the global Cartesian frame.  The rotor (block 0 of the
 // cylinder) turns rigidly about the z axis by phi(t); its metrics at time t are R(phi)
@@ -20,7 +21,7 @@
 // cos, sin of the frame rotation of a block: the rotor of the cylinder turns by phi
 template <typename T>
 __device__ __forceinline__ void block_frame(const MeshDev& m, const StageParams* sp, int blk, T& c, T& s) {
-  if (m.geom == 1 && blk == 0) {
+  if (rotating_geom(m.geom) && blk == 0) {
     c = Prec<T>::rot(sp)[0];
     s = Prec<T>::rot(sp)[1];
   } else {
@@ -30,7 +31,7 @@ __device__ __forceinline__ void block_frame(const MeshDev& m, const StageParams*
 }
 
 // the moving block: the plane's block 1 translates, the cylinder's block 0 (rotor) turns
-__device__ __forceinline__ bool moving_block(const MeshDev& m, int blk) { return m.geom == 1 ? blk == 0 : blk == 1; }
+__device__ __forceinline__ bool moving_block(const MeshDev& m, int blk) { return rotating_geom(m.geom) ? blk == 0 : blk == 1; }
 
 // Viscous flux of a state and its gradients dotted with a vector N (all three columns).
 template <typename T>
@@ -173,12 +174,12 @@ __device__ __forceinline__ void curved_element_block(const MeshDev& m, const Sta
         for (int v = 0; v < 5; ++v) uout[v] = Un[v * NN];
         rotate_state_z(uout, ec, -es);
         const int iy = pos_f % m.ny;
-        if (m.geom == 1 && d == 0 && ((side && iy == m.ny - 1) || (!side && iy == 0))) {
+        if (rotating_geom(m.geom) && d == 0 && ((side && iy == m.ny - 1) || (!side && iy == 0))) {
           pc = c[MC_PCOS];
           ps = side ? c[MC_PSIN] : -c[MC_PSIN];
           rotate_state_z(uout, pc, ps);
         }
-      } else if (m.geom == 1) {
+      } else if (rotating_geom(m.geom)) {
         // slip wall: interior state with the normal momentum reflected; the wall moves
         // tangentially (zero normal grid velocity)
         wall = true;
@@ -354,8 +355,8 @@ __device__ __forceinline__ void curved_interface_tile(const MeshDev& m, const St
     T ac = T(1), as = T(0);
     // the halo static face i0 + TFe = n_par of the last tile is static face 0's periodic
     // image: turned by +Theta, like the moving faces it meets
-    const bool image = m.geom == 1 && !side && i0 + r >= ny;
-    if (m.geom == 1) {
+    const bool image = rotating_geom(m.geom) && !side && i0 + r >= ny;
+    if (rotating_geom(m.geom)) {
       if (side) {
         const T* a = Prec<T>::arot(sp, s_wk[r]);
         ac = a[0];
@@ -425,7 +426,7 @@ __device__ __forceinline__ void curved_interface_tile(const MeshDev& m, const St
       }
       Nm[c3] = an;
     }
-    if (m.geom == 1 && r == TFe && i0 + TFe >= ny) {
+    if (rotating_geom(m.geom) && r == TFe && i0 + TFe >= ny) {
       // the halo face is static face 0's image: its normal turned by +Theta
       const T x = c[MC_PCOS] * Nm[0] - c[MC_PSIN] * Nm[1], y = c[MC_PSIN] * Nm[0] + c[MC_PCOS] * Nm[1];
       Nm[0] = x;
@@ -486,7 +487,7 @@ __device__ __forceinline__ void curved_interface_tile(const MeshDev& m, const St
       for (int jj = 0; jj < NP; ++jj) acc += Blo[jj] * flo[v * NP2 + jj] + Bhi[jj] * fhi[v * NP2 + jj];
       o[v] = side ? -acc : acc;
     }
-    if (m.geom == 1) {
+    if (rotating_geom(m.geom)) {
       T oc = rc, os = rs;
       if (side) {
         const T* a = Prec<T>::arot(sp, s_wk[r + 1]);
@@ -590,9 +591,9 @@ __device__ __forceinline__ void curved_lift_block(const MeshDev& m, const StageP
         for (int v = 0; v < 5; ++v) uout[v] = Un[v * NN];
         rotate_state_z(uout, ec, -es);
         const int iy = pos_f % m.ny;
-        if (m.geom == 1 && d == 0 && ((side && iy == m.ny - 1) || (!side && iy == 0)))
+        if (rotating_geom(m.geom) && d == 0 && ((side && iy == m.ny - 1) || (!side && iy == 0)))
           rotate_state_z(uout, c[MC_PCOS], side ? c[MC_PSIN] : -c[MC_PSIN]);
-      } else if (m.geom == 1) {
+      } else if (rotating_geom(m.geom)) {
         const T isJ = Prec<T>::rcp(Prec<T>::sqrt_(Nv[0] * Nv[0] + Nv[1] * Nv[1] + Nv[2] * Nv[2]));
         const T nrm[3] = {Nv[0] * isJ, Nv[1] * isJ, Nv[2] * isJ};
         const T mn = uin[1] * nrm[0] + uin[2] * nrm[1] + uin[3] * nrm[2];

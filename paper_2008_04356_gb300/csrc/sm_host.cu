@@ -212,6 +212,13 @@ void curvilinear_geometry(const MeshDev& m, const BasisDev& b, int N, std::vecto
           const double s2 = m.z0 + p.iz * m.hz + (b.x[j] + 1.0) * 0.5 * m.hz;
           const double s3 = lo3 + p.ix * h3 + (b.x[k] + 1.0) * 0.5 * h3;
           const int q = idx(i, j, k);
+          if (m.geom == 3) {        // annular: (theta, r from z1 down to z0, z), right-handed
+            const double r = 2.0 * m.z0 + m.nz * m.hz - s2;
+            X[q] = r * cos(s1);
+            X[nn + q] = r * sin(s1);
+            X[2 * nn + q] = s3;
+            continue;
+          }
           if (m.geom == 1) {
             X[q] = s3 * cos(s1);
             X[nn + q] = s3 * sin(s1);
@@ -226,9 +233,10 @@ void curvilinear_geometry(const MeshDev& m, const BasisDev& b, int N, std::vecto
     double Xc[3];
     {
       const double s1 = m.y0 + (p.iy + 0.5) * m.hy, s2 = m.z0 + (p.iz + 0.5) * m.hz, s3 = lo3 + (p.ix + 0.5) * h3;
-      Xc[0] = m.geom == 1 ? s3 * cos(s1) : s3;
-      Xc[1] = m.geom == 1 ? s3 * sin(s1) : s1;
-      Xc[2] = s2;
+      const double rc = 2.0 * m.z0 + m.nz * m.hz - s2;
+      Xc[0] = m.geom == 3 ? rc * cos(s1) : (m.geom == 1 ? s3 * cos(s1) : s3);
+      Xc[1] = m.geom == 3 ? rc * sin(s1) : (m.geom == 1 ? s3 * sin(s1) : s1);
+      Xc[2] = m.geom == 3 ? s3 : s2;
     }
     std::vector<double> Xg(X);   // global coordinates for the grid-velocity factors
     for (int c = 0; c < 3; ++c)
@@ -255,11 +263,11 @@ void curvilinear_geometry(const MeshDev& m, const BasisDev& b, int N, std::vecto
         for (int q = 0; q < nn; ++q) g[(3 * i + n) * nn + q] = -0.5 * (T1[q] - T2[q]);
       }
     }
-    const bool moving = m.geom == 1 ? p.blk == 0 : p.blk == 1;
+    const bool moving = rotating_geom(m.geom) ? p.blk == 0 : p.blk == 1;
     if (moving)
       for (int i = 0; i < 3; ++i)
         for (int q = 0; q < nn; ++q)
-          g[(10 + i) * nn + q] = m.geom == 1 ? -Xg[nn + q] * g[(3 * i) * nn + q] + Xg[q] * g[(3 * i + 1) * nn + q]
+          g[(10 + i) * nn + q] = rotating_geom(m.geom) ? -Xg[nn + q] * g[(3 * i) * nn + q] + Xg[q] * g[(3 * i + 1) * nn + q]
                                             : g[(3 * i + 1) * nn + q];
   }
 }
@@ -530,9 +538,15 @@ void free_solver(sm_solver* s) {
 int valid_desc(const sm_mesh_desc* d) {
   if (!d) return fail(SM_ERR_ARG, "desc is NULL");
   if (d->N < 1 || d->N > 7) return fail(SM_ERR_UNSUPPORTED, "N must be in 1..7");
-  if (d->geom != SM_GEOM_PLANE && d->geom != SM_GEOM_CYLINDER && d->geom != SM_GEOM_PLANE_CURVILINEAR)
+  if (d->geom != SM_GEOM_PLANE && d->geom != SM_GEOM_CYLINDER && d->geom != SM_GEOM_PLANE_CURVILINEAR &&
+      d->geom != SM_GEOM_ANNULAR)
     return fail(SM_ERR_UNSUPPORTED, "unknown interface geometry");
-  if (d->geom == SM_GEOM_CYLINDER) {
+  if (d->geom == SM_GEOM_ANNULAR) {
+    if (!(d->z0 > 0.0)) return fail(SM_ERR_ARG, "annular radii must be positive");
+    if (!(d->y1 - d->y0 <= 2.0 * M_PI + 1e-12)) return fail(SM_ERR_ARG, "the angular sector exceeds 2 pi");
+    if (d->flow != SM_FLOW_CONSTANT && d->flow != SM_FLOW_AXIAL_PULSE && d->flow != SM_FLOW_RIGID_ROTATION)
+      return fail(SM_ERR_ARG, "annular flows: constant, axial pulse, rigid rotation");
+  } else if (d->geom == SM_GEOM_CYLINDER) {
     if (!(d->x0 > 0.0)) return fail(SM_ERR_ARG, "cylinder radii must be positive");
     if (!(d->y1 - d->y0 <= 2.0 * M_PI + 1e-12)) return fail(SM_ERR_ARG, "the angular sector exceeds 2 pi");
     if (d->flow != SM_FLOW_CONSTANT && d->flow != SM_FLOW_AXIAL_PULSE && d->flow != SM_FLOW_RIGID_ROTATION)
@@ -737,7 +751,7 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
 
 int sm_set_motion(sm_solver* s, const sm_motion* mo) {
   if (!s || !mo) return fail(SM_ERR_ARG, "NULL argument");
-  const bool cyl = s->desc.geom == SM_GEOM_CYLINDER;
+  const bool cyl = rotating_geom(s->desc.geom);
   if (!cyl && mo->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");
   if (cyl && mo->v != 0.0) return fail(SM_ERR_UNSUPPORTED, "the cylinder's rotor rotates (omega), it does not translate");
   if (!std::isfinite(mo->v) || !std::isfinite(mo->omega) || !std::isfinite(mo->delta0))

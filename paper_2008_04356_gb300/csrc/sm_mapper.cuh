@@ -100,7 +100,7 @@ __device__ __forceinline__ void stage_params_body(const MeshDev& m, int np, Stag
     sp->sig_m = __dsub_rn(1.0, two_s);
     s_sig[0] = sp->sig_s;
     s_sig[1] = sp->sig_m;
-    if (m.geom == 1) {
+    if (rotating_geom(m.geom)) {
       // the rotor turns by phi = -delta; stator faces seen through w wraps: w Theta - phi
       const double phi = -delta;
       double c0, s0;

@@ -221,9 +221,9 @@ class Solver:
             pass
 
     def set_motion(self, v: float, delta0: float = 0.0):
-        """Plane: block speed v and initial displacement; cylinder: rotor angular speed v
+        """Plane: block speed v and initial displacement; cylinder and annulus: rotor angular speed v
         and initial angle delta0."""
-        if getattr(self.problem, "geom", 0) == synth.GEOM_CYLINDER:
+        if getattr(self.problem, "geom", 0) in (synth.GEOM_CYLINDER, synth.GEOM_ANNULAR):
             mo = SmMotion(0.0, float(v), float(delta0))
         else:
             mo = SmMotion(float(v), 0.0, float(delta0))
@@ -350,7 +350,7 @@ class Server:
     def submit(self, problem: synth.Problem, dt: float, nsteps: int, keep_state: bool = False) -> int:
         req = SmRequest()
         req.desc = mesh_desc(problem)
-        if getattr(problem, "geom", 0) == synth.GEOM_CYLINDER:
+        if getattr(problem, "geom", 0) in (synth.GEOM_CYLINDER, synth.GEOM_ANNULAR):
             req.motion = SmMotion(0.0, float(problem.v), float(problem.delta0))
         else:
             req.motion = SmMotion(float(problem.v), 0.0, float(problem.delta0))

@@ -1,0 +1,136 @@
+"""The plane annular sliding interface normal to the rotation axis (rotor below the stator,
+slip walls at the radii and the axial ends, periodic sector) on the GPU against the
+curvilinear oracle: right-hand side and interface fluxes (FP64 to 1e-12, FP32 to 1e-5
+relative L2), RK steps, conserved mass and energy, Navier-Stokes with BR1 lifting."""
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2008_04356_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sm():
+    from paper_2008_04356_gb300 import build, slidemesh
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    build.build_library()
+    slidemesh.lib()
+    return slidemesh
+
+
+def rel_max(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def dev(U, dt=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(U)).to(dt).cuda()
+
+
+def annulus(N, riemann=synth.RUSANOV, prec=synth.FP64, phi0=0.913, flow="pulse", nel=(2, 9, 3)):
+    """Uneven element counts: 2 axial layers per block, 9 angular, 3 radial."""
+    p = synth.config_annular(N=N, nel=nel, omega=0.4, phi0=phi0, flow=flow, precision=prec)
+    p.riemann = riemann
+    return p
+
+
+def check_rhs(sm, p, seed, t, tol=FP64_TOL):
+    o = O.Oracle(p)
+    U = synth.random_state(p, seed=seed)
+    ref = o.rhs(U, t)
+    s = sm.Solver(p)
+    got = s.rhs(dev(U), t).cpu().numpy()
+    assert rel_max(got, ref) < tol
+    Fs, Fm = s.interface(dev(U), t)
+    Fs_ref, Fm_ref = o.interface_fluxes(U, t)
+    assert rel_max(Fs.cpu().numpy(), Fs_ref) < tol
+    assert rel_max(Fm.cpu().numpy(), Fm_ref) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("riemann", [synth.RUSANOV, synth.ROE_HH])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+def test_annular_rhs_fp64(sm, N, riemann):
+    # phi0 + omega t beyond the sector angle: stator faces are seen through periodic wraps
+    check_rhs(sm, annulus(N, riemann), 140 + N, 0.37)
+
+
+@pytest.mark.parametrize("t", [0.0, 0.5, 3.1])
+def test_annular_rhs_across_wraps(sm, t):
+    check_rhs(sm, annulus(3, phi0=0.0, nel=(2, 8, 2)), 17, t)
+
+
+@pytest.mark.parametrize("N", [3, 7])
+def test_annular_rhs_fp32(sm, N):
+    p = annulus(N)
+    o = O.Oracle(p)
+    U = synth.random_state(p, seed=150 + N)
+    ref = o.rhs(U, 0.37)
+    p32 = copy.deepcopy(p)
+    p32.precision = synth.FP32
+    s = sm.Solver(p32)
+    got = s.rhs(dev(U, torch.float32), 0.37).cpu().numpy()
+    s.close()
+    assert rel_l2(got, ref) < FP32_TOL
+
+
+@pytest.mark.parametrize("N", [2, 5])
+def test_annular_steps(sm, N):
+    p = annulus(N, flow="pulse")
+    o = O.Oracle(p)
+    U0 = o.init_state()
+    dt = 0.5 * synth.cfl_dt(p)
+    Uo, Go = U0.copy(), np.zeros_like(U0)
+    o.step(Uo, Go, 0.0, dt, 4)
+    s = sm.Solver(p)
+    s.init_state()
+    U_init, _ = s.get_state()
+    assert rel_max(U_init.cpu().numpy(), U0) < 1e-13
+    s.step(dt, 4)
+    Ug, t = s.get_state()
+    assert abs(t - 4 * dt) < 1e-15
+    assert rel_max(Ug.cpu().numpy(), Uo) < FP64_TOL
+    # mass and energy: slip walls and the periodic sector keep them (to rounding)
+    d = s.diag()
+    t0 = o.totals(U0)
+    for v in (0, 4):
+        assert abs(d["totals"][v] - t0[v]) < 1e-12 * abs(t0[v])
+    s.close()
+    p32 = copy.deepcopy(p)
+    p32.precision = synth.FP32
+    s32 = sm.Solver(p32)
+    s32.set_state(U0.astype(np.float32), 0.0)
+    s32.step(dt, 4)
+    U32, _ = s32.get_state()
+    s32.close()
+    assert rel_l2(U32.cpu().numpy(), Uo) < FP32_TOL
+
+
+def test_annular_zero_rotation_is_conforming(sm):
+    p = annulus(3, phi0=0.0)
+    p.v = 0.0
+    U = dev(synth.random_state(p, seed=3))
+    a = sm.Solver(p).rhs(U, 0.0).cpu().numpy()
+    p.interface_conforming = 1
+    b = sm.Solver(p).rhs(U, 0.0).cpu().numpy()
+    assert rel_max(a, b) < 1e-13
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_annular_ns_fp64(sm, N):
+    p = annulus(N, riemann=synth.ROE_HH)
+    p.physics, p.mu = synth.NAVIER_STOKES, 0.01
+    check_rhs(sm, p, 160 + N, 0.21)

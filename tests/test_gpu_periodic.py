@@ -181,3 +181,46 @@ def test_periodic_rejected_where_unsupported(sm):
     with pytest.raises(sm.SlidemeshError):
         sm.Batch([s1], [1e-3])
     s1.close()
+
+
+def test_periodic_interface_heavy_full_size_sampled(sm):
+    """2 x 4 x 256 x 256 elements closed in x (2 x 65,536 interface face pairs), N = 5, FP32,
+    Rusanov: the launch configuration of the benchmark's two-interface leg; sampled elements,
+    among them both interfaces' layers, against the oracle."""
+    p = synth.config_interface_heavy(seed=1, precision=synth.FP32)
+    p.periodic_x = 1
+    E, nn = p.nelem, (p.N + 1) ** 3
+    iz_s = [0, 129, 255]
+    slabs = sorted({(iz + d) % 256 for iz in iz_s for d in (-1, 0, 1)})
+    per_slab = 4 * 256
+    Uh = torch.empty((E, 5, nn), dtype=torch.float32, pin_memory=True)
+    chunk = 16 * per_slab
+    lo = np.array([0.8, -0.3, -0.3, -0.3, 2.3])[None, :, None]
+    hi = np.array([1.2, 0.3, 0.3, 0.3, 2.7])[None, :, None]
+    for e0 in range(0, E, chunk):
+        e1 = min(E, e0 + chunk)
+        vals = synth.uniform(23, (e1 - e0) * 5 * nn, offset=e0 * 5 * nn).reshape(e1 - e0, 5, nn)
+        Uh[e0:e1] = torch.from_numpy((lo + (hi - lo) * vals).astype(np.float32))
+    sol = sm.Solver(p)
+    t = 0.0321
+    Ut = sol.rhs(Uh.cuda(), t)
+    torch.cuda.synchronize()
+    U64 = np.zeros((E, 5, nn))
+    Es = p.nelem // 2
+    for blk in (0, 1):
+        for iz in slabs:
+            a = blk * Es + iz * per_slab
+            U64[a:a + per_slab] = Uh[a:a + per_slab].numpy().astype(np.float64)
+    rng = np.random.default_rng(11)
+    elems = []
+    for blk in (0, 1):
+        for iz in iz_s:
+            for ix in (0, 3):                 # both interface layers of each block
+                for iy in rng.choice(256, 5, replace=False):
+                    elems.append(blk * Es + ix + 4 * (int(iy) + 256 * iz))
+    elems = np.array(sorted(set(elems)))
+    ref = O.Oracle(p).rhs_elements(U64, t, elems)
+    got = Ut[torch.from_numpy(elems).cuda()].cpu().numpy()
+    sol.close()
+    assert rel_l2(got, ref) < FP32_TOL
+    assert rel_max(got, ref) < 1e-4
