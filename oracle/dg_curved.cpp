@@ -12,7 +12,11 @@
  *           plane annular axial interface" geometry of the paper's overview figure): rotor
  *           z in [x0, x1] below the stator z in [x1, x2], both annular sectors with radii
  *           [z0, z1] (xi^2 runs from r = z1 to r = z0, which keeps the map (theta, r, z)
- *           right-handed); slip walls at both radii and at the axial ends.
+ *           right-handed); slip walls at both radii and at the axial ends;
+ *   geom 4: the conical interface about the rotation axis (a rotor inside the cone, the
+ *           stator outside): radius s sin(alpha) + n cos(alpha), height s cos(alpha) -
+ *           n sin(alpha) for generator coordinate s and normal offset n; slip walls at
+ *           the ends of s and n.
  *
  * Readings (the paper does not print them):
  *   - metrics: conservative curl form of Kopriva (2006), antisymmetrised,
@@ -52,6 +56,8 @@ struct Curved {
   double h1, h2, h3[2];      /* element sizes along xi^1, xi^2, xi^3 (per block) */
   bool cyl, ns;              /* cyl: a rotor turning about z (geom 1 and 3) */
   bool annular;              /* geom 3: reference axes (theta, r, z) instead of (theta, z, r) */
+  bool cone;                 /* geom 4: reference axes (theta, s, n) across a cone */
+  double sa, ca;             /* sin, cos of the cone's half-angle */
   double Theta;              /* periodic sector angle (geom 1) */
   std::vector<double> x, w, D, Dhat;
   double A[5], B[5], c[5];
@@ -191,6 +197,13 @@ void build_geometry(Curved& o) {
           double s2 = o.p.z0 + id.iz * o.h2 + (o.x[j] + 1.0) * 0.5 * o.h2;
           double s3 = lo3 + id.ix * o.h3[id.blk] + (o.x[k] + 1.0) * 0.5 * o.h3[id.blk];
           int nd = node(o, i, j, k);
+          if (o.cone) {             /* xi^1 -> theta, xi^2 -> s (generator), xi^3 -> n (across) */
+            double rr = s2 * o.sa + s3 * o.ca;
+            X[nd] = rr * std::cos(s1);
+            X[nn + nd] = rr * std::sin(s1);
+            X[2 * nn + nd] = s2 * o.ca - s3 * o.sa;
+            continue;
+          }
           if (o.annular) {          /* xi^1 -> theta, xi^2 -> -r (right-handed), xi^3 -> z */
             double rr = o.p.z0 + o.p.z1 - s2;
             X[nd] = rr * std::cos(s1);
@@ -218,6 +231,12 @@ void build_geometry(Curved& o) {
       Xc[0] = o.annular ? rc * std::cos(s1) : (o.cyl ? s3 * std::cos(s1) : s3);
       Xc[1] = o.annular ? rc * std::sin(s1) : (o.cyl ? s3 * std::sin(s1) : s1);
       Xc[2] = o.annular ? s3 : s2;
+      if (o.cone) {
+        double rk = s2 * o.sa + s3 * o.ca;
+        Xc[0] = rk * std::cos(s1);
+        Xc[1] = rk * std::sin(s1);
+        Xc[2] = s2 * o.ca - s3 * o.sa;
+      }
     }
     for (int n = 0; n < 3; ++n)
       for (int nd = 0; nd < nn; ++nd) X[n * nn + nd] -= Xc[n];
@@ -282,7 +301,7 @@ int neighbour(const Curved& o, const Id& id, int d, int side, long long* nb, dou
   }
   if (d == 1) {
     int iz = id.iz + (side ? 1 : -1);
-    if (o.annular && (iz < 0 || iz >= o.nz)) return 1;   /* slip walls at the radii */
+    if ((o.annular || o.cone) && (iz < 0 || iz >= o.nz)) return 1;   /* slip walls at the xi^2 ends */
     *nb = elem_index(o, id.blk, id.ix, id.iy, wrap(iz, o.nz));
     return 0;
   }
@@ -731,9 +750,12 @@ void* orc_curved_create(const orc_problem* p) {
   o->Es = (long long)p->nel_s[0] * o->ny * o->nz;
   o->Em = (long long)p->nel_m[0] * o->ny * o->nz;
   o->E = o->Es + o->Em;
-  if (p->geom < 1 || p->geom > 3) { delete o; return nullptr; }
-  o->cyl = p->geom == 1 || p->geom == 3;
+  if (p->geom < 1 || p->geom > 4) { delete o; return nullptr; }
+  o->cyl = p->geom == 1 || p->geom == 3 || p->geom == 4;
   o->annular = p->geom == 3;
+  o->cone = p->geom == 4;
+  o->sa = std::sin(p->cone_angle);
+  o->ca = std::cos(p->cone_angle);
   o->ns = p->physics == 1;
   o->h1 = (p->y1 - p->y0) / o->ny;
   o->h2 = (p->z1 - p->z0) / o->nz;

@@ -41,7 +41,8 @@ typedef struct {
   int geom;              /* 0 plane interface (Cartesian operator); 1 cylindrical interface
                             (curvilinear operator); 2 plane interface through the
                             curvilinear operator (general metrics); 3 plane annular interface
-                            normal to the rotation axis (curvilinear operator) */
+                            normal to the rotation axis; 4 conical interface about the axis
+                            (both curvilinear operator) */
   int volume;            /* volume integral (Sec. 3.1): 0 weak form; 1 split form with
                             Pirozzoli's two-point flux; 2 split form with the central
                             two-point flux (equal to the weak form by summation by parts).
@@ -49,8 +50,17 @@ typedef struct {
   int periodic_x;        /* 1: x periodic with period x2 - x0, so that the moving block's face
                             x = x2 meets the static block's face x = x0 in a second sliding
                             interface (several interfaces, Sec. 4.3); geom 0, Euler physics */
+  double cone_angle;     /* geom 4: half-angle alpha of the conical interface from the z axis */
 } orc_problem;
 
+/* geom 4, the conical sliding interface of Sec. 3.3 about the rotation axis: a point of
+ * reference coordinates (theta, s, n) lies at radius rho = s sin(alpha) + n cos(alpha) and
+ * height z = s cos(alpha) - n sin(alpha) (alpha = cone_angle), so s runs along the cone's
+ * generator and n across it; x0 < x1 < x2 are values of n (block 0 = rotor, n in [x0, x1],
+ * inside; block 1 = stator, n in [x1, x2]), [y0, y1] the periodic angular sector, [z0, z1]
+ * the range of s; slip walls at s = z0, z1 and n = x0, x2; reference axes xi^1 -> theta
+ * (sliding), xi^2 -> s, xi^3 -> n (J = rho h_theta h_s h_n / 8 > 0).  alpha = 0 is the
+ * cylinder's map.  Motion and flows as for geom 1. */
 /* geom 3, the plane annular interface of Sec. 3.3 normal to the rotation axis: x0 < x1 < x2
  * are axial positions (block 0 = rotor, z in [x0, x1]; block 1 = stator, z in [x1, x2]),
  * [y0, y1] the periodic angular sector, [z0, z1] the radii (z0 > 0); slip walls at both radii

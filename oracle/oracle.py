@@ -30,7 +30,7 @@ class OrcProblem(C.Structure):
                 ("riemann", C.c_int), ("interface_conforming", C.c_int), ("flow", C.c_int),
                 ("fpar", C.c_double * 16), ("modes", C.c_double * 160),
                 ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double),
-                ("geom", C.c_int), ("volume", C.c_int), ("periodic_x", C.c_int)]
+                ("geom", C.c_int), ("volume", C.c_int), ("periodic_x", C.c_int), ("cone_angle", C.c_double)]
 
 
 _LIB = None
@@ -207,6 +207,7 @@ def to_orc_problem(p) -> OrcProblem:
     s.geom = int(getattr(p, "geom", 0))
     s.volume = int(getattr(p, "volume", 0))
     s.periodic_x = int(getattr(p, "periodic_x", 0))
+    s.cone_angle = float(getattr(p, "cone_angle", 0.0))
     return s
 
 

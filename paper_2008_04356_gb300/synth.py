@@ -22,7 +22,7 @@ M2 = np.uint64(0x94D049BB133111EB)
 
 FLOW_CONSTANT, FLOW_ENTROPY_WAVE, FLOW_MODES, FLOW_POLY_X, FLOW_SHEAR_X = 0, 1, 2, 3, 4
 FLOW_AXIAL_PULSE, FLOW_RIGID_ROTATION = 5, 6
-GEOM_PLANE, GEOM_CYLINDER, GEOM_PLANE_CURVILINEAR, GEOM_ANNULAR = 0, 1, 2, 3
+GEOM_PLANE, GEOM_CYLINDER, GEOM_PLANE_CURVILINEAR, GEOM_ANNULAR, GEOM_CONE = 0, 1, 2, 3, 4
 EULER, NAVIER_STOKES = 0, 1
 RUSANOV, ROE_HH = 0, 1
 FP64, FP32 = 0, 1
@@ -88,6 +88,7 @@ class Problem:
     geom: int = GEOM_PLANE
     volume: int = VOLUME_WEAK
     periodic_x: int = 0          # 1: x periodic, a second sliding interface at x0 = x2
+    cone_angle: float = 0.0      # GEOM_CONE: half-angle of the conical interface from the z axis
 
     @property
     def np_(self) -> int:
@@ -216,6 +217,36 @@ def config_annular(N: int = 3, nel=(2, 8, 2), omega: float = 0.4, phi0: float = 
                    v=omega, delta0=phi0, flow=fl, fpar=fpar, precision=precision, geom=GEOM_ANNULAR)
 
 
+def cone_radii(p: Problem):
+    """Smallest and largest radius of a conical mesh (at the corners of its (s, n) ranges)."""
+    sa, ca = math.sin(p.cone_angle), math.cos(p.cone_angle)
+    rs = [s * sa + n * ca for s in (p.z0, p.z1) for n in (p.x0, p.x2)]
+    return min(rs), max(rs)
+
+
+def config_cone(N: int = 3, nel=(2, 8, 2), omega: float = 0.4, phi0: float = 0.0, alpha: float = math.pi / 6,
+                n=(1.0, 1.25, 1.5), s=(0.0, 0.5), sector: float = math.pi / 4, flow: str = "pulse",
+                precision: int = FP64) -> Problem:
+    """Conical sliding interface about the z axis with half-angle alpha: a point of
+    generator coordinate s and normal offset n lies at radius s sin(alpha) + n cos(alpha),
+    height s cos(alpha) - n sin(alpha); rotor n in [n0, n1] inside, stator [n1, n2]; angular
+    sector periodic, slip walls at the ends of s and n; nel = (normal per block, angular,
+    along the generator).  Flows as for config_annular."""
+    p = Problem(N=N, nel_s=(nel[0], nel[1], nel[2]), nel_m=(nel[0], nel[1], nel[2]),
+                x0=n[0], x1=n[1], x2=n[2], y0=0.0, y1=sector, z0=s[0], z1=s[1],
+                v=omega, delta0=phi0, precision=precision, geom=GEOM_CONE, cone_angle=alpha)
+    sa, ca = math.sin(alpha), math.cos(alpha)
+    if flow == "pulse":
+        sm, nm = 0.5 * (s[0] + s[1]), n[1]
+        p.flow = FLOW_AXIAL_PULSE
+        p.fpar = (1.0, 1.0, 0.0, 1.0e-2, sm * sa + nm * ca, 0.5 * sector, sm * ca - nm * sa, 0.08)
+    elif flow == "rotation":
+        p.flow, p.fpar = FLOW_RIGID_ROTATION, (1.0, 1.0, omega)
+    else:
+        p.flow, p.fpar = FLOW_CONSTANT, (1.0, 0.0, 0.0, 0.0, 1.0)
+    return p
+
+
 def config_poly_x(N: int = 3, v: float = 0.5, coeffs=(1.0, 0.1, -0.05, 0.02),
                   vel=(0.3, 0.2, -0.1), p: float = 1.0) -> Problem:
     """State polynomial in x (degree <= 3) with constant velocity and pressure."""
@@ -242,7 +273,8 @@ def wave_speed_bounds(p: Problem):
     elif p.flow == FLOW_AXIAL_PULSE:
         rho_min, pmax, vel = f[0], f[1] + abs(f[3]), [0.0, 0.0, abs(f[2])]
     elif p.flow == FLOW_RIGID_ROTATION:
-        rmax = max(abs(p.z0), abs(p.z1)) if p.geom == GEOM_ANNULAR else max(abs(p.x0), abs(p.x2))
+        rmax = (max(abs(p.z0), abs(p.z1)) if p.geom == GEOM_ANNULAR else
+                (cone_radii(p)[1] if p.geom == GEOM_CONE else max(abs(p.x0), abs(p.x2))))
         w = abs(f[2]) * rmax
         rho_min, pmax, vel = f[0], f[1] + 0.5 * f[0] * w * w, [w, w, 0.0]
     elif p.flow == FLOW_POLY_X:
@@ -260,6 +292,17 @@ def cfl_dt(p: Problem, cfl: float = 0.9) -> float:
     """dt = CFL / ((2N+1) * sum_d (|v_d - v^g_d| + c) / h_d), the largest over both blocks
     (grid velocity 0 in the static block, v along y in the moving one)."""
     vel, c = wave_speed_bounds(p)
+    if p.geom == GEOM_CONE:
+        # angular (arc length at the smallest radius), generator and normal sizes; the rotor's
+        # grid speed is at most omega rho_max
+        rmin, rmax = cone_radii(p)
+        ha = rmin * (p.y1 - p.y0) / p.nel_s[1]
+        hs = (p.z1 - p.z0) / p.nel_s[2]
+        vmax = math.sqrt(vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)
+        rate = 0.0
+        for hn, vg in (((p.x1 - p.x0) / p.nel_s[0], abs(p.v) * rmax), ((p.x2 - p.x1) / p.nel_m[0], 0.0)):
+            rate = max(rate, (vmax + c) / hn + (vmax + vg + c) / ha + (vmax + c) / hs)
+        return cfl / ((2 * p.N + 1) * rate)
     if p.geom == GEOM_ANNULAR:
         # angular (arc length at the inner radius), radial and axial sizes; the rotor's grid
         # speed is at most omega r1
