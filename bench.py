@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -48,7 +49,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=256, help="elements along z (256 = the full workload)")
-    ap.add_argument("--workload", choices=["interface-heavy", "serving", "cylinder", "annular"], default="interface-heavy")
+    ap.add_argument("--workload", choices=["interface-heavy", "serving", "cylinder", "annular", "cone"],
+                    default="interface-heavy")
     ap.add_argument("--volume", choices=["weak", "split"], default="weak",
                     help="volume integral of the interface-heavy headline: weak form, or the split form")
     ap.add_argument("--riemann", choices=["rusanov", "roe"], default=None,
@@ -359,6 +361,13 @@ ANN_WORKLOAD = ("rotating plane annular sliding interface normal to the axis, Eu
                 "rotor omega=0.4, N=7 (18.9M DOF), fluid at rest with a pressure pulse on the interface")
 
 
+CONE_WORKLOAD = ("rotating conical sliding interface about the axis, Euler: half-angle pi/6, generator s in "
+                 "[0,0.5], normal offset n in [1,1.25] (rotor, inside) and [1.25,1.5] (stator), theta in "
+                 "[0,pi/4] periodic, slip walls; rotor and stator blocks of 24x48x16 curved hexes each (36,864 "
+                 "elements, 768 sliding faces per side), rotor omega=0.4, N=7 (18.9M DOF), fluid at rest with a "
+                 "pressure pulse on the interface")
+
+
 def run_cylinder(args, rank, world, local):
     """The rotating cylindrical interface with Navier-Stokes at N = 7 (or, --workload
     annular, the plane annular interface with Euler): RK steps through the curvilinear
@@ -373,8 +382,10 @@ def run_cylinder(args, rank, world, local):
     B.build_library()
     stream = torch.cuda.current_stream()
     prec = synth.FP64 if args.precision == "fp64" else synth.FP32
-    annular = args.workload == "annular"
-    if annular:
+    annular = args.workload in ("annular", "cone")     # the Euler shapes
+    if args.workload == "cone":
+        p = synth.config_cone(N=7, nel=(24, 48, 16), omega=0.4, alpha=math.pi / 6, flow="pulse", precision=prec)
+    elif annular:
         p = synth.config_annular(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec)
     else:
         p = synth.config_cylinder(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec,
@@ -415,7 +426,8 @@ def run_cylinder(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32", "data": "synthetic",
-        "config": {"workload": ANN_WORKLOAD if annular else CYL_WORKLOAD, "elements": p.nelem, "N": p.N, "dof": p.ndof,
+        "config": {"workload": {"cone": CONE_WORKLOAD, "annular": ANN_WORKLOAD}.get(args.workload, CYL_WORKLOAD),
+                   "elements": p.nelem, "N": p.N, "dof": p.ndof,
                    "sliding_faces_per_side": p.n_faces, "riemann": "rusanov", "mu": p.mu,
                    "l2": "inputs larger than L2 (%.2f GB state + %.2f GB geometry)" % (
                        p.ndof * 5 * sb / 1e9, p.ndof * 13 * sb / 1e9),
@@ -451,7 +463,7 @@ def main():
         if rank == 0:
             run_serving(args)
         return
-    if args.workload in ("cylinder", "annular"):
+    if args.workload in ("cylinder", "annular", "cone"):
         run_cylinder(args, rank, world, local)
         return
     import numpy as np

@@ -47,7 +47,8 @@ typedef enum {
 
 enum { SM_FP64 = 0, SM_FP32 = 1 };
 enum { SM_RUSANOV = 0, SM_ROE_HH = 1 };
-enum { SM_GEOM_PLANE = 0, SM_GEOM_CYLINDER = 1, SM_GEOM_PLANE_CURVILINEAR = 2, SM_GEOM_ANNULAR = 3 };
+enum { SM_GEOM_PLANE = 0, SM_GEOM_CYLINDER = 1, SM_GEOM_PLANE_CURVILINEAR = 2, SM_GEOM_ANNULAR = 3,
+       SM_GEOM_CONE = 4 };
 enum { SM_EULER = 0, SM_NAVIER_STOKES = 1 };
 /* Volume integral of the element operator (Sec. 3.1):
  *  SM_VOLUME_WEAK   weak-form DGSEM, sum-factorised flux divergence with Dhat = -M^-1 D^T M;
@@ -98,7 +99,14 @@ enum { SM_FLOW_CONSTANT = 0, SM_FLOW_ENTROPY_WAVE = 1, SM_FLOW_MODES = 2, SM_FLO
  * stator, z in [x1, x2]), [y0, y1] is the periodic angular sector, [z0, z1] the radii
  * (z0 > 0; element index iz runs from the outer radius inwards, which keeps the map right-
  * handed); slip walls at both radii and at z = x0, x2.  Motion, flows and curved elements
- * as for the cylinder; Euler or Navier-Stokes. */
+ * as for the cylinder; Euler or Navier-Stokes.
+ *
+ * geom SM_GEOM_CONE: the conical sliding interface about the rotation axis (Sec. 3.3, the
+ * conical geometry of the overview figure): a node of angle theta, generator coordinate s in
+ * [z0, z1] and normal offset n lies at radius s sin(cone_angle) + n cos(cone_angle) and height
+ * s cos(cone_angle) - n sin(cone_angle); n in [x0, x1] is the rotor (inside the cone), n in
+ * [x1, x2] the stator; [y0, y1] is the periodic angular sector; slip walls at s = z0, z1 and
+ * n = x0, x2.  cone_angle = 0 gives the cylinder's map (with walls instead of periodic ends). */
 typedef struct {
   int N;                   /* polynomial degree, 1..7 */
   int geom;                /* SM_GEOM_PLANE */
@@ -122,6 +130,7 @@ typedef struct {
                               (several interfaces, Sec. 4.3); no Dirichlet faces remain.
                               sm_interface and sm_diag's interface sums cover the interface
                               x = x1 only.  Not for batches or sm_rhs_static. */
+  double cone_angle;       /* SM_GEOM_CONE: half-angle of the cone from the z axis, [0, pi/2) */
 } sm_mesh_desc;
 
 /* Motion of the moving block: displacement Delta(t) = delta0 + v t along +y (Sec. 4.3,

@@ -106,6 +106,7 @@ struct MeshDev {
   // angle Theta), 2 the plane box through the curvilinear kernels.
   int geom;
   double Theta;
+  double cone_s, cone_c;      // geom 4: sin, cos of the cone's half-angle
   // per-node geometry [E][13][NN] in solver precision: Ja^i_n at t = 0 (slot 3 i + n),
   // J (slot 9), and the grid-velocity factors Ja^i . v^g / |v| of the moving block
   // (slots 10..12; the grid speed is MC_VG)
@@ -166,8 +167,10 @@ struct ElemPos { int blk, ix, iy, iz; };
 
 // Geometries with a rotor turning about the z axis: 1 the cylindrical interface, 3 the plane
 // annular interface normal to the axis (reference axes xi^1 -> theta, xi^2 -> r from the outer
-// radius z1 down to z0, xi^3 -> z).
-__host__ __device__ __forceinline__ bool rotating_geom(int geom) { return geom == 1 || geom == 3; }
+// radius z1 down to z0, xi^3 -> z), 4 the conical interface (xi^1 -> theta, xi^2 -> s along
+// the generator, xi^3 -> n across: radius s sin(alpha) + n cos(alpha), height
+// s cos(alpha) - n sin(alpha)).
+__host__ __device__ __forceinline__ bool rotating_geom(int geom) { return geom == 1 || geom == 3 || geom == 4; }
 
 // Element counts stay below 2^31 (checked when a solver is created): 32-bit arithmetic.
 __host__ __device__ __forceinline__ ElemPos decode_elem(const MeshDev& m, long long e64) {
@@ -206,7 +209,7 @@ __host__ __device__ __forceinline__ int face_neighbor(const MeshDev& m, const El
   }
   if (d == 1) {
     int iz = p.iz + (side ? 1 : -1);
-    if (m.geom == 3 && (iz < 0 || iz >= m.nz)) return 1;   // annular: slip walls at the radii
+    if ((m.geom == 3 || m.geom == 4) && (iz < 0 || iz >= m.nz)) return 1;   // slip walls at the xi^2 ends
     iz = iz < 0 ? iz + m.nz : (iz >= m.nz ? iz - m.nz : iz);
     *nb = encode_elem(m, p.blk, p.ix, p.iy, iz);
     return 0;
@@ -597,14 +600,15 @@ __device__ __forceinline__ void node_position(const MeshDev& m, const ElemPos& p
     const double s3 = xlo + p.ix * hx + (xi[k] + 1.0) * 0.5 * hx;
     const double s2 = m.z0 + p.iz * m.hz + (xi[j] + 1.0) * 0.5 * m.hz;
     const double th = m.y0 + p.iy * m.hy + (xi[i] + 1.0) * 0.5 * m.hy;
-    // cylinder: r = s3, z = s2; annular: r = z0 + z1 - s2, z = s3
-    const double r = m.geom == 1 ? s3 : 2.0 * m.z0 + m.nz * m.hz - s2;
+    // cylinder: r = s3, z = s2; annular: r = z0 + z1 - s2, z = s3; cone: r = s2 sin(alpha) +
+    // s3 cos(alpha), z = s2 cos(alpha) - s3 sin(alpha)
+    const double r = m.geom == 1 ? s3 : (m.geom == 3 ? 2.0 * m.z0 + m.nz * m.hz - s2 : s2 * m.cone_s + s3 * m.cone_c);
     const double a0 = r * cos(th), a1 = r * sin(th);
     double c = 1.0, s = 0.0;
     if (p.blk == 0) sincos(-delta, &s, &c);
     X[0] = c * a0 - s * a1;
     X[1] = s * a0 + c * a1;
-    X[2] = m.geom == 1 ? s2 : s3;
+    X[2] = m.geom == 1 ? s2 : (m.geom == 3 ? s3 : s2 * m.cone_c - s3 * m.cone_s);
     return;
   }
   X[0] = xlo + p.ix * hx + (xi[k] + 1.0) * 0.5 * hx;

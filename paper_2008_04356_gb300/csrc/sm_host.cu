@@ -212,6 +212,13 @@ void curvilinear_geometry(const MeshDev& m, const BasisDev& b, int N, std::vecto
           const double s2 = m.z0 + p.iz * m.hz + (b.x[j] + 1.0) * 0.5 * m.hz;
           const double s3 = lo3 + p.ix * h3 + (b.x[k] + 1.0) * 0.5 * h3;
           const int q = idx(i, j, k);
+          if (m.geom == 4) {        // cone: (theta, s along the generator, n across)
+            const double r = s2 * m.cone_s + s3 * m.cone_c;
+            X[q] = r * cos(s1);
+            X[nn + q] = r * sin(s1);
+            X[2 * nn + q] = s2 * m.cone_c - s3 * m.cone_s;
+            continue;
+          }
           if (m.geom == 3) {        // annular: (theta, r from z1 down to z0, z), right-handed
             const double r = 2.0 * m.z0 + m.nz * m.hz - s2;
             X[q] = r * cos(s1);
@@ -237,6 +244,12 @@ void curvilinear_geometry(const MeshDev& m, const BasisDev& b, int N, std::vecto
       Xc[0] = m.geom == 3 ? rc * cos(s1) : (m.geom == 1 ? s3 * cos(s1) : s3);
       Xc[1] = m.geom == 3 ? rc * sin(s1) : (m.geom == 1 ? s3 * sin(s1) : s1);
       Xc[2] = m.geom == 3 ? s3 : s2;
+      if (m.geom == 4) {
+        const double rk = s2 * m.cone_s + s3 * m.cone_c;
+        Xc[0] = rk * cos(s1);
+        Xc[1] = rk * sin(s1);
+        Xc[2] = s2 * m.cone_c - s3 * m.cone_s;
+      }
     }
     std::vector<double> Xg(X);   // global coordinates for the grid-velocity factors
     for (int c = 0; c < 3; ++c)
@@ -539,9 +552,17 @@ int valid_desc(const sm_mesh_desc* d) {
   if (!d) return fail(SM_ERR_ARG, "desc is NULL");
   if (d->N < 1 || d->N > 7) return fail(SM_ERR_UNSUPPORTED, "N must be in 1..7");
   if (d->geom != SM_GEOM_PLANE && d->geom != SM_GEOM_CYLINDER && d->geom != SM_GEOM_PLANE_CURVILINEAR &&
-      d->geom != SM_GEOM_ANNULAR)
+      d->geom != SM_GEOM_ANNULAR && d->geom != SM_GEOM_CONE)
     return fail(SM_ERR_UNSUPPORTED, "unknown interface geometry");
-  if (d->geom == SM_GEOM_ANNULAR) {
+  if (d->geom == SM_GEOM_CONE) {
+    if (!(d->cone_angle >= 0.0 && d->cone_angle < 0.5 * M_PI)) return fail(SM_ERR_ARG, "cone half-angle in [0, pi/2)");
+    const double sa = sin(d->cone_angle), ca = cos(d->cone_angle);
+    if (!(d->z0 * sa + d->x0 * ca > 0.0 && d->z1 * sa + d->x0 * ca > 0.0))
+      return fail(SM_ERR_ARG, "the conical mesh must stay off the axis (positive radii)");
+    if (!(d->y1 - d->y0 <= 2.0 * M_PI + 1e-12)) return fail(SM_ERR_ARG, "the angular sector exceeds 2 pi");
+    if (d->flow != SM_FLOW_CONSTANT && d->flow != SM_FLOW_AXIAL_PULSE && d->flow != SM_FLOW_RIGID_ROTATION)
+      return fail(SM_ERR_ARG, "cone flows: constant, axial pulse, rigid rotation");
+  } else if (d->geom == SM_GEOM_ANNULAR) {
     if (!(d->z0 > 0.0)) return fail(SM_ERR_ARG, "annular radii must be positive");
     if (!(d->y1 - d->y0 <= 2.0 * M_PI + 1e-12)) return fail(SM_ERR_ARG, "the angular sector exceeds 2 pi");
     if (d->flow != SM_FLOW_CONSTANT && d->flow != SM_FLOW_AXIAL_PULSE && d->flow != SM_FLOW_RIGID_ROTATION)
@@ -638,6 +659,8 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   m.Rgas = desc->Rgas;
   m.geom = desc->geom;
   m.Theta = desc->y1 - desc->y0;
+  m.cone_s = sin(desc->cone_angle);
+  m.cone_c = cos(desc->cone_angle);
   for (int k = 0; k < 16; ++k) m.fpar[k] = desc->fpar[k];
   s->nstate = m.E * 5 * s->nn;
   s->nface_vals = (long long)m.ny * m.nz * 5 * s->np * s->np;

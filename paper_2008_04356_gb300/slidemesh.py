@@ -27,7 +27,7 @@ class SmMeshDesc(C.Structure):
                 ("riemann", C.c_int), ("precision", C.c_int), ("interface_conforming", C.c_int),
                 ("flow", C.c_int), ("fpar", C.c_double * 16), ("modes", C.c_double * 160),
                 ("physics", C.c_int), ("mu", C.c_double), ("Pr", C.c_double), ("Rgas", C.c_double),
-                ("volume", C.c_int), ("periodic_x", C.c_int)]
+                ("volume", C.c_int), ("periodic_x", C.c_int), ("cone_angle", C.c_double)]
 
 
 class SmMotion(C.Structure):
@@ -150,6 +150,7 @@ def mesh_desc(p: synth.Problem) -> SmMeshDesc:
     d.physics, d.mu, d.Pr, d.Rgas = int(p.physics), float(p.mu), float(p.Pr), float(p.Rgas)
     d.volume = int(getattr(p, "volume", 0))
     d.periodic_x = int(getattr(p, "periodic_x", 0))
+    d.cone_angle = float(getattr(p, "cone_angle", 0.0))
     return d
 
 
@@ -223,7 +224,7 @@ class Solver:
     def set_motion(self, v: float, delta0: float = 0.0):
         """Plane: block speed v and initial displacement; cylinder and annulus: rotor angular speed v
         and initial angle delta0."""
-        if getattr(self.problem, "geom", 0) in (synth.GEOM_CYLINDER, synth.GEOM_ANNULAR):
+        if getattr(self.problem, "geom", 0) in (synth.GEOM_CYLINDER, synth.GEOM_ANNULAR, synth.GEOM_CONE):
             mo = SmMotion(0.0, float(v), float(delta0))
         else:
             mo = SmMotion(float(v), 0.0, float(delta0))
@@ -350,7 +351,7 @@ class Server:
     def submit(self, problem: synth.Problem, dt: float, nsteps: int, keep_state: bool = False) -> int:
         req = SmRequest()
         req.desc = mesh_desc(problem)
-        if getattr(problem, "geom", 0) in (synth.GEOM_CYLINDER, synth.GEOM_ANNULAR):
+        if getattr(problem, "geom", 0) in (synth.GEOM_CYLINDER, synth.GEOM_ANNULAR, synth.GEOM_CONE):
             req.motion = SmMotion(0.0, float(problem.v), float(problem.delta0))
         else:
             req.motion = SmMotion(float(problem.v), 0.0, float(problem.delta0))

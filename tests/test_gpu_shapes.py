@@ -1,7 +1,8 @@
-"""The plane annular sliding interface normal to the rotation axis (rotor below the stator,
-slip walls at the radii and the axial ends, periodic sector) on the GPU against the
-curvilinear oracle: right-hand side and interface fluxes (FP64 to 1e-12, FP32 to 1e-5
-relative L2), RK steps, conserved mass and energy, Navier-Stokes with BR1 lifting."""
+"""The other rotating interface shapes on the GPU against the curvilinear oracle: the plane
+annular interface normal to the rotation axis (rotor below the stator) and the conical
+interface (rotor inside the cone), both with slip walls and a periodic sector: right-hand
+side and interface fluxes (FP64 to 1e-12, FP32 to 1e-5 relative L2), RK steps, conserved
+mass and energy, Navier-Stokes with BR1 lifting."""
 import copy
 
 import numpy as np
@@ -47,6 +48,16 @@ def annulus(N, riemann=synth.RUSANOV, prec=synth.FP64, phi0=0.913, flow="pulse",
     return p
 
 
+def cone(N, riemann=synth.RUSANOV, prec=synth.FP64, phi0=0.913, flow="pulse", nel=(2, 9, 3)):
+    """Half-angle 0.6 rad; 2 normal layers per block, 9 angular, 3 along the generator."""
+    p = synth.config_cone(N=N, nel=nel, omega=0.4, phi0=phi0, alpha=0.6, flow=flow, precision=prec)
+    p.riemann = riemann
+    return p
+
+
+SHAPES = {"annular": annulus, "cone": cone}
+
+
 def check_rhs(sm, p, seed, t, tol=FP64_TOL):
     o = O.Oracle(p)
     U = synth.random_state(p, seed=seed)
@@ -61,21 +72,24 @@ def check_rhs(sm, p, seed, t, tol=FP64_TOL):
     s.close()
 
 
+@pytest.mark.parametrize("shape", ["annular", "cone"])
 @pytest.mark.parametrize("riemann", [synth.RUSANOV, synth.ROE_HH])
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
-def test_annular_rhs_fp64(sm, N, riemann):
+def test_shape_rhs_fp64(sm, N, riemann, shape):
     # phi0 + omega t beyond the sector angle: stator faces are seen through periodic wraps
-    check_rhs(sm, annulus(N, riemann), 140 + N, 0.37)
+    check_rhs(sm, SHAPES[shape](N, riemann), 140 + N, 0.37)
 
 
+@pytest.mark.parametrize("shape", ["annular", "cone"])
 @pytest.mark.parametrize("t", [0.0, 0.5, 3.1])
-def test_annular_rhs_across_wraps(sm, t):
-    check_rhs(sm, annulus(3, phi0=0.0, nel=(2, 8, 2)), 17, t)
+def test_shape_rhs_across_wraps(sm, t, shape):
+    check_rhs(sm, SHAPES[shape](3, phi0=0.0, nel=(2, 8, 2)), 17, t)
 
 
+@pytest.mark.parametrize("shape", ["annular", "cone"])
 @pytest.mark.parametrize("N", [3, 7])
-def test_annular_rhs_fp32(sm, N):
-    p = annulus(N)
+def test_shape_rhs_fp32(sm, N, shape):
+    p = SHAPES[shape](N)
     o = O.Oracle(p)
     U = synth.random_state(p, seed=150 + N)
     ref = o.rhs(U, 0.37)
@@ -87,9 +101,10 @@ def test_annular_rhs_fp32(sm, N):
     assert rel_l2(got, ref) < FP32_TOL
 
 
+@pytest.mark.parametrize("shape", ["annular", "cone"])
 @pytest.mark.parametrize("N", [2, 5])
-def test_annular_steps(sm, N):
-    p = annulus(N, flow="pulse")
+def test_shape_steps(sm, N, shape):
+    p = SHAPES[shape](N, flow="pulse")
     o = O.Oracle(p)
     U0 = o.init_state()
     dt = 0.5 * synth.cfl_dt(p)
@@ -119,8 +134,9 @@ def test_annular_steps(sm, N):
     assert rel_l2(U32.cpu().numpy(), Uo) < FP32_TOL
 
 
-def test_annular_zero_rotation_is_conforming(sm):
-    p = annulus(3, phi0=0.0)
+@pytest.mark.parametrize("shape", ["annular", "cone"])
+def test_shape_zero_rotation_is_conforming(sm, shape):
+    p = SHAPES[shape](3, phi0=0.0)
     p.v = 0.0
     U = dev(synth.random_state(p, seed=3))
     a = sm.Solver(p).rhs(U, 0.0).cpu().numpy()
@@ -129,8 +145,9 @@ def test_annular_zero_rotation_is_conforming(sm):
     assert rel_max(a, b) < 1e-13
 
 
+@pytest.mark.parametrize("shape", ["annular", "cone"])
 @pytest.mark.parametrize("N", [2, 4])
-def test_annular_ns_fp64(sm, N):
-    p = annulus(N, riemann=synth.ROE_HH)
+def test_shape_ns_fp64(sm, N, shape):
+    p = SHAPES[shape](N, riemann=synth.ROE_HH)
     p.physics, p.mu = synth.NAVIER_STOKES, 0.01
     check_rhs(sm, p, 160 + N, 0.21)
