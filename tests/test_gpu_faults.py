@@ -5,7 +5,8 @@
   exactly the state they reach alone;
 * malformed requests (degree outside 1..7, non-positive time step, a request that can never
   fit the memory budget) are refused at submission with their status, and the server keeps
-  serving.
+  serving;
+* checkpoint and resume (state and time through the C-ABI) continue a solve bit for bit.
 """
 import copy
 
@@ -83,3 +84,31 @@ def test_malformed_requests_are_refused_and_serving_continues(sm):
     r = srv.poll(t)
     srv.close()
     assert r["status"] == 0
+
+
+@pytest.mark.parametrize("prec", [synth.FP64, synth.FP32])
+def test_checkpoint_resume_is_bit_exact(sm, prec):
+    """A solve checkpointed with sm_get_state after 3 steps and resumed in a new solver with
+    sm_set_state (state and time; the RK register restarts every step) continues bit for bit
+    like the uninterrupted solve."""
+    p = synth.config_box(N=3, v=0.43, precision=prec)
+    p.delta0 = 0.21
+    dt = synth.cfl_dt(p)
+    a = sm.Solver(p)
+    a.init_state()
+    a.step(dt, 7)
+    ua, ta = a.get_state()
+    b = sm.Solver(p)
+    b.init_state()
+    b.step(dt, 3)
+    ub, tb = b.get_state()
+    ck = (ub.cpu().clone(), tb)
+    b.close()
+    c = sm.Solver(p)
+    c.set_state(ck[0].numpy(), ck[1])
+    c.step(dt, 4)
+    uc, tc = c.get_state()
+    assert tc == ta
+    assert torch.equal(uc.cpu(), ua.cpu())
+    a.close()
+    c.close()
