@@ -611,8 +611,92 @@ void face_flux(const Curved& o, const double* U, const double* grad, double t, l
     }
 }
 
+/* Contravariant two-point volume flux of the split form (Sec. 3.1) along one reference
+ * direction, between nodes a and b with metric vectors Ja_a, Ja_b (Ja^d at each node) and
+ * normal grid speeds V_a = Ja_a . v^g, V_b (reading, the curvilinear form of Pirozzoli's
+ * products): kind 0 the products of means of Pirozzoli's flux with the averaged metric
+ * m = {{Ja}} in place of the unit normal and the averaged V in place of the normal grid
+ * speed; kind 1 the central flux {{Ja . F(U) - V U}}.  For equal nodes both reduce to the
+ * contravariant ALE flux Ja . F(U) - V U. */
+void curved_two_point(int kind, const double* Ua, const double* Ub, const double* Jaa, const double* Jab,
+                      double Va, double Vb, double gamma, double* F) {
+  if (kind == 1) {
+    double Fa[5], Fb[5];
+    orc_euler_flux(Ua, Jaa, Va, gamma, Fa);
+    orc_euler_flux(Ub, Jab, Vb, gamma, Fb);
+    for (int v = 0; v < 5; ++v) F[v] = 0.5 * (Fa[v] + Fb[v]);
+    return;
+  }
+  double m[3] = {0.5 * (Jaa[0] + Jab[0]), 0.5 * (Jaa[1] + Jab[1]), 0.5 * (Jaa[2] + Jab[2])};
+  orc_two_point_flux(0, Ua, Ub, m, 0.5 * (Va + Vb), gamma, F);
+}
+
+/* Split-form residual of a curved element (Sec. 3.1, the split formulation with Pirozzoli's
+ * flux), strong form:
+ *   J dU/dt = - sum_d sum_l 2 D_il F~#^d(U_node, U_l)  - sum_faces ell(+-1)/w (F* . N sJ - F~^d(U_node)) ,
+ * F~^d(U) = Ja^d . F(U) - (Ja^d . v^g) U the node's own contravariant flux. */
+void split_residual(const Curved& o, const double* U, double t, long long e, const std::vector<double>* Fs,
+                    const std::vector<double>* Fm, double* Ut) {
+  int np = o.np, nn = o.nn, nq = np * np;
+  int kind = o.p.volume == 2 ? 1 : 0;
+  std::vector<double> Ja(9 * nn), V(3 * nn);       /* Ja[(d*3 + c)*nn + nd], V[d*nn + nd] */
+  for (int nd = 0; nd < nn; ++nd) {
+    double vg[3];
+    node_vg(o, e, nd, t, vg);
+    for (int d = 0; d < 3; ++d) {
+      double a[3];
+      node_Ja(o, e, d, nd, t, a);
+      for (int c = 0; c < 3; ++c) Ja[(d * 3 + c) * nn + nd] = a[c];
+      V[d * nn + nd] = a[0] * vg[0] + a[1] * vg[1] + a[2] * vg[2];
+    }
+  }
+  auto ja = [&](int d, int nd, double* out) { for (int c = 0; c < 3; ++c) out[c] = Ja[(d * 3 + c) * nn + nd]; };
+  for (int k = 0; k < np; ++k)
+    for (int j = 0; j < np; ++j)
+      for (int i = 0; i < np; ++i) {
+        int nd = node(o, i, j, k);
+        double u[5], ul[5], f[5], acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * nn + nd];
+        for (int d = 0; d < 3; ++d) {
+          int row = d == 0 ? i : (d == 1 ? j : k);
+          double Jn[3];
+          ja(d, nd, Jn);
+          for (int l = 0; l < np; ++l) {
+            int nl = d == 0 ? node(o, l, j, k) : (d == 1 ? node(o, i, l, k) : node(o, i, j, l));
+            double Jl[3];
+            ja(d, nl, Jl);
+            for (int v = 0; v < 5; ++v) ul[v] = U[(e * 5 + v) * nn + nl];
+            curved_two_point(kind, u, ul, Jn, Jl, V[d * nn + nd], V[d * nn + nl], o.p.gamma, f);
+            for (int v = 0; v < 5; ++v) acc[v] += 2.0 * o.D[row * np + l] * f[v];
+          }
+        }
+        for (int v = 0; v < 5; ++v) Ut[v * nn + nd] = -acc[v];
+      }
+  std::vector<double> Fout(5 * nq);
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side) {
+      face_flux(o, U, nullptr, t, e, d, side, Fs, Fm, Fout.data());
+      double wend = o.w[side ? o.N : 0], sg = side ? 1.0 : -1.0;
+      for (int b = 0; b < np; ++b)
+        for (int a = 0; a < np; ++a) {
+          int nd = face_node(o, d, side, a, b);
+          double u[5], Jn[3], f[5];
+          for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * nn + nd];
+          ja(d, nd, Jn);
+          orc_euler_flux(u, Jn, V[d * nn + nd], o.p.gamma, f);
+          for (int v = 0; v < 5; ++v) Ut[v * nn + nd] -= (Fout[v * nq + a + np * b] - sg * f[v]) / wend;
+        }
+    }
+  for (int v = 0; v < 5; ++v)
+    for (int nd = 0; nd < nn; ++nd) Ut[v * nn + nd] /= o.J0[e * nn + nd];
+}
+
 void residual(const Curved& o, const double* U, const double* grad, double t, long long e,
               const std::vector<double>* Fs, const std::vector<double>* Fm, double* Ut) {
+  if (o.p.volume != 0) {
+    split_residual(o, U, t, e, Fs, Fm, Ut);
+    return;
+  }
   int np = o.np, nn = o.nn, nq = np * np;
   std::vector<double> Ft(15 * nn);
   for (int nd = 0; nd < nn; ++nd) {

@@ -1154,7 +1154,8 @@ extern "C" {
 static bool curved(void* h) { return *(int*)h == 1; }
 
 void* orc_create(const orc_problem* p) {
-  if (p->geom != 0) return (p->volume != 0 || p->periodic_x) ? nullptr : orc_curved_create(p);
+  if (p->volume < 0 || p->volume > 2 || (p->volume != 0 && p->physics != 0)) return nullptr;
+  if (p->geom != 0) return p->periodic_x ? nullptr : orc_curved_create(p);
   if (p->N < 1 || p->N > 15) return nullptr;
   if (p->nel_s[1] != p->nel_m[1] || p->nel_s[2] != p->nel_m[2]) return nullptr;
   if (p->volume < 0 || p->volume > 2 || (p->volume != 0 && p->physics != 0)) return nullptr;

@@ -46,7 +46,8 @@ typedef struct {
   int volume;            /* volume integral (Sec. 3.1): 0 weak form; 1 split form with
                             Pirozzoli's two-point flux; 2 split form with the central
                             two-point flux (equal to the weak form by summation by parts).
-                            The split forms take geom 0 and Euler physics. */
+                            The split forms take Euler physics; on curved geometries the
+                            two-point flux uses the averaged metric terms of its two nodes. */
   int periodic_x;        /* 1: x periodic with period x2 - x0, so that the moving block's face
                             x = x2 meets the static block's face x = x0 in a second sliding
                             interface (several interfaces, Sec. 4.3); geom 0, Euler physics */
