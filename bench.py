@@ -387,6 +387,10 @@ def run_cylinder(args, rank, world, local):
         p = synth.config_cone(N=7, nel=(24, 48, 16), omega=0.4, alpha=math.pi / 6, flow="pulse", precision=prec)
     elif annular:
         p = synth.config_annular(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec)
+    split = annular and args.volume == "split"
+    if split:                      # the split form on the Euler shapes, Roe/HH unless asked otherwise
+        p.volume = synth.VOLUME_SPLIT
+        p.riemann = synth.RUSANOV if args.riemann == "rusanov" else synth.ROE_HH
     else:
         p = synth.config_cylinder(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec,
                                   physics=synth.NAVIER_STOKES)
@@ -428,14 +432,17 @@ def run_cylinder(args, rank, world, local):
         "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32", "data": "synthetic",
         "config": {"workload": {"cone": CONE_WORKLOAD, "annular": ANN_WORKLOAD}.get(args.workload, CYL_WORKLOAD),
                    "elements": p.nelem, "N": p.N, "dof": p.ndof,
-                   "sliding_faces_per_side": p.n_faces, "riemann": "rusanov", "mu": p.mu,
+                   "sliding_faces_per_side": p.n_faces, "riemann": "roe_hh" if p.riemann == synth.ROE_HH else "rusanov",
+                   "volume": "split form, Pirozzoli two-point flux" if split else "weak form", "mu": p.mu,
                    "l2": "inputs larger than L2 (%.2f GB state + %.2f GB geometry)" % (
                        p.ndof * 5 * sb / 1e9, p.ndof * 13 * sb / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU", "dt": dt, "final_t": d["t"]},
         "interface_face_updates_per_s": rep.value(p.n_faces * 5 * args.steps, ms * 1e-3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "curved_element_kernel<N=7, %s, Rusanov, stage%s>" % (
-                         "double" if prec == synth.FP64 else "float", "" if annular else ", NS"),
+                     "traffic": None, "kernel": "%s<N=7, %s, %s, stage%s>" % (
+                         "curved_split_kernel" if split else "curved_element_kernel",
+                         "double" if prec == synth.FP64 else "float",
+                         "Roe/HH" if p.riemann == synth.ROE_HH else "Rusanov", "" if annular else ", NS"),
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": elem_bytes, "avg_launch_ms": elem_ms},
         "kernels": {"stage_params": {"launches": kcnt[0], "ms": kms[0]},
                     "lifting_and_interface": {"launches": kcnt[1], "ms": kms[1], "avg_ms": kms[1] / max(kcnt[1], 1)},

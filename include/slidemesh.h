@@ -57,8 +57,9 @@ enum { SM_EULER = 0, SM_NAVIER_STOKES = 1 };
  *                   term sum_l (2 D - M^-1 B)_il F#(U_i, U_l) per direction with
  *                   F#_rho = {{rho}}{{w}}, F#_rho v = F#_rho {{v}} + {{p}} n,
  *                   F#_rho e = F#_rho {{H}} + {{p}} v^g.n, {{a}} the arithmetic mean,
- *                   w = v.n - v^g.n the velocity relative to the grid, H the total enthalpy.
- *                   Plane geometry (SM_GEOM_PLANE) and Euler physics only. */
+ *                   w = v.n - v^g.n the velocity relative to the grid, H the total enthalpy;
+ *                   on curved elements n and v^g.n are the means of the two nodes' metric
+ *                   vectors Ja^d and of Ja^d.v^g.  Euler physics, every geometry. */
 enum { SM_VOLUME_WEAK = 0, SM_VOLUME_SPLIT = 1 };
 /* Flows used as initial data (sm_init_state) and as the weak Dirichlet state at x = x0, x2
  * (SM_FLOW_SHEAR_X: rho = fpar0, p = fpar1, velocity (0, 0, fpar2 + fpar3 x + fpar4 x^2)):

@@ -44,79 +44,20 @@ __device__ __forceinline__ void viscous_dot_n(const T U[5], const T g[15], const
   for (int v = 0; v < 5; ++v) out[v] = N[0] * f0[v] + N[1] * f1[v] + N[2] * f2[v];
 }
 
-// One CTA: elements e0 .. e0+EPB-1 (same work split and shared-memory layouts as the
-// Cartesian element kernel).  PHYS 1 adds the viscous fluxes of the lifted gradients Gr
-// ([E][15][NN] in the global frame, turned into the element's frame on load).
-template <int N, typename T, int RIEM, int MODE, int PHYS>
-__device__ __forceinline__ void curved_element_block(const MeshDev& m, const StageParams* __restrict__ sp,
-                                                     const T* __restrict__ U, T* __restrict__ out,
-                                                     T* __restrict__ G, const T* __restrict__ Fs,
-                                                     const T* __restrict__ Fm, const T rkA, const T rkB,
-                                                     const T dt, const long long e0, const T* __restrict__ Gr) {
+// Face fluxes of the CTA's EPB curved elements (elements e0 ..), one work item per (element,
+// face, face node), in each element's frame, into sS[EPB][6][5][NP^2] as outward fluxes times
+// the surface element.  Reads global memory only.
+template <int N, typename T, int RIEM, int PHYS>
+__device__ __forceinline__ void curved_face_fluxes(const MeshDev& m, const StageParams* __restrict__ sp,
+                                                   const T* __restrict__ U, const T* __restrict__ Fs,
+                                                   const T* __restrict__ Fm, const T* __restrict__ Gr,
+                                                   const long long e0, T* sS, const int tid) {
   using C = ElemCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sF = reinterpret_cast<T*>(smem_raw);        // [EPB][3][5][NN], node order
-  T* sS = sF + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
   const T* c = Prec<T>::c(m);
   const T* geo = reinterpret_cast<const T*>(m.geo);
-  const int tid = threadIdx.x;
-  const int le = tid / NN, nd = tid - le * NN;
-  const long long e = e0 + le;
-  const bool active = e < m.E;
-  const long long base = e * 5 * NN + nd;
   const T gamma = c[MC_GAMMA];
   const T vspeed = c[MC_VG];
-  const int blk = active && e >= m.Es;
-  T fc, fs;
-  block_frame<T>(m, sp, blk, fc, fs);
-
-  T u[5], g[5];
-  if (active) {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) u[v] = U[base + v * NN];
-    if (MODE == ELEM_STAGE) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) g[v] = G[base + v * NN];
-    }
-    T ub[5] = {u[0], u[1], u[2], u[3], u[4]};
-    rotate_state_z(ub, fc, -fs);
-    const Prim<T> q = primitives(ub, gamma);
-    T F[3][5];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      F[a][0] = ub[0] * q.u[a];
-      F[a][1] = ub[1] * q.u[a] + (a == 0 ? q.p : T(0));
-      F[a][2] = ub[2] * q.u[a] + (a == 1 ? q.p : T(0));
-      F[a][3] = ub[3] * q.u[a] + (a == 2 ? q.p : T(0));
-      F[a][4] = (ub[4] + q.p) * q.u[a];
-    }
-    if (PHYS) {
-      T gn[15], fv[5];
-#pragma unroll
-      for (int kk = 0; kk < 15; ++kk) gn[kk] = Gr[(e * 15 + kk) * NN + nd];
-      rotate_grad_z(gn, fc, -fs);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        viscous_flux_axis(ub, gn, a, c, fv);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) F[a][v] -= fv[v];
-      }
-    }
-    const T* ge = geo + e * 13 * NN + nd;
-    const T vs = moving_block(m, blk) ? vspeed : T(0);
-    const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
-    T* Fe = sF + le * 15 * NN;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const T J0 = ge[(3 * d) * NN], J1 = ge[(3 * d + 1) * NN], J2 = ge[(3 * d + 2) * NN];
-      const T V = vs * ge[(10 + d) * NN];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Fe[(5 * d + v) * NN + nd] = J0 * F[0][v] + J1 * F[1][v] + J2 * F[2][v] - V * ub[v];
-    }
-  }
-
-  // ---- face fluxes: one work item per (element, face, face node), in the element's frame ----
   for (int w = tid; w < EPB * 6 * NP2; w += THREADS) {
     const int l2 = w / (6 * NP2);
     const int r = w - l2 * 6 * NP2;
@@ -231,19 +172,22 @@ __device__ __forceinline__ void curved_element_block(const MeshDev& m, const Sta
     for (int v = 0; v < 5; ++v) sS[((l2 * 6 + fc2) * 5 + v) * NP2 + ab] = Fo[v];
   }
 
-  __syncthreads();
-  contract_lines_inplace<N, T>(sF, tid);
-  __syncthreads();
-  if (!active) return;
+}
+
+// Surface integral, 1/J, the turn back to the global frame (rotor) and the RK update of node
+// nd of curved element e, given the node's volume term acc (in the element's frame).
+template <int N, typename T, int MODE>
+__device__ __forceinline__ void curved_surface_update(const MeshDev& m, const T* Se, T (&acc)[5], const int nd,
+                                                      const long long e, const long long base, const T (&u)[5],
+                                                      const T (&g)[5], const T fc, const T fs,
+                                                      T* __restrict__ out, T* __restrict__ G, const T rkA,
+                                                      const T rkB, const T dt) {
+  using C = ElemCfg<N>;
+  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN;
+  const T* c = Prec<T>::c(m);
+  const T* geo = reinterpret_cast<const T*>(m.geo);
   const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
-  T acc[5];
-  {
-    const T* Fe = sF + le * 15 * NN + nd;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = Fe[v * NN] + Fe[(5 + v) * NN] + Fe[(10 + v) * NN];
-  }
   const T iw0 = c[MC_IW0];
-  const T* Se = sS + le * 30 * NP2;
   if (i == 0 || i == N) {
     const T* s = Se + (i == 0 ? 0 : 1) * 5 * NP2 + j + NP * k;
 #pragma unroll
@@ -275,6 +219,92 @@ __device__ __forceinline__ void curved_element_block(const MeshDev& m, const Sta
       out[base + v * NN] = u[v] + rkB * gn;
     }
   }
+}
+
+// One CTA: elements e0 .. e0+EPB-1 (same work split and shared-memory layouts as the
+// Cartesian element kernel).  PHYS 1 adds the viscous fluxes of the lifted gradients Gr
+// ([E][15][NN] in the global frame, turned into the element's frame on load).
+template <int N, typename T, int RIEM, int MODE, int PHYS>
+__device__ __forceinline__ void curved_element_block(const MeshDev& m, const StageParams* __restrict__ sp,
+                                                     const T* __restrict__ U, T* __restrict__ out,
+                                                     T* __restrict__ G, const T* __restrict__ Fs,
+                                                     const T* __restrict__ Fm, const T rkA, const T rkB,
+                                                     const T dt, const long long e0, const T* __restrict__ Gr) {
+  using C = ElemCfg<N>;
+  constexpr int NP2 = C::NP2, NN = C::NN, EPB = C::EPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sF = reinterpret_cast<T*>(smem_raw);        // [EPB][3][5][NN], node order
+  T* sS = sF + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
+  const T* c = Prec<T>::c(m);
+  const T* geo = reinterpret_cast<const T*>(m.geo);
+  const int tid = threadIdx.x;
+  const int le = tid / NN, nd = tid - le * NN;
+  const long long e = e0 + le;
+  const bool active = e < m.E;
+  const long long base = e * 5 * NN + nd;
+  const T gamma = c[MC_GAMMA];
+  const T vspeed = c[MC_VG];
+  const int blk = active && e >= m.Es;
+  T fc, fs;
+  block_frame<T>(m, sp, blk, fc, fs);
+
+  T u[5], g[5];
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = U[base + v * NN];
+    if (MODE == ELEM_STAGE) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) g[v] = G[base + v * NN];
+    }
+    T ub[5] = {u[0], u[1], u[2], u[3], u[4]};
+    rotate_state_z(ub, fc, -fs);
+    const Prim<T> q = primitives(ub, gamma);
+    T F[3][5];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      F[a][0] = ub[0] * q.u[a];
+      F[a][1] = ub[1] * q.u[a] + (a == 0 ? q.p : T(0));
+      F[a][2] = ub[2] * q.u[a] + (a == 1 ? q.p : T(0));
+      F[a][3] = ub[3] * q.u[a] + (a == 2 ? q.p : T(0));
+      F[a][4] = (ub[4] + q.p) * q.u[a];
+    }
+    if (PHYS) {
+      T gn[15], fv[5];
+#pragma unroll
+      for (int kk = 0; kk < 15; ++kk) gn[kk] = Gr[(e * 15 + kk) * NN + nd];
+      rotate_grad_z(gn, fc, -fs);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        viscous_flux_axis(ub, gn, a, c, fv);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[a][v] -= fv[v];
+      }
+    }
+    const T* ge = geo + e * 13 * NN + nd;
+    const T vs = moving_block(m, blk) ? vspeed : T(0);
+    T* Fe = sF + le * 15 * NN;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T J0 = ge[(3 * d) * NN], J1 = ge[(3 * d + 1) * NN], J2 = ge[(3 * d + 2) * NN];
+      const T V = vs * ge[(10 + d) * NN];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fe[(5 * d + v) * NN + nd] = J0 * F[0][v] + J1 * F[1][v] + J2 * F[2][v] - V * ub[v];
+    }
+  }
+
+  curved_face_fluxes<N, T, RIEM, PHYS>(m, sp, U, Fs, Fm, Gr, e0, sS, tid);
+
+  __syncthreads();
+  contract_lines_inplace<N, T>(sF, tid);
+  __syncthreads();
+  if (!active) return;
+  T acc[5];
+  {
+    const T* Fe = sF + le * 15 * NN + nd;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] = Fe[v * NN] + Fe[(5 + v) * NN] + Fe[(10 + v) * NN];
+  }
+  curved_surface_update<N, T, MODE>(m, sS + le * 30 * NP2, acc, nd, e, base, u, g, fc, fs, out, G, rkA, rkB, dt);
 }
 
 // Curved sliding interface, one CTA per tile of TF static faces of line iz (Sec. 3.3,

@@ -482,6 +482,9 @@ cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a0, cudaStream_t
     return s->prec == SM_FP64 ? launch_curved_element_ns_f64(s->N, s->desc.riemann, mode, a, st)
                               : launch_curved_element_ns_f32(s->N, s->desc.riemann, mode, a, st);
   }
+  if (s->m.geom != 0 && s->desc.volume == SM_VOLUME_SPLIT)
+    return s->prec == SM_FP64 ? launch_curved_split_f64(s->N, s->desc.riemann, mode, a, st)
+                              : launch_curved_split_f32(s->N, s->desc.riemann, mode, a, st);
   if (s->m.geom != 0)
     return s->prec == SM_FP64 ? launch_curved_element_f64(s->N, s->desc.riemann, mode, a, st)
                               : launch_curved_element_f32(s->N, s->desc.riemann, mode, a, st);
@@ -588,8 +591,8 @@ int valid_desc(const sm_mesh_desc* d) {
   if (d->physics == SM_NAVIER_STOKES && !(d->mu >= 0.0 && d->Pr > 0.0 && d->Rgas > 0.0))
     return fail(SM_ERR_ARG, "Navier-Stokes needs mu >= 0, Pr > 0, Rgas > 0");
   if (d->volume != SM_VOLUME_WEAK && d->volume != SM_VOLUME_SPLIT) return fail(SM_ERR_ARG, "unknown volume integral");
-  if (d->volume == SM_VOLUME_SPLIT && (d->geom != SM_GEOM_PLANE || d->physics != SM_EULER))
-    return fail(SM_ERR_UNSUPPORTED, "the split-form volume integral takes the plane interface and Euler physics");
+  if (d->volume == SM_VOLUME_SPLIT && d->physics != SM_EULER)
+    return fail(SM_ERR_UNSUPPORTED, "the split-form volume integral takes Euler physics");
   if (d->periodic_x != 0 && d->periodic_x != 1) return fail(SM_ERR_ARG, "periodic_x must be 0 or 1");
   if (d->periodic_x && (d->geom != SM_GEOM_PLANE || d->physics != SM_EULER))
     return fail(SM_ERR_UNSUPPORTED, "the second sliding interface (periodic x) takes the plane geometry and Euler physics");
@@ -756,6 +759,9 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   else if (desc->geom != SM_GEOM_PLANE &&
            (e = (s->prec == SM_FP64 ? prepare_curved_f64(s->N) : prepare_curved_f32(s->N))) != cudaSuccess)
     what = "curvilinear kernel attributes";
+  else if (desc->geom != SM_GEOM_PLANE && desc->volume == SM_VOLUME_SPLIT &&
+           (e = (s->prec == SM_FP64 ? prepare_curved_split_f64(s->N) : prepare_curved_split_f32(s->N))) != cudaSuccess)
+    what = "curvilinear split-form kernel attributes";
   else if (desc->geom != SM_GEOM_PLANE && desc->physics == SM_NAVIER_STOKES &&
            (e = (s->prec == SM_FP64 ? prepare_curved_ns_f64(s->N) : prepare_curved_ns_f32(s->N))) != cudaSuccess)
     what = "curvilinear Navier-Stokes kernel attributes";

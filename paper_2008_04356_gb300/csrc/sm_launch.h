@@ -35,6 +35,12 @@ cudaError_t launch_curved_interface_f32(int N, int riemann, const MeshDev& m, co
 cudaError_t launch_curved_interface_f64(int N, int riemann, const MeshDev& m, const StageParams* sp, const void* U,
                                         void* Fs, void* Fm, cudaStream_t st);
 cudaError_t prepare_curved_f32(int N);
+// sm_curved_split_f32.cu / sm_curved_split_f64.cu: the split-form volume integral on curved
+// elements (Euler), same faces, surface integral and RK update as the curved element kernel
+cudaError_t launch_curved_split_f32(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t launch_curved_split_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t prepare_curved_split_f32(int N);
+cudaError_t prepare_curved_split_f64(int N);
 cudaError_t prepare_curved_f64(int N);
 cudaError_t upload_dhat_curved_f32(const float* f, const double* d);
 cudaError_t upload_dhat_curved_f64(const float* f, const double* d);

@@ -158,15 +158,11 @@ def test_split_free_stream_preserved_gpu(sm, N):
         assert (U1 - U0).abs().max().item() < tol, (N, prec)
 
 
-def test_split_rejects_unsupported_configurations(sm):
-    for geom_or_phys in ("cylinder", "ns"):
-        if geom_or_phys == "cylinder":
-            p = synth.config_cylinder(N=3)
-        else:
-            p = synth.config_shear_x(N=3)
-        p.volume = synth.VOLUME_SPLIT
-        with pytest.raises(sm.SlidemeshError):
-            sm.Solver(p)
+def test_split_rejects_navier_stokes(sm):
+    p = synth.config_shear_x(N=3)
+    p.volume = synth.VOLUME_SPLIT
+    with pytest.raises(sm.SlidemeshError):
+        sm.Solver(p)
 
 
 def test_split_interface_heavy_full_size_sampled(sm):
