@@ -155,7 +155,7 @@ ELEMENT_SOURCES = ["paper_2008_04356_gb300/csrc/sm_element.cuh", "paper_2008_043
 # FP64 operations the plain FP64 path executes per DOF-update (N = 5, Rusanov), averaged over
 # the five stages of a step: DFMA x 2 + DADD + DMUL counted with ncu on the element kernel
 # (426.3 per DOF in a stage, 416.3 in the first stage, which reads no RK register), plus the
-# interface kernel's share (16.1 per DOF; profiles/dg_element_N5_fp64_flops.md)
+# interface kernel's share (16.1 per DOF), counted on 2 x 4 x 256 x 8 hexes
 FP64_FLOP_PER_DOF = (4 * 426.25 + 416.25) / 5 + 16.07
 # FP64 peak of one GB300: 152 SMs x 2 DFMA per clock x 2 flop x 2.07 GHz (the nominal
 # 1.25 TFLOP/s; a dependent-chain DFMA probe measured 1.0 TFLOP/s at about 1990 MHz)
