@@ -368,10 +368,33 @@ CONE_WORKLOAD = ("rotating conical sliding interface about the axis, Euler: half
                  "pressure pulse on the interface")
 
 
+def shape_problem(workload: str, volume: str, riemann, prec: int):
+    """The curved-element workload at full size: the cylinder with Navier-Stokes (weak form
+    only), or the annulus or the cone with Euler, weak or split form (the split form with
+    Roe/HH unless Rusanov is asked for)."""
+    from paper_2008_04356_gb300 import synth
+    if workload == "cone":
+        p = synth.config_cone(N=7, nel=(24, 48, 16), omega=0.4, alpha=math.pi / 6, flow="pulse", precision=prec)
+    elif workload == "annular":
+        p = synth.config_annular(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec)
+    elif workload == "cylinder":
+        p = synth.config_cylinder(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec,
+                                  physics=synth.NAVIER_STOKES)
+    else:
+        raise ValueError(workload)
+    if volume == "split":
+        if workload == "cylinder":
+            raise ValueError("the split form is built for Euler; the cylinder workload is Navier-Stokes")
+        p.volume = synth.VOLUME_SPLIT
+        p.riemann = synth.RUSANOV if riemann == "rusanov" else synth.ROE_HH
+    return p
+
+
 def run_cylinder(args, rank, world, local):
-    """The rotating cylindrical interface with Navier-Stokes at N = 7 (or, --workload
-    annular, the plane annular interface with Euler): RK steps through the curvilinear
-    kernels (interface lifting, lifting, viscous interface flux, element)."""
+    """The rotating cylindrical interface with Navier-Stokes at N = 7 (or, --workload annular
+    or cone, the plane annular or the conical interface with Euler, weak or split form): RK
+    steps through the curvilinear kernels (interface lifting, lifting, viscous interface
+    flux, element)."""
     import torch
     from paper_2008_04356_gb300 import build as B, slidemesh, synth
     import torch.distributed as dist
@@ -383,17 +406,8 @@ def run_cylinder(args, rank, world, local):
     stream = torch.cuda.current_stream()
     prec = synth.FP64 if args.precision == "fp64" else synth.FP32
     annular = args.workload in ("annular", "cone")     # the Euler shapes
-    if args.workload == "cone":
-        p = synth.config_cone(N=7, nel=(24, 48, 16), omega=0.4, alpha=math.pi / 6, flow="pulse", precision=prec)
-    elif annular:
-        p = synth.config_annular(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec)
-    split = annular and args.volume == "split"
-    if split:                      # the split form on the Euler shapes, Roe/HH unless asked otherwise
-        p.volume = synth.VOLUME_SPLIT
-        p.riemann = synth.RUSANOV if args.riemann == "rusanov" else synth.ROE_HH
-    else:
-        p = synth.config_cylinder(N=7, nel=(24, 48, 16), omega=0.4, flow="pulse", precision=prec,
-                                  physics=synth.NAVIER_STOKES)
+    p = shape_problem(args.workload, args.volume, args.riemann, prec)
+    split = p.volume == synth.VOLUME_SPLIT
     sol = slidemesh.Solver(p)
     sol.init_state()
     dt = synth.cfl_dt(p)
