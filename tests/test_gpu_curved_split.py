@@ -4,6 +4,7 @@ cylindrical, annular and conical interfaces and the plane box through general me
 right-hand side (FP64 to 1e-12, FP32 to 1e-5 relative L2), RK steps, conserved mass and
 energy."""
 import copy
+import math
 
 import numpy as np
 import pytest
@@ -71,7 +72,7 @@ def test_curved_split_rhs_fp64(sm, N, riemann, name):
 
 @pytest.mark.parametrize("name", ["cylinder", "annular", "cone"])
 def test_curved_split_rhs_fp32(sm, name):
-    for N in (3, 6):
+    for N in (3, 6, 7):
         p = shape(name, N)
         U = synth.random_state(p, seed=250 + N)
         ref = O.Oracle(p).rhs(U, 0.37)
@@ -102,3 +103,36 @@ def test_curved_split_steps(sm, name):
     t0 = o.totals(U0)
     for v in (0, 4):
         assert abs(d["totals"][v] - t0[v]) < 1e-12 * abs(t0[v])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["annular", "cone"])
+def test_curved_split_full_size_sampled(sm, name):
+    """The 2 x 24x48x16 annulus or cone at N = 7 (18.9 M DOF) with the split form and Roe/HH,
+    the benchmark's launch configuration: sampled elements (walls, interface, periodic ends,
+    interior) of the GPU RHS against the oracle element by element, FP64 to 1e-12 and FP32 to
+    1e-5 relative L2."""
+    if name == "cone":
+        p = synth.config_cone(N=7, nel=(24, 48, 16), omega=0.4, phi0=0.913, alpha=math.pi / 6, flow="pulse")
+    else:
+        p = synth.config_annular(N=7, nel=(24, 48, 16), omega=0.4, phi0=0.913, flow="pulse")
+    p.riemann, p.volume = synth.ROE_HH, synth.VOLUME_SPLIT
+    o = O.Oracle(p)
+    U = synth.random_state(p, seed=78)
+    rng = np.random.default_rng(6)
+    nx, ny, nz = 24, 48, 16
+    pick = [(b, ix, iy, iz) for b in (0, 1) for ix in (0, nx - 1) for iy in (0, ny - 1) for iz in (0, nz - 1)]
+    pick += [(int(rng.integers(2)), int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))) for _ in range(16)]
+    elems = np.array([b * nx * ny * nz + ix + nx * (iy + ny * iz) for b, ix, iy, iz in pick], dtype=np.int64)
+    t = 0.37
+    ref = o.rhs_elements(U, t, elems)
+    s = sm.Solver(p)
+    got = s.rhs(dev(U), t).cpu().numpy()[elems]
+    s.close()
+    assert rel_max(got, ref) < FP64_TOL
+    p32 = copy.deepcopy(p)
+    p32.precision = synth.FP32
+    s = sm.Solver(p32)
+    got32 = s.rhs(dev(U, torch.float32), t).cpu().numpy()[elems]
+    s.close()
+    assert rel_l2(got32, ref) < FP32_TOL
