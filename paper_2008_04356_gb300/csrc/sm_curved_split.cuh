@@ -25,6 +25,13 @@
 template <int N> struct CurvedSplitCfg {
   using C = ElemCfg<N>;
   static constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
+  // resident CTAs per SM asked of the register allocator: FP32 at N = 7 two CTAs of 512
+  // threads (64 registers), so that 32 warps hide the global-load latency instead of 16
+#ifdef SM_CSPLIT_MINB_OVERRIDE
+  template <typename T> __host__ __device__ static constexpr int minb() { return SM_CSPLIT_MINB_OVERRIDE; }
+#else
+  template <typename T> __host__ __device__ static constexpr int minb() { return sizeof(T) == 4 && N == 7 ? 2 : 1; }
+#endif
   template <typename T> static constexpr size_t smem_bytes() {
     // primitives, metric quadruples per direction, face fluxes, the Ds table
     return sizeof(T) * (size_t)(EPB * 6 * NN + EPB * 12 * NN + EPB * 30 * NP2 + NP * NP);
@@ -127,7 +134,7 @@ __device__ __forceinline__ void curved_split_block(const MeshDev& m, const Stage
 namespace {
 
 template <int N, typename T, int RIEM, int MODE>
-__global__ void __launch_bounds__(ElemCfg<N>::THREADS)
+__global__ void __launch_bounds__(ElemCfg<N>::THREADS, CurvedSplitCfg<N>::template minb<T>())
 curved_split_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
                     T* __restrict__ out, T* __restrict__ G, const T* __restrict__ Fs, const T* __restrict__ Fm,
                     const T rkA, const T rkB, const T dt) {
