@@ -6,8 +6,20 @@
 
 namespace {
 
+// Resident CTAs per SM asked of the register allocator for the element kernel: FP32 at N = 7
+// two CTAs of 512 threads (64 registers), so that 32 warps hide the global-load latency of the
+// state, geometry and neighbour traces instead of 16.
+template <int N, typename T>
+__host__ __device__ constexpr int curved_elem_minb() {
+#ifdef SM_CURVED_MINB_OVERRIDE
+  return SM_CURVED_MINB_OVERRIDE;
+#else
+  return sizeof(T) == 4 && N == 7 ? 2 : 1;
+#endif
+}
+
 template <int N, typename T, int RIEM, int MODE, int PHYS>
-__global__ void __launch_bounds__(ElemCfg<N>::THREADS)
+__global__ void __launch_bounds__(ElemCfg<N>::THREADS, curved_elem_minb<N, T>())
 curved_element_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
                       T* __restrict__ out, T* __restrict__ G, const T* __restrict__ Fs, const T* __restrict__ Fm,
                       const T rkA, const T rkB, const T dt, const T* __restrict__ Gr) {

@@ -188,6 +188,33 @@ def test_cylinder_ns_steps(sm, N):
     assert rel_l2(U32.cpu().numpy(), Uo) < FP32_TOL
 
 
+@pytest.mark.parametrize("physics", ["euler", "ns"])
+@pytest.mark.parametrize("riemann", [synth.RUSANOV, synth.ROE_HH])
+def test_cylinder_fp32_n7_rhs_and_steps(sm, riemann, physics):
+    """FP32 at N = 7 (the benchmark's degree, built for two CTAs per SM): the right-hand side
+    and three RK steps (first-stage and later-stage kernels) against the FP64 oracle."""
+    p = cylinder(7, riemann)
+    if physics == "ns":
+        p = ns(p)
+    o = O.Oracle(p)
+    U = synth.random_state(p, seed=90 + riemann)
+    ref = o.rhs(U, 0.37)
+    p32 = copy.deepcopy(p)
+    p32.precision = synth.FP32
+    s32 = sm.Solver(p32)
+    got = s32.rhs(dev(U, torch.float32), 0.37).cpu().numpy()
+    assert rel_l2(got, ref) < FP32_TOL
+    U0 = o.init_state()
+    dt = 0.5 * synth.cfl_dt(p)
+    Uo, Go = U0.copy(), np.zeros_like(U0)
+    o.step(Uo, Go, 0.0, dt, 3)
+    s32.set_state(U0.astype(np.float32), 0.0)
+    s32.step(dt, 3)
+    U32, _ = s32.get_state()
+    s32.close()
+    assert rel_l2(U32.cpu().numpy(), Uo) < FP32_TOL
+
+
 @pytest.mark.slow
 def test_cylinder_full_size_sampled(sm):
     """The 2 x 24x48x16 cylinder at N = 7 (18.9 M DOF) in the benchmark's launch
