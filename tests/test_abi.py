@@ -1,6 +1,7 @@
 """The C-ABI library builds, loads without a GPU and exports every function that
 include/*.h declares; the binding's signatures name only exported functions."""
 import ctypes
+import math
 import glob
 import os
 import re
@@ -64,3 +65,98 @@ def test_invalid_descriptions_are_rejected_before_any_cuda_call(libpath):
     assert L.sm_init_mesh(ctypes.byref(slidemesh.mesh_desc(p)), ctypes.byref(h)) == -1
     assert b"interface faces" in L.sm_last_error()
     assert L.sm_init_mesh(None, ctypes.byref(h)) == -1
+
+
+def _init(L, slidemesh, p):
+    h = ctypes.c_void_p()
+    rc = L.sm_init_mesh(ctypes.byref(slidemesh.mesh_desc(p)), ctypes.byref(h))
+    return rc, L.sm_last_error()
+
+
+@pytest.mark.parametrize("case", [
+    "split_ns", "periodic_cylinder", "periodic_ns", "periodic_bad", "volume_bad", "geom_bad",
+    "cone_angle", "cone_axis", "cone_flow", "annular_radius", "annular_flow", "plane_rotation_flow",
+])
+def test_shape_and_option_checks_without_gpu(libpath, case):
+    """Descriptions the library does not build are refused by sm_init_mesh before any CUDA
+    call: the split form with Navier-Stokes, the second interface off the plane Euler case,
+    out-of-range options, and geometry that the annulus and the cone cannot map."""
+    from paper_2008_04356_gb300 import slidemesh, synth
+    L = slidemesh.lib()
+    if case == "split_ns":
+        p = synth.config_shear_x(N=3)
+        p.volume = synth.VOLUME_SPLIT
+        want, msg = -7, b"split-form"
+    elif case == "periodic_cylinder":
+        p = synth.config_cylinder(N=3)
+        p.periodic_x = 1
+        want, msg = -7, b"periodic x"
+    elif case == "periodic_ns":
+        p = synth.config_shear_x(N=3)
+        p.periodic_x = 1
+        want, msg = -7, b"periodic x"
+    elif case == "periodic_bad":
+        p = synth.config_box(N=3)
+        p.periodic_x = 2
+        want, msg = -1, b"periodic_x"
+    elif case == "volume_bad":
+        p = synth.config_box(N=3)
+        p.volume = 5
+        want, msg = -1, b"volume integral"
+    elif case == "geom_bad":
+        p = synth.config_box(N=3)
+        p.geom = 9
+        want, msg = -7, b"geometry"
+    elif case == "cone_angle":
+        p = synth.config_cone(N=3)
+        p.cone_angle = 0.5 * math.pi
+        want, msg = -1, b"half-angle"
+    elif case == "cone_axis":
+        p = synth.config_cone(N=3, n=(-1.0, 0.1, 0.5), s=(0.0, 0.5))
+        want, msg = -1, b"off the axis"
+    elif case == "cone_flow":
+        p = synth.config_cone(N=3)
+        p.flow = synth.FLOW_ENTROPY_WAVE
+        want, msg = -1, b"cone flows"
+    elif case == "annular_radius":
+        p = synth.config_annular(N=3, r=(0.0, 1.0))
+        want, msg = -1, b"radii"
+    elif case == "annular_flow":
+        p = synth.config_annular(N=3)
+        p.flow = synth.FLOW_MODES
+        want, msg = -1, b"annular flows"
+    else:
+        p = synth.config_box(N=3)
+        p.flow = synth.FLOW_RIGID_ROTATION
+        want, msg = -1, b"need the cylinder"
+    rc, err = _init(L, slidemesh, p)
+    assert rc == want, (rc, err)
+    assert msg in err, err
+
+
+@pytest.mark.parametrize("case", ["ns", "cylinder", "split", "periodic", "rotation", "aliased", "null"])
+def test_no_alloc_entry_point_checks_without_gpu(libpath, case):
+    """sm_rhs_static takes the plane, one-interface, weak-form Euler operator and refuses the
+    rest (and malformed calls) before touching the device."""
+    from paper_2008_04356_gb300 import slidemesh, synth
+    L = slidemesh.lib()
+    p = synth.config_box(N=3)
+    mo = slidemesh.SmMotion(v=0.5, omega=0.0, delta0=0.0)
+    a, b = ctypes.c_void_p(16), ctypes.c_void_p(32)      # never dereferenced: refused first
+    want = -7
+    if case == "ns":
+        p = synth.config_shear_x(N=3)
+    elif case == "cylinder":
+        p = synth.config_cylinder(N=3)
+    elif case == "split":
+        p.volume = synth.VOLUME_SPLIT
+    elif case == "periodic":
+        p.periodic_x = 1
+    elif case == "rotation":
+        mo = slidemesh.SmMotion(v=0.0, omega=0.4, delta0=0.0)
+    elif case == "aliased":
+        b, want = a, -1
+    else:
+        a, want = None, -1
+    rc = L.sm_rhs_static(ctypes.byref(slidemesh.mesh_desc(p)), ctypes.byref(mo), 0.0, a, b, None)
+    assert rc == want, (rc, L.sm_last_error())
