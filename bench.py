@@ -169,8 +169,13 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
 
 
-def ncu_traffic():
-    """DRAM bytes per element-kernel launch from the committed ncu summary, if it was taken
+# elements of the full interface-heavy workload (2 blocks x 4x256x256)
+FULL_ELEMENTS = 2 * 4 * 256 * 256
+
+
+def ncu_traffic(nelem: int = FULL_ELEMENTS):
+    """DRAM bytes per element-kernel launch of nelem elements from the committed ncu summary
+    (scaled from the full workload by the element count, as the traffic is), if it was taken
     on the current element-kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "dg_element_traffic.json")
     try:
@@ -179,7 +184,8 @@ def ncu_traffic():
         return None
     if rec.get("source_sha") != source_sha(ELEMENT_SOURCES):
         return None
-    return rec.get("dram_bytes_per_launch_full_workload")
+    full = rec.get("dram_bytes_per_launch_full_workload")
+    return None if full is None else full * nelem / FULL_ELEMENTS
 
 
 def cpu_baseline(seconds: float, volume: int = 0, riemann: int = 0):
@@ -538,7 +544,7 @@ def main():
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     achieved = elem_bytes / (elem_ms * 1e-3) / 1e9
-    traffic = ncu_traffic()
+    traffic = ncu_traffic(p.nelem)
 
     # FP64 plain path, same workload, one solve
     p64 = synth.config_interface_heavy(seed=1 + rank, precision=synth.FP64, nz=args.nz)

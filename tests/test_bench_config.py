@@ -41,3 +41,18 @@ def test_split_cylinder_rejected():
 def test_unknown_workload_rejected():
     with pytest.raises(ValueError):
         bench.shape_problem("sphere", "weak", None, synth.FP32)
+
+
+def test_traffic_scales_with_the_launch_element_count(monkeypatch):
+    import json
+    import os
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "dg_element_traffic.json")))
+    monkeypatch.setattr(bench, "source_sha", lambda paths: rec["source_sha"])
+    assert bench.ncu_traffic() == rec["dram_bytes_per_launch_full_workload"]
+    # the captured case (2 x 4x256x64) reads back its own measured bytes
+    assert bench.ncu_traffic(2 * 4 * 256 * 64) == pytest.approx(rec["dram_bytes_per_launch_captured"], rel=1e-12)
+
+
+def test_traffic_is_dropped_when_the_kernel_source_changed(monkeypatch):
+    monkeypatch.setattr(bench, "source_sha", lambda paths: "0000000000000000")
+    assert bench.ncu_traffic() is None
