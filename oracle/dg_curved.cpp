@@ -634,9 +634,12 @@ void curved_two_point(int kind, const double* Ua, const double* Ub, const double
 /* Split-form residual of a curved element (Sec. 3.1, the split formulation with Pirozzoli's
  * flux), strong form:
  *   J dU/dt = - sum_d sum_l 2 D_il F~#^d(U_node, U_l)  - sum_faces ell(+-1)/w (F* . N sJ - F~^d(U_node)) ,
- * F~^d(U) = Ja^d . F(U) - (Ja^d . v^g) U the node's own contravariant flux. */
-void split_residual(const Curved& o, const double* U, double t, long long e, const std::vector<double>* Fs,
-                    const std::vector<double>* Fm, double* Ut) {
+ * F~^d(U) = Ja^d . F(U) - (Ja^d . v^g) U the node's own contravariant flux.  Navier-Stokes
+ * (grad given, the BR1 gradients): the viscous flux keeps the weak form of the weak-form
+ * residual, + sum_d sum_l Dhat_il Ja^d . F^v(U_l, grad_l), and the face flux F* carries the
+ * BR1 viscous mean (the node's own flux subtracted is the advective one only). */
+void split_residual(const Curved& o, const double* U, const double* grad, double t, long long e,
+                    const std::vector<double>* Fs, const std::vector<double>* Fm, double* Ut) {
   int np = o.np, nn = o.nn, nq = np * np;
   int kind = o.p.volume == 2 ? 1 : 0;
   std::vector<double> Ja(9 * nn), V(3 * nn);       /* Ja[(d*3 + c)*nn + nd], V[d*nn + nd] */
@@ -672,10 +675,36 @@ void split_residual(const Curved& o, const double* U, double t, long long e, con
         }
         for (int v = 0; v < 5; ++v) Ut[v * nn + nd] = -acc[v];
       }
+  if (grad) {
+    std::vector<double> Gt(15 * nn);         /* Ja^d . F^v, [(d*5 + v)*nn + nd] */
+    for (int nd = 0; nd < nn; ++nd) {
+      double u[5], g15[15], Fv[15];
+      for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * nn + nd];
+      for (int k = 0; k < 15; ++k) g15[k] = grad[(e * 15 + k) * nn + nd];
+      orc_viscous_flux(u, g15, o.p.mu, o.p.Pr, o.p.Rgas, o.p.gamma, Fv);
+      for (int d = 0; d < 3; ++d) {
+        double a[3];
+        ja(d, nd, a);
+        for (int v = 0; v < 5; ++v) Gt[(d * 5 + v) * nn + nd] = a[0] * Fv[v] + a[1] * Fv[5 + v] + a[2] * Fv[10 + v];
+      }
+    }
+    for (int v = 0; v < 5; ++v)
+      for (int k = 0; k < np; ++k)
+        for (int j = 0; j < np; ++j)
+          for (int i = 0; i < np; ++i) {
+            double acc = 0.0;
+            for (int l = 0; l < np; ++l) {
+              acc += o.Dhat[i * np + l] * Gt[(0 * 5 + v) * nn + node(o, l, j, k)];
+              acc += o.Dhat[j * np + l] * Gt[(1 * 5 + v) * nn + node(o, i, l, k)];
+              acc += o.Dhat[k * np + l] * Gt[(2 * 5 + v) * nn + node(o, i, j, l)];
+            }
+            Ut[v * nn + node(o, i, j, k)] += acc;
+          }
+  }
   std::vector<double> Fout(5 * nq);
   for (int d = 0; d < 3; ++d)
     for (int side = 0; side < 2; ++side) {
-      face_flux(o, U, nullptr, t, e, d, side, Fs, Fm, Fout.data());
+      face_flux(o, U, grad, t, e, d, side, Fs, Fm, Fout.data());
       double wend = o.w[side ? o.N : 0], sg = side ? 1.0 : -1.0;
       for (int b = 0; b < np; ++b)
         for (int a = 0; a < np; ++a) {
@@ -694,7 +723,7 @@ void split_residual(const Curved& o, const double* U, double t, long long e, con
 void residual(const Curved& o, const double* U, const double* grad, double t, long long e,
               const std::vector<double>* Fs, const std::vector<double>* Fm, double* Ut) {
   if (o.p.volume != 0) {
-    split_residual(o, U, t, e, Fs, Fm, Ut);
+    split_residual(o, U, grad, t, e, Fs, Fm, Ut);
     return;
   }
   int np = o.np, nn = o.nn, nq = np * np;

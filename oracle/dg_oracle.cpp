@@ -914,9 +914,14 @@ void face_flux_out(const Oracle& o, const Interface* I, const double* U, const d
  * form, the volume term carried by the two-point flux:
  *   J dU/dt = - sum_d sum_l 2 D_il |Ja^d| F#^d(U_node, U_l)        (l along xi^{d+1})
  *             - sum_faces ell(+-1)/w (F* . N - F(U_node) . N) sJ ,
- * the surface term being the Riemann flux minus the node's own flux. */
-void split_element_residual(const Oracle& o, const Interface* I, const double* U, double t, long long e,
-                            const std::vector<double>* Fs, const std::vector<double>* Fm, double* Ut_e) {
+ * the surface term being the Riemann flux minus the node's own flux.  Navier-Stokes (grad
+ * given, the BR1 gradients): the viscous flux keeps the weak form of the weak-form residual,
+ *   + sum_d sum_l Dhat_il |Ja^d| F^v_d(U_l, grad_l),
+ * and the face flux F* carries the BR1 viscous mean, F* = F*_adv - {{F^v}} . N (the node's
+ * own flux subtracted is the advective one only). */
+void split_element_residual(const Oracle& o, const Interface* I, const double* U, const double* grad, double t,
+                            long long e, const std::vector<double>* Fs, const std::vector<double>* Fm,
+                            double* Ut_e) {
   ElemId id = elem_id(o, e);
   int np = o.np, nn = o.nn, nq = np * np;
   int kind = o.p.volume == 2 ? 1 : 0;
@@ -939,10 +944,33 @@ void split_element_residual(const Oracle& o, const Interface* I, const double* U
         }
         for (int v = 0; v < 5; ++v) Ut_e[v * nn + node] = -acc[v];
       }
+  if (grad) {
+    std::vector<double> Fvt(3 * 5 * nn);     /* |Ja^d| F^v along xi^{d+1}'s physical axis */
+    for (int node = 0; node < nn; ++node) {
+      double u[5], g15[15], Fv[15];
+      for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * nn + node];
+      for (int k = 0; k < 15; ++k) g15[k] = grad[(e * 15 + k) * nn + node];
+      orc_viscous_flux(u, g15, o.p.mu, o.p.Pr, o.p.Rgas, o.p.gamma, Fv);
+      for (int d = 0; d < 3; ++d)
+        for (int v = 0; v < 5; ++v) Fvt[(d * 5 + v) * nn + node] = metric(o, id.blk, d) * Fv[phys_axis(d) * 5 + v];
+    }
+    for (int v = 0; v < 5; ++v)
+      for (int k = 0; k < np; ++k)
+        for (int j = 0; j < np; ++j)
+          for (int i = 0; i < np; ++i) {
+            double acc = 0.0;
+            for (int l = 0; l < np; ++l) {
+              acc += o.Dhat[i * np + l] * Fvt[(0 * 5 + v) * nn + l + np * (j + np * k)];
+              acc += o.Dhat[j * np + l] * Fvt[(1 * 5 + v) * nn + i + np * (l + np * k)];
+              acc += o.Dhat[k * np + l] * Fvt[(2 * 5 + v) * nn + i + np * (j + np * l)];
+            }
+            Ut_e[v * nn + i + np * (j + np * k)] += acc;
+          }
+  }
   std::vector<double> Fout(5 * nq);
   for (int d = 0; d < 3; ++d)
     for (int side = 0; side < 2; ++side) {
-      face_flux_out(o, I, U, nullptr, t, e, d, side, Fs, Fm, Fout.data());
+      face_flux_out(o, I, U, grad, t, e, d, side, Fs, Fm, Fout.data());
       double wend = o.w[side == 0 ? 0 : o.N], sJ = metric(o, id.blk, d), sg = side == 1 ? 1.0 : -1.0;
       double n[3], u[5], f[5];
       unit_normal(d, n);
@@ -965,7 +993,7 @@ void split_element_residual(const Oracle& o, const Interface* I, const double* U
 void element_residual(const Oracle& o, const Interface* I, const double* U, const double* grad, double t, long long e,
                       const std::vector<double>* Fs, const std::vector<double>* Fm, double* Ut_e) {
   if (o.p.volume != 0) {
-    split_element_residual(o, I, U, t, e, Fs, Fm, Ut_e);
+    split_element_residual(o, I, U, grad, t, e, Fs, Fm, Ut_e);
     return;
   }
   ElemId id = elem_id(o, e);
@@ -1154,11 +1182,10 @@ extern "C" {
 static bool curved(void* h) { return *(int*)h == 1; }
 
 void* orc_create(const orc_problem* p) {
-  if (p->volume < 0 || p->volume > 2 || (p->volume != 0 && p->physics != 0)) return nullptr;
+  if (p->volume < 0 || p->volume > 2) return nullptr;
   if (p->geom != 0) return p->periodic_x ? nullptr : orc_curved_create(p);
   if (p->N < 1 || p->N > 15) return nullptr;
   if (p->nel_s[1] != p->nel_m[1] || p->nel_s[2] != p->nel_m[2]) return nullptr;
-  if (p->volume < 0 || p->volume > 2 || (p->volume != 0 && p->physics != 0)) return nullptr;
   if (p->periodic_x && p->physics != 0) return nullptr;
   Oracle* o = new Oracle();
   o->p = *p;

@@ -46,8 +46,10 @@ typedef struct {
   int volume;            /* volume integral (Sec. 3.1): 0 weak form; 1 split form with
                             Pirozzoli's two-point flux; 2 split form with the central
                             two-point flux (equal to the weak form by summation by parts).
-                            The split forms take Euler physics; on curved geometries the
-                            two-point flux uses the averaged metric terms of its two nodes. */
+                            With Navier-Stokes physics the viscous flux keeps the weak form
+                            and the face flux carries the BR1 viscous mean; on curved
+                            geometries the two-point flux uses the averaged metric terms of
+                            its two nodes. */
   int periodic_x;        /* 1: x periodic with period x2 - x0, so that the moving block's face
                             x = x2 meets the static block's face x = x0 in a second sliding
                             interface (several interfaces, Sec. 4.3); geom 0, Euler physics */
