@@ -228,22 +228,24 @@ void sm_destroy(sm_solver* s);
  * the device memory through its own pool, code in regions where an allocation (which
  * synchronises the device) is not acceptable, or embedders that forbid allocations after
  * start-up.  It computes dU/dt = R(U, t) for the mesh desc and motion into dUt exactly
- * as sm_init_mesh + sm_set_motion + sm_rhs would, but needs no solver: its scratch (basis
- * tables, stage parameters, both sides' interface face fluxes) lives in one fixed
- * 16 MiB device array inside the library, which every GPU that loads the library holds
- * until the process exits.  The caller owns dU and dUt (device pointers, the solver
- * layout and precision of desc, not overlapping).
+ * as sm_init_mesh + sm_set_motion + sm_rhs would, but needs no solver: its scratch (stage
+ * parameters, both sides' interface face fluxes) lives in one fixed 16 MiB device array
+ * inside the library, and the LGL basis tables of N = 1..7 in a second fixed array; every
+ * GPU that loads the library holds both until the process exits.  The caller owns dU and
+ * dUt (device pointers, the solver layout and precision of desc, not overlapping).
+ * Plane interface, Euler, weak form, one interface (SM_ERR_UNSUPPORTED otherwise).
  *  - Sizes: the scratch needed is about 2 * faces * 5 (N+1)^2 * bytes-per-scalar plus
  *    ~10 KB (faces = nel_static[1] * nel_static[2]); larger problems are rejected with
  *    SM_ERR_ARG and a message naming both sizes (use sm_rhs for them).
- *  - The first call on a device sets that device up (looks up the array's device address
- *    and sets kernel attributes); make that first call before any stream capture.
+ *  - The first call on a device sets that device up (looks up both arrays' device
+ *    addresses, writes the basis tables with a synchronous copy, sets kernel attributes);
+ *    make that first call before any stream capture.  After it, a call enqueues kernel
+ *    launches on stream and copies nothing between host and device.
  *  - It calls no cudaMalloc, cudaFree or other allocating routine.
- *  - All calls share the one array, whose contents persist from the last call: every byte
- *    a call reads is written by that same call first, so nothing needs clearing, but calls
- *    whose work overlaps on the GPU (other streams, other host threads) race with each
- *    other; serialise them, e.g. on one stream.
- * Asynchronous on stream. */
+ *  - All calls share the one scratch array, whose contents persist from the last call:
+ *    every byte a call reads is written by that same call first, so nothing needs
+ *    clearing, but calls whose work overlaps on the GPU (other streams, other host threads)
+ *    race with each other; serialise them, e.g. on one stream. */
 int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, double t, const void* dU, void* dUt,
                   void* stream);
 
@@ -351,6 +353,16 @@ int sm_map(const double* d_delta, int count, double l, int n_par, long long* d_n
  * P[j][i] maps face node i to mortar node j and B[i][j] maps mortar node j to face
  * node i; lo is the mortar xi <= sigma (Jacobian (1+sigma)/2), hi the mortar xi > sigma. */
 int sm_mortar_matrices(int N, double sigma, double* d_out, void* stream);
+
+/* ---- measurement aid ---- */
+
+/* FP64 fused multiply-add throughput probe for the roofline of the FP64 path (the paper
+ * has no counterpart): launches blocks x threads threads, each running eight independent
+ * chains x <- fma(x, a, b) for iters rounds, i.e. 16 * iters * blocks * threads FP64
+ * flop, and writes one double per thread to d_out (device, blocks * threads doubles,
+ * caller-owned).  Time it with events on stream.  Errors: SM_ERR_ARG (blocks < 1, threads
+ * not a multiple of 32 in 32..1024, iters < 1, NULL d_out), SM_ERR_CUDA. */
+int sm_fp64_fma_probe(int blocks, int threads, int iters, double* d_out, void* stream);
 
 const char* sm_status_string(int status);
 const char* sm_last_error(void);

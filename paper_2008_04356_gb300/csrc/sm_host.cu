@@ -601,6 +601,39 @@ int valid_desc(const sm_mesh_desc* d) {
   return SM_OK;
 }
 
+// The mesh, flow and physics fields of the kernels' mesh description from the C-ABI
+// description (shared by sm_init_mesh and sm_rhs_static); device pointers, the motion and
+// the per-precision constants are set by the callers.
+void mesh_from_desc(const sm_mesh_desc* desc, MeshDev& m) {
+  memset(&m, 0, sizeof(m));
+  m.nxs = desc->nel_static[0];
+  m.nxm = desc->nel_moving[0];
+  m.ny = desc->nel_static[1];
+  m.nz = desc->nel_static[2];
+  m.Es = (long long)m.nxs * m.ny * m.nz;
+  m.E = m.Es + (long long)m.nxm * m.ny * m.nz;
+  m.hx0 = (desc->x1 - desc->x0) / m.nxs;
+  m.hx1 = (desc->x2 - desc->x1) / m.nxm;
+  m.hy = (desc->y1 - desc->y0) / m.ny;
+  m.hz = (desc->z1 - desc->z0) / m.nz;
+  m.x0 = desc->x0;
+  m.x1 = desc->x1;
+  m.y0 = desc->y0;
+  m.z0 = desc->z0;
+  m.gamma = desc->gamma;
+  m.conforming = desc->interface_conforming;
+  m.flow = desc->flow;
+  m.physics = desc->physics;
+  m.mu = desc->mu;
+  m.Pr = desc->Pr;
+  m.Rgas = desc->Rgas;
+  m.geom = desc->geom;
+  m.Theta = desc->y1 - desc->y0;
+  m.cone_s = sin(desc->cone_angle);
+  m.cone_c = cos(desc->cone_angle);
+  for (int k = 0; k < 16; ++k) m.fpar[k] = desc->fpar[k];
+}
+
 }  // namespace
 
 extern "C" {
@@ -638,33 +671,7 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   s->sb = s->prec == SM_FP64 ? 8 : 4;
   lgl_basis(s->N, s->basis_h);
   MeshDev& m = s->m;
-  memset(&m, 0, sizeof(m));
-  m.nxs = desc->nel_static[0];
-  m.nxm = desc->nel_moving[0];
-  m.ny = desc->nel_static[1];
-  m.nz = desc->nel_static[2];
-  m.Es = (long long)m.nxs * m.ny * m.nz;
-  m.E = m.Es + (long long)m.nxm * m.ny * m.nz;
-  m.hx0 = (desc->x1 - desc->x0) / m.nxs;
-  m.hx1 = (desc->x2 - desc->x1) / m.nxm;
-  m.hy = (desc->y1 - desc->y0) / m.ny;
-  m.hz = (desc->z1 - desc->z0) / m.nz;
-  m.x0 = desc->x0;
-  m.x1 = desc->x1;
-  m.y0 = desc->y0;
-  m.z0 = desc->z0;
-  m.gamma = desc->gamma;
-  m.conforming = desc->interface_conforming;
-  m.flow = desc->flow;
-  m.physics = desc->physics;
-  m.mu = desc->mu;
-  m.Pr = desc->Pr;
-  m.Rgas = desc->Rgas;
-  m.geom = desc->geom;
-  m.Theta = desc->y1 - desc->y0;
-  m.cone_s = sin(desc->cone_angle);
-  m.cone_c = cos(desc->cone_angle);
-  for (int k = 0; k < 16; ++k) m.fpar[k] = desc->fpar[k];
+  mesh_from_desc(desc, m);
   s->nstate = m.E * 5 * s->nn;
   s->nface_vals = (long long)m.ny * m.nz * 5 * s->np * s->np;
   s->red_blocks = 304;
@@ -974,6 +981,13 @@ int sm_map(const double* d_delta, int count, double l, int n_par, long long* d_n
   if (count < 0 || n_par < 1 || !(l > 0.0) || (count > 0 && (!d_delta || !d_n || !d_s)))
     return fail(SM_ERR_ARG, "invalid sm_map arguments");
   SM_CK(launch_map_batch(d_delta, count, l, n_par, d_n, d_s, d_pairs, (cudaStream_t)stream), "map kernel");
+  return SM_OK;
+}
+
+int sm_fp64_fma_probe(int blocks, int threads, int iters, double* d_out, void* stream) {
+  if (blocks < 1 || threads < 32 || threads > 1024 || threads % 32 || iters < 1 || !d_out)
+    return fail(SM_ERR_ARG, "sm_fp64_fma_probe: blocks >= 1, threads a multiple of 32 in 32..1024, iters >= 1, d_out");
+  SM_CK(launch_fp64_fma_probe(blocks, threads, iters, d_out, (cudaStream_t)stream), "FP64 FMA probe");
   return SM_OK;
 }
 
@@ -1311,22 +1325,31 @@ extern "C" void sm_batch_destroy(sm_batch* b) { free_batch(b); }
 #define SM_STATIC_SCRATCH_BYTES (16u << 20)
 
 static __device__ __align__(256) unsigned char g_static_scratch[SM_STATIC_SCRATCH_BYTES];
+// The LGL basis tables of N = 1..7, written once per device when the entry point sets the
+// device up, so that a call copies nothing from the host.
+static __device__ BasisDev g_static_basis[7];
 
 namespace {
 
 std::mutex g_static_mu;
-void* g_static_addr[256] = {nullptr};
+struct StaticDevice { unsigned char* scratch; BasisDev* basis; };
+StaticDevice g_static_dev[256] = {};
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
-// Once per device, with that device current: the device address of the scratch array and
-// the kernels' shared-memory attributes.
-int static_scratch_address(int dev, unsigned char** out) {
+// Once per device, with that device current: the device addresses of the scratch array and
+// of the basis tables (filled here by a synchronous copy), and the kernels' attributes.
+int static_device_setup(int dev, StaticDevice* out) {
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (dev < 0 || dev >= 256) return fail(SM_ERR_ARG, "device ordinal out of range");
-  if (!g_static_addr[dev]) {
+  if (!g_static_dev[dev].scratch) {
     void* p = nullptr;
+    void* pb = nullptr;
     SM_CK(cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress of the static scratch");
+    SM_CK(cudaGetSymbolAddress(&pb, g_static_basis), "cudaGetSymbolAddress of the static basis tables");
+    static BasisDev tables[7];
+    for (int n = 1; n <= 7; ++n) lgl_basis(n, tables[n - 1]);
+    SM_CK(cudaMemcpyToSymbol(g_static_basis, tables, sizeof(tables)), "upload the static basis tables");
     SM_CK(ensure_dhat_constants(), "derivative constants");
     for (int n = 1; n <= 7; ++n) {
       SM_CK(prepare_element_f64(n), "element kernel attributes");
@@ -1334,9 +1357,10 @@ int static_scratch_address(int dev, unsigned char** out) {
       SM_CK(prepare_interface(n, SM_FP64), "interface kernel attributes");
       SM_CK(prepare_interface(n, SM_FP32), "interface kernel attributes");
     }
-    g_static_addr[dev] = p;
+    g_static_dev[dev].basis = (BasisDev*)pb;
+    g_static_dev[dev].scratch = (unsigned char*)p;
   }
-  *out = (unsigned char*)g_static_addr[dev];
+  *out = g_static_dev[dev];
   return SM_OK;
 }
 
@@ -1344,8 +1368,7 @@ size_t static_scratch_bytes(const sm_mesh_desc* desc) {
   if (!desc || desc->N < 1 || desc->N > 7) return 0;
   const size_t np = desc->N + 1, sb = desc->precision == SM_FP64 ? 8 : 4;
   const size_t faces = (size_t)desc->nel_static[1] * (size_t)desc->nel_static[2];
-  return align256(sizeof(BasisDev)) + align256(sizeof(double) * 160) + align256(sizeof(StageParams)) +
-         2 * align256(faces * 5 * np * np * sb);
+  return align256(sizeof(StageParams)) + 2 * align256(faces * 5 * np * np * sb);
 }
 
 }  // namespace
@@ -1374,58 +1397,35 @@ extern "C" int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, 
   }
   int dev = 0;
   SM_CK(cudaGetDevice(&dev), "cudaGetDevice");
-  unsigned char* base = nullptr;
-  rc = static_scratch_address(dev, &base);
+  StaticDevice sd;
+  rc = static_device_setup(dev, &sd);
   if (rc != SM_OK) return rc;
   const int N = desc->N, np = N + 1, prec = desc->precision, sb = prec == SM_FP64 ? 8 : 4;
-  BasisDev* d_basis = (BasisDev*)base;
-  double* d_modes = (double*)(base + align256(sizeof(BasisDev)));
-  StageParams* d_sp = (StageParams*)((unsigned char*)d_modes + align256(sizeof(double) * 160));
-  unsigned char* d_fs = (unsigned char*)d_sp + align256(sizeof(StageParams));
+  StageParams* d_sp = (StageParams*)sd.scratch;
+  unsigned char* d_fs = sd.scratch + align256(sizeof(StageParams));
   const size_t fbytes = (size_t)desc->nel_static[1] * desc->nel_static[2] * 5 * np * np * sb;
   unsigned char* d_fm = d_fs + align256(fbytes);
-  // mesh description, as sm_init_mesh builds it
+  // the mesh description as sm_init_mesh builds it for the plane interface, with the
+  // device's basis table of degree N; the modes of the initial flow are not read by the
+  // right-hand side's kernels (the weak Dirichlet state of that flow is its background)
   BasisDev basis;
   lgl_basis(N, basis);
   MeshDev m;
-  memset(&m, 0, sizeof(m));
-  m.nxs = desc->nel_static[0];
-  m.nxm = desc->nel_moving[0];
-  m.ny = desc->nel_static[1];
-  m.nz = desc->nel_static[2];
-  m.Es = (long long)m.nxs * m.ny * m.nz;
-  m.E = m.Es + (long long)m.nxm * m.ny * m.nz;
-  m.hx0 = (desc->x1 - desc->x0) / m.nxs;
-  m.hx1 = (desc->x2 - desc->x1) / m.nxm;
-  m.hy = (desc->y1 - desc->y0) / m.ny;
-  m.hz = (desc->z1 - desc->z0) / m.nz;
-  m.x0 = desc->x0;
-  m.x1 = desc->x1;
-  m.y0 = desc->y0;
-  m.z0 = desc->z0;
-  m.gamma = desc->gamma;
-  m.conforming = desc->interface_conforming;
-  m.flow = desc->flow;
+  mesh_from_desc(desc, m);
   m.v = motion->v;
   m.delta0 = motion->delta0;
-  for (int k = 0; k < 16; ++k) m.fpar[k] = desc->fpar[k];
-  m.basis = d_basis;
-  m.modes = d_modes;
+  m.basis = sd.basis + (N - 1);
+  m.modes = nullptr;
   fill_constants(m, basis, desc->fpar);
-  // Every byte the kernels read is written by this call first (basis and modes here, the
-  // stage parameters by the mapper kernel, every interface face by the interface kernel),
-  // so nothing of a previous call's contents is used.
+  // Every byte of the scratch the kernels read is written by this call first (the stage
+  // parameters by the mapper kernel, every interface face by the interface kernel), so
+  // nothing of a previous call's contents is used.  The call enqueues kernel launches only.
   cudaStream_t st = (cudaStream_t)stream;
-  SM_CK(cudaMemcpyAsync(d_basis, &basis, sizeof(BasisDev), cudaMemcpyHostToDevice, st), "upload basis");
-  SM_CK(cudaMemcpyAsync(d_modes, &desc->modes[0][0][0], sizeof(double) * 160, cudaMemcpyHostToDevice, st),
-        "upload modes");
   SM_CK(launch_stage_params(m, np, d_sp, nullptr, t, 0.0, 0.0, 0, st), "stage parameters");
   if (!desc->interface_conforming)
     SM_CK(launch_interface(N, prec, desc->riemann, m, d_sp, dU, d_fs, d_fm, st), "interface kernel");
   ElemArgs a{m, d_sp, dU, dUt, nullptr, d_fs, d_fm, 0.0, 0.0, 0.0};
   SM_CK(prec == SM_FP64 ? launch_element_f64(N, desc->riemann, ELEM_RHS, a, st)
                         : launch_element_f32(N, desc->riemann, ELEM_RHS, a, st), "element kernel");
-  // the host copies of basis and modes above are pageable: cudaMemcpyAsync has staged
-  // them before returning, so the stack buffers may go out of scope here.
   return SM_OK;
 }

@@ -56,3 +56,15 @@ def test_traffic_scales_with_the_launch_element_count(monkeypatch):
 def test_traffic_is_dropped_when_the_kernel_source_changed(monkeypatch):
     monkeypatch.setattr(bench, "source_sha", lambda paths: "0000000000000000")
     assert bench.ncu_traffic() is None
+
+
+def test_algorithmic_flop_count_of_the_fp64_path():
+    """The method's FP64 operations per DOF-update: the per-node terms at N = 5 add up to
+    12 + 27 + 180 + 25 + 39 + 10 + 5 + 25 = 323, and the interface adds its per-face-pair
+    work (80 (N+1)^3 + 156 (N+1)^2 flop) spread over the DOF of the two blocks."""
+    faces, dof = 65536, 2 * 4 * 256 * 256 * 216
+    per_face = 80 * 216 + 156 * 36
+    assert bench.algorithmic_flop_per_dof(5, faces, dof) == pytest.approx(323 + per_face * faces / dof, rel=1e-12)
+    assert bench.algorithmic_flop_per_dof(5, 0, dof) == pytest.approx(323, rel=1e-12)
+    # the contractions grow with N + 1, the face terms shrink with it
+    assert bench.algorithmic_flop_per_dof(7, 0, 1) > bench.algorithmic_flop_per_dof(3, 0, 1)

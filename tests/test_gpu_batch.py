@@ -13,6 +13,8 @@ import pytest
 from oracle import oracle as O
 from paper_2008_04356_gb300 import synth
 
+import fp32_steps as F
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -50,27 +52,33 @@ def fresh(sm, p):
 
 
 def test_batch_matches_one_at_a_time_and_oracle(sm):
+    """Batched steps from perturbed initial states (fp32_steps): the same as each solve
+    stepped alone, and every solve's increment against the FP64 oracle at 1e-5."""
     ps = problems()
     dts = [synth.cfl_dt(p) for p in ps]
-    batched = [fresh(sm, p) for p in ps]
+    oracles = [O.Oracle(p) for p in ps]
+    U0s = [F.perturbed(o.init_state(), seed=140 + k) for k, o in enumerate(oracles)]
+    batched = []
+    for p, U0 in zip(ps, U0s):
+        s = sm.Solver(p)
+        s.set_state(U0.astype(np.float32), 0.0)
+        batched.append(s)
     bt = sm.Batch(batched, dts)
     bt.step(3)
     bt.step(4)
-    for p, dt, s in zip(ps, dts, batched):
-        alone = fresh(sm, p)
+    for p, dt, s, o, U0 in zip(ps, dts, batched, oracles, U0s):
+        alone = sm.Solver(p)
+        alone.set_state(U0.astype(np.float32), 0.0)
         alone.step(dt, 7)
         ub, tb = s.get_state()
         ua, ta = alone.get_state()
         assert abs(tb - ta) < 1e-15
         assert rel_l2(ub.cpu().numpy(), ua.cpu().numpy()) < FP32_TOL
-    # one of them against the FP64 oracle
-    p, dt = ps[1], dts[1]
-    o = O.Oracle(p)
-    U = o.init_state()
-    G = np.zeros_like(U)
-    o.step(U, G, 0.0, dt, 7)
-    ub, _ = batched[1].get_state()
-    assert rel_l2(ub.cpu().numpy(), U) < FP32_TOL
+        Uo, Go = U0.copy(), np.zeros_like(U0)
+        o.step(Uo, Go, 0.0, dt, 7)
+        err = F.increment_error(U0, ub.cpu().numpy(), Uo)
+        print("N=%d: batched increment rel L2 %.2e" % (p.N, err))
+        assert err < F.INCREMENT_TOL
 
 
 def test_result_independent_of_batch_and_launch_shapes(sm):

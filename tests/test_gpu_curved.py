@@ -10,6 +10,8 @@ import pytest
 from oracle import oracle as O
 from paper_2008_04356_gb300 import synth
 
+import fp32_steps as F
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -115,10 +117,9 @@ def test_cylinder_steps(sm, N):
     p32 = copy.deepcopy(p)
     p32.precision = synth.FP32
     s32 = sm.Solver(p32)
-    s32.set_state(U0.astype(np.float32), 0.0)
-    s32.step(dt, 4)
-    U32, _ = s32.get_state()
-    assert rel_l2(U32.cpu().numpy(), Uo) < FP32_TOL
+    err = F.check_fp32_steps(s32, o, F.perturbed(U0, seed=70 + N), dt, 4)
+    print("FP32 increment rel L2 %.2e" % err)
+    s32.close()
     # mass and energy: slip walls and the periodic sector keep them (to rounding)
     d = s.diag()
     t0 = o.totals(U0)
@@ -182,10 +183,9 @@ def test_cylinder_ns_steps(sm, N):
     p32 = copy.deepcopy(p)
     p32.precision = synth.FP32
     s32 = sm.Solver(p32)
-    s32.set_state(U0.astype(np.float32), 0.0)
-    s32.step(dt, 3)
-    U32, _ = s32.get_state()
-    assert rel_l2(U32.cpu().numpy(), Uo) < FP32_TOL
+    err = F.check_fp32_steps(s32, o, F.perturbed(U0, seed=80 + N), dt, 3)
+    print("FP32 increment rel L2 %.2e" % err)
+    s32.close()
 
 
 @pytest.mark.parametrize("physics", ["euler", "ns"])
@@ -204,15 +204,10 @@ def test_cylinder_fp32_n7_rhs_and_steps(sm, riemann, physics):
     s32 = sm.Solver(p32)
     got = s32.rhs(dev(U, torch.float32), 0.37).cpu().numpy()
     assert rel_l2(got, ref) < FP32_TOL
-    U0 = o.init_state()
     dt = 0.5 * synth.cfl_dt(p)
-    Uo, Go = U0.copy(), np.zeros_like(U0)
-    o.step(Uo, Go, 0.0, dt, 3)
-    s32.set_state(U0.astype(np.float32), 0.0)
-    s32.step(dt, 3)
-    U32, _ = s32.get_state()
+    err = F.check_fp32_steps(s32, o, F.perturbed(o.init_state(), seed=95 + riemann), dt, 3)
+    print("FP32 increment rel L2 %.2e" % err)
     s32.close()
-    assert rel_l2(U32.cpu().numpy(), Uo) < FP32_TOL
 
 
 @pytest.mark.slow

@@ -11,6 +11,8 @@ import pytest
 from oracle import oracle as O
 from paper_2008_04356_gb300 import synth
 
+import fp32_steps as F
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -219,54 +221,111 @@ def test_step_fp64_ragged(sm, N, riemann):
 
 
 def test_step_fp32_vs_oracle(sm):
+    """FP32 steps of the 2 x 4^3 box, N = 5, by increments (see fp32_steps): the smooth
+    entropy wave over 100 steps, whose increment the FP32 storage pins only to its emulated
+    floor of 1.6e-5 (bar 5e-5), and the same flow with seeded noise over 10 steps at 1e-5."""
     p = synth.config_box(N=5, k=4, precision=synth.FP32)
     o = O.Oracle(p)
-    U0 = o.init_state()
     dt = synth.cfl_dt(p)
-    Uo, Go = U0.copy(), np.zeros_like(U0)
-    o.step(Uo, Go, 0.0, dt, 100)
     sol = sm.Solver(p)
-    sol.set_state(U0.astype(np.float32), 0.0)
-    sol.step(dt, 100)
-    Ug, _ = sol.get_state()
-    assert rel_l2(Ug.cpu().numpy(), Uo) < FP32_TOL
+    U0 = o.init_state().astype(np.float32).astype(np.float64)
+    err = F.check_fp32_steps(sol, o, U0, dt, 100, tol=5e-5)
+    print("smooth 100 steps: increment rel L2 %.2e" % err)
+    err = F.check_fp32_steps(sol, o, F.perturbed(o.init_state(), seed=21), dt, 10)
+    print("perturbed 10 steps: increment rel L2 %.2e" % err)
+    sol.close()
 
 
 @pytest.mark.parametrize("N", [3, 5, 7])
 def test_step_fp32_ragged_tiles(sm, N):
     """FP32 steps through the compact interface traces (the stepping path of the interface
     kernel): 37 faces along the sliding direction (4 full tiles and a ragged one), moving
-    block crossing several faces, against the oracle."""
+    block crossing several faces; increments against the oracle (fp32_steps), in two sm_step
+    calls so that both buffer parities of the captured step run."""
     p = ragged_box(N, synth.RUSANOV, ny=37, nz=2, delta0=1.93, v=0.9, prec=synth.FP32)
     o = O.Oracle(p)
-    U0 = o.init_state()
-    dt = synth.cfl_dt(p)
-    Uo, Go = U0.copy(), np.zeros_like(U0)
-    o.step(Uo, Go, 0.0, dt, 6)
     sol = sm.Solver(p)
-    sol.set_state(U0.astype(np.float32), 0.0)
-    sol.step(dt, 6)
-    Ug, _ = sol.get_state()
-    assert rel_l2(Ug.cpu().numpy(), Uo) < FP32_TOL
+    err = F.check_fp32_steps(sol, o, F.perturbed(o.init_state(), seed=30 + N), synth.cfl_dt(p), 6, pieces=[1, 5])
+    print("N=%d: increment rel L2 %.2e" % (N, err))
     sol.close()
 
 
 def test_step_fp32_interface_ring_wraps(sm):
     """More interface tiles than resident CTAs (2 x 4 x 256 x 32 elements, N = 5: 1,024
     tiles of 8 faces), so every CTA of the persistent FP32 interface kernel cycles its
-    three trace buffers; one RK step against the oracle."""
+    three trace buffers; one RK step (first-stage and later-stage element kernels, trace
+    writes, interface kernel on the written traces) by increments against the oracle."""
     p = synth.config_interface_heavy(seed=3, precision=synth.FP32, nz=32)
     o = O.Oracle(p)
-    U0 = o.init_state()
-    dt = synth.cfl_dt(p)
-    Uo, Go = U0.copy(), np.zeros_like(U0)
-    o.step(Uo, Go, 0.0, dt, 1)
     sol = sm.Solver(p)
-    sol.set_state(U0.astype(np.float32), 0.0)
+    err = F.check_fp32_steps(sol, o, F.perturbed(o.init_state(), seed=41), synth.cfl_dt(p), 1)
+    print("increment rel L2 %.2e" % err)
+    sol.close()
+
+
+def near_uniform_state(E, nn, seed, out):
+    """Fills the pinned FP32 tensor out (E, 5, nn) with conservative states drawn uniformly
+    around rho = 1, m = 0, rho e = 2.5 (rho in [0.9, 1.1], m in [-0.1, 0.1]^3, rho e in
+    [2.25, 2.75]): an input generated without the oracle and the CUDA path alike."""
+    lo = np.array([0.9, -0.1, -0.1, -0.1, 2.25])[None, :, None]
+    hi = np.array([1.1, 0.1, 0.1, 0.1, 2.75])[None, :, None]
+    chunk = 16384
+    for e0 in range(0, E, chunk):
+        e1 = min(E, e0 + chunk)
+        vals = synth.uniform(seed, (e1 - e0) * 5 * nn, offset=e0 * 5 * nn).reshape(e1 - e0, 5, nn)
+        out[e0:e1] = torch.from_numpy((lo + (hi - lo) * vals).astype(np.float32))
+
+
+@pytest.mark.slow
+def test_step_fp32_full_size_sampled(sm):
+    """The benchmarked stage-mode launches at full size: 2 x 4 x 256 x 256 elements, N = 5,
+    FP32, one RK step through sm_step (element kernel with the RK update and trace writes,
+    persistent interface kernel on the written traces).  The increment of whole z-slabs is
+    compared with the oracle's FP64 stages, which are run on shrinking slab ranges: the five
+    stages of a step reach at most five elements along z (through faces, the interface and
+    its partner shift), so stage k is evaluated on the slabs within 4 - k of a sampled slab,
+    from a state that is exact on the slabs within 5 - k."""
+    p = synth.config_interface_heavy(seed=1, precision=synth.FP32)
+    E, nn = p.nelem, (p.N + 1) ** 3
+    nx, ny, nz = p.nel_s
+    per_slab = nx * ny
+    Es = E // 2
+    Uh = torch.empty((E, 5, nn), dtype=torch.float32, pin_memory=True)
+    near_uniform_state(E, nn, 17, Uh)
+    dt = synth.cfl_dt(p)
+    sol = sm.Solver(p)
+    sol.set_state(Uh, 0.0)
     sol.step(dt, 1)
     Ug, _ = sol.get_state()
-    assert rel_l2(Ug.cpu().numpy(), Uo) < FP32_TOL
+    torch.cuda.synchronize()
     sol.close()
+    A, B, c = O.lsrk_coeffs()
+    o = O.Oracle(p)
+    for izc in (0, 137):
+        def slab_elems(radius):
+            out = []
+            for blk in (0, 1):
+                for dz in range(-radius, radius + 1):
+                    a = blk * Es + ((izc + dz) % nz) * per_slab
+                    out.append(np.arange(a, a + per_slab))
+            return np.concatenate(out)
+        # a lazily zeroed full-size FP64 state, exact on the slabs within 5 of izc
+        U = np.zeros((E, 5, nn))
+        e5 = slab_elems(5)
+        U[e5] = Uh[torch.from_numpy(e5)].numpy().astype(np.float64)
+        U0c = U[slab_elems(0)].copy()
+        G = np.zeros((E, 5, nn))
+        for k in range(5):
+            ek = slab_elems(4 - k)
+            Ut = o.rhs_elements(U, c[k] * dt, ek)
+            G[ek] = A[k] * G[ek] + dt * Ut
+            U[ek] += B[k] * G[ek]
+        e0 = slab_elems(0)
+        got = Ug[torch.from_numpy(e0).cuda()].cpu().numpy().astype(np.float64)
+        err = F.increment_error(U0c, got, U[e0])
+        print("slab %d: increment rel L2 %.2e" % (izc, err))
+        assert err < F.INCREMENT_TOL
+        assert rel_max(got - U0c, U[e0] - U0c) < 1e-4
 
 
 def test_init_state_matches_oracle(sm):

@@ -10,6 +10,8 @@ import pytest
 from oracle import oracle as O
 from paper_2008_04356_gb300 import synth
 
+import fp32_steps as F
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -113,19 +115,14 @@ def test_periodic_step_fp64_with_rhs_between(sm, N, volume):
 @pytest.mark.parametrize("N", [3, 5, 7])
 def test_periodic_step_fp32_ragged_tiles(sm, N):
     """FP32 steps: 37 faces along the sliding direction (ragged interface tiles), the moving
-    block crossing several faces; both interfaces through the FP32 interface kernel."""
+    block crossing several faces; both interfaces through the FP32 interface kernel; the
+    increments against the oracle (fp32_steps)."""
     p = periodic_box(N, synth.RUSANOV, ny=37, nz=2, delta0=1.93, v=0.9, prec=synth.FP32)
     o = O.Oracle(p)
-    U0 = o.init_state()
-    dt = synth.cfl_dt(p)
-    Uo, Go = U0.copy(), np.zeros_like(U0)
-    o.step(Uo, Go, 0.0, dt, 6)
     sol = sm.Solver(p)
-    sol.set_state(U0.astype(np.float32), 0.0)
-    sol.step(dt, 6)
-    Ug, _ = sol.get_state()
+    err = F.check_fp32_steps(sol, o, F.perturbed(o.init_state(), seed=60 + N), synth.cfl_dt(p), 6, pieces=[2, 4])
+    print("N=%d: increment rel L2 %.2e" % (N, err))
     sol.close()
-    assert rel_l2(Ug.cpu().numpy(), Uo) < FP32_TOL
 
 
 @pytest.mark.parametrize("volume", [synth.VOLUME_WEAK, synth.VOLUME_SPLIT])

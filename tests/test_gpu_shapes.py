@@ -11,6 +11,8 @@ import pytest
 from oracle import oracle as O
 from paper_2008_04356_gb300 import synth
 
+import fp32_steps as F
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -127,11 +129,9 @@ def test_shape_steps(sm, N, shape):
     p32 = copy.deepcopy(p)
     p32.precision = synth.FP32
     s32 = sm.Solver(p32)
-    s32.set_state(U0.astype(np.float32), 0.0)
-    s32.step(dt, 4)
-    U32, _ = s32.get_state()
+    err = F.check_fp32_steps(s32, o, F.perturbed(U0, seed=110 + N), dt, 4)
+    print("FP32 increment rel L2 %.2e" % err)
     s32.close()
-    assert rel_l2(U32.cpu().numpy(), Uo) < FP32_TOL
 
 
 @pytest.mark.parametrize("shape", ["annular", "cone"])

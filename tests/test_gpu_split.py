@@ -13,6 +13,8 @@ import pytest
 from oracle import oracle as O
 from paper_2008_04356_gb300 import synth
 
+import fp32_steps as F
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -131,16 +133,10 @@ def test_split_step_fp64_box_100_steps(sm):
 def test_split_step_fp32_vs_oracle(sm, N):
     p = split_box(N, synth.ROE_HH, ny=37, nz=2, delta0=1.93, v=0.9, prec=synth.FP32)
     o = O.Oracle(p)
-    U0 = o.init_state()
-    dt = synth.cfl_dt(p)
-    Uo, Go = U0.copy(), np.zeros_like(U0)
-    o.step(Uo, Go, 0.0, dt, 20)
     sol = sm.Solver(p)
-    sol.set_state(U0.astype(np.float32), 0.0)
-    sol.step(dt, 20)
-    Ug, _ = sol.get_state()
+    err = F.check_fp32_steps(sol, o, F.perturbed(o.init_state(), seed=120 + N), synth.cfl_dt(p), 20, pieces=[7, 13])
+    print("N=%d: increment rel L2 %.2e" % (N, err))
     sol.close()
-    assert rel_l2(Ug.cpu().numpy(), Uo) < FP32_TOL
 
 
 @pytest.mark.parametrize("N", range(1, 8))

@@ -6,9 +6,11 @@ regions where an allocation (which synchronises the device) is not acceptable, a
 embedders that forbid allocations after start-up.  Its scratch lives in one fixed-size
 device array inside the library, so these tests check that
 
-  * it returns what the ordinary entry point (sm_init_mesh + sm_rhs) returns, on two calls
-    in a row with different problems and inputs (the shared array keeps the previous call's
-    contents, which must never leak into the next result);
+  * it returns what the ordinary entry point (sm_init_mesh + sm_rhs) returns, and what the
+    FP64 oracle returns, on two calls in a row with different problems and inputs (the
+    shared array keeps the previous call's contents, which must never leak into the next
+    result);
+  * once the device is set up, calls leave the device's free memory unchanged;
   * a problem whose scratch would not fit is refused with a clear error.
 
 This file is collected last so that a run stopping at the first failure has already run
@@ -19,6 +21,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2008_04356_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -47,7 +50,8 @@ def _problems():
 
 
 def _close(got, ref, precision):
-    got, ref = got.double().cpu().numpy(), ref.double().cpu().numpy()
+    got = got.double().cpu().numpy()
+    ref = ref if isinstance(ref, np.ndarray) else ref.double().cpu().numpy()
     if precision == synth.FP64:
         return np.abs(got - ref).max() / np.abs(ref).max() < FP64_TOL
     return np.linalg.norm(got - ref) / np.linalg.norm(ref) < FP32_TOL
@@ -58,14 +62,37 @@ def test_static_rhs_matches_sm_rhs_on_two_calls_in_a_row(sm):
     cases = []
     for p, seed, t in ((a, 5, 0.21), (b, 6, 0.05)):
         dt = torch.float64 if p.precision == synth.FP64 else torch.float32
-        dU = torch.from_numpy(synth.random_state(p, seed=seed)).to(dt).cuda()
+        U = synth.random_state(p, seed=seed)
+        dU = torch.from_numpy(U).to(dt).cuda()
         ref = sm.Solver(p).rhs(dU, t)
-        cases.append((p, dU, t, ref))
+        ref_o = O.Oracle(p).rhs(dU.double().cpu().numpy(), t)
+        cases.append((p, dU, t, ref, ref_o))
     # two calls in a row on different problems, then the first again
-    for p, dU, t, ref in cases + cases[:1]:
+    for p, dU, t, ref, ref_o in cases + cases[:1]:
         got = sm.sm_rhs_static(p, dU, t)
         torch.cuda.synchronize()
         assert _close(got, ref, p.precision)
+        assert _close(got, ref_o, p.precision)
+
+
+def test_static_rhs_allocates_nothing(sm):
+    """After a first call per problem (the device's set-up and the kernels' first loads),
+    further calls leave cudaMemGetInfo's free bytes unchanged."""
+    a, b = _problems()
+    cases = []
+    for p, seed in ((a, 15), (b, 16)):
+        dt = torch.float64 if p.precision == synth.FP64 else torch.float32
+        dU = torch.from_numpy(synth.random_state(p, seed=seed)).to(dt).cuda()
+        out = torch.empty_like(dU)
+        sm.sm_rhs_static(p, dU, 0.1, out=out)
+        cases.append((p, dU, out))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        for p, dU, out in cases:
+            sm.sm_rhs_static(p, dU, 0.17, out=out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_static_rhs_refuses_scratch_beyond_its_maximum(sm):
