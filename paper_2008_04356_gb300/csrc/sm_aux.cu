@@ -108,7 +108,31 @@ __global__ void gather_traces_kernel(const MeshDev m, int np, const T* __restric
   }
 }
 
+// FP64 fused multiply-add throughput probe, a measurement aid for the roofline of the FP64
+// path (not part of the method): every thread runs eight independent dependency chains
+// x <- x a + b for iters rounds (2 flop per link) and stores their sum so that none is
+// removed.  With a = 1 - 1e-7, b = 1e-7 the chains stay near 1.
+__global__ void fp64_fma_probe_kernel(const int iters, const double a, const double b, double* __restrict__ out) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1.0 + 1e-3 * (threadIdx.x + 8 * k);
+#pragma unroll 4
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
+
+cudaError_t launch_fp64_fma_probe(int blocks, int threads, int iters, double* out, cudaStream_t st) {
+  fp64_fma_probe_kernel<<<blocks, threads, 0, st>>>(iters, 1.0 - 1e-7, 1e-7, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gather_traces(int N, int prec, const MeshDev& m, const void* U, void* Ts, void* Tm, cudaStream_t st,
                                  int ifc) {

@@ -111,6 +111,7 @@ cudaError_t prepare_interface(int N, int prec);
 
 // sm_aux.cu: initial data, reductions
 cudaError_t launch_init_state(int N, int prec, const MeshDev& m, void* U, cudaStream_t st);
+cudaError_t launch_fp64_fma_probe(int blocks, int threads, int iters, double* out, cudaStream_t st);
 cudaError_t launch_totals(int N, int prec, const MeshDev& m, const void* U, double* partial, int nblk,
                           double* out5, cudaStream_t st);
 cudaError_t launch_face_sums(int N, int prec, const MeshDev& m, const void* F, double* partial, int nblk,

@@ -5,7 +5,9 @@
 // resident solves.  Every iteration advances all resident solves together by the same
 // number of RK steps (FP32 Euler plane-interface solves through one batch with shared
 // launches, the others one at a time), at most a few steps so that new arrivals join
-// quickly, then retires the finished ones and frees their memory.  Built on the library's
+// quickly, then retires the finished ones and frees their memory.  A solve's time to
+// solution ends at a CUDA event recorded right after its last step, mapped onto the host
+// clock through an anchor event recorded when the worker starts.  Built on the library's
 // own C-ABI.
 #include <algorithm>
 #include <atomic>
@@ -34,6 +36,8 @@ struct Job {
   sm_solver* solver = nullptr;
   size_t bytes = 0;
   int remaining = 0;
+  cudaEvent_t done_ev = nullptr;   // recorded after the solve's last step
+  bool done_recorded = false;
   std::vector<unsigned char> state;
 };
 
@@ -73,6 +77,8 @@ struct sm_server {
   sm_server_stats_out stats;
   sm_batch* batch = nullptr;
   bool batch_dirty = true;
+  cudaEvent_t anchor = nullptr;    // recorded (and waited for) when the worker starts
+  double anchor_host = 0.0;        // host-clock time of the anchor event
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -82,7 +88,14 @@ struct sm_server {
 };
 
 void sm_server::finish(Job* j, int status, cudaStream_t st) {
-  j->res.t_done = now();
+  // time to solution: the event after the last step on the device clock, else the host clock
+  float ms = 0.0f;
+  if (status == SM_OK && j->done_recorded && anchor && cudaEventElapsedTime(&ms, anchor, j->done_ev) == cudaSuccess)
+    j->res.t_done = anchor_host + 1e-3 * (double)ms;
+  else
+    j->res.t_done = now();
+  if (j->done_ev) cudaEventDestroy(j->done_ev);
+  j->done_ev = nullptr;
   if (status == SM_OK && j->solver) {
     sm_diag_out d;
     int rc = sm_diag(j->solver, &d, (void*)st);
@@ -120,6 +133,13 @@ void sm_server::run() {
   cudaSetDevice(device);
   cudaStream_t st = nullptr;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (cudaEventCreate(&anchor) == cudaSuccess && cudaEventRecord(anchor, st) == cudaSuccess &&
+      cudaEventSynchronize(anchor) == cudaSuccess) {
+    anchor_host = now();
+  } else {
+    if (anchor) cudaEventDestroy(anchor);
+    anchor = nullptr;
+  }
   double busy_since = -1.0;
   while (!stop.load()) {
     std::vector<Job*> admit;
@@ -147,6 +167,7 @@ void sm_server::run() {
       int rc = sm_init_mesh(&j->req.desc, &j->solver);
       if (rc == SM_OK) rc = sm_set_motion(j->solver, &j->req.motion);
       if (rc == SM_OK) rc = sm_init_state(j->solver, (void*)st);
+      if (rc == SM_OK && cudaEventCreate(&j->done_ev) != cudaSuccess) { j->done_ev = nullptr; rc = SM_ERR_CUDA; }
       if (rc != SM_OK) { finish(j, rc, st); continue; }
       active.push_back(j);
       batch_dirty = true;
@@ -184,9 +205,15 @@ void sm_server::run() {
     int rc = SM_OK;
     if (k > 0) {
       if (batch) rc = sm_batch_step(batch, k, (void*)st);
+      // the batched solves that take their last step here end with this launch sequence
       for (Job* j : active)
-        if (rc == SM_OK && !batchable(j->req.desc))
+        if (rc == SM_OK && batchable(j->req.desc) && j->remaining == k)
+          j->done_recorded = cudaEventRecord(j->done_ev, st) == cudaSuccess;
+      for (Job* j : active)
+        if (rc == SM_OK && !batchable(j->req.desc)) {
           rc = sm_step(j->solver, j->req.dt, k, (void*)st);
+          if (rc == SM_OK && j->remaining == k) j->done_recorded = cudaEventRecord(j->done_ev, st) == cudaSuccess;
+        }
       if (rc == SM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SM_ERR_CUDA;
       std::lock_guard<std::mutex> lk(mu);
       stats.batched_steps += k;
@@ -209,8 +236,12 @@ void sm_server::run() {
   for (Job* j : active) {
     if (j->solver) sm_destroy(j->solver);
     j->solver = nullptr;
+    if (j->done_ev) cudaEventDestroy(j->done_ev);
+    j->done_ev = nullptr;
   }
   active.clear();
+  if (anchor) cudaEventDestroy(anchor);
+  anchor = nullptr;
   if (st) cudaStreamDestroy(st);
 }
 

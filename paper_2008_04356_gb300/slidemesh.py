@@ -78,6 +78,7 @@ _SIGS = {
     "sm_rhs_static": (C.c_int, [C.POINTER(SmMeshDesc), C.POINTER(SmMotion), C.c_double, _vp, _vp, _vp]),
     "sm_map": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, _vp, _vp, _vp, _vp]),
     "sm_mortar_matrices": (C.c_int, [C.c_int, C.c_double, _vp, _vp]),
+    "sm_fp64_fma_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "sm_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(C.c_double), C.c_int, C.POINTER(_vp)]),
     "sm_batch_autotune": (C.c_int, [_vp, _vp]),
     "sm_batch_step": (C.c_int, [_vp, C.c_int, _vp]),
@@ -176,6 +177,15 @@ def sm_rhs_static(problem: synth.Problem, dU, t: float, out=None, stream=None):
     mo = SmMotion(float(problem.v), 0.0, float(problem.delta0))
     check(lib().sm_rhs_static(C.byref(desc), C.byref(mo), float(t), dU.data_ptr(), out.data_ptr(),
                               _stream(stream)), "sm_rhs_static")
+    return out
+
+
+def sm_fp64_fma_probe(blocks: int, threads: int, iters: int, out, stream=None):
+    """Launches the FP64 FMA throughput probe (16 * iters * blocks * threads flop) on the
+    stream; out: a cuda float64 tensor of blocks * threads elements."""
+    assert out.is_cuda and out.numel() >= blocks * threads
+    check(lib().sm_fp64_fma_probe(int(blocks), int(threads), int(iters), out.data_ptr(), _stream(stream)),
+          "sm_fp64_fma_probe")
     return out
 
 
