@@ -187,18 +187,21 @@ int sm_get_state(sm_solver* s, void* U, int on_device, double* t, void* stream);
 /* dU/dt = R(U, t) for a caller-owned device state dU into caller-owned dUt (same layout
  * and precision), on stream: mapper and mortar matrices at time t (Sec. 4.3, 3.2), the
  * fused interface kernel (Sec. 3.3 steps 3-5), then volume + surface (Sec. 3.1).
- * dU and dUt must not overlap.  The solver's own state is not touched. */
+ * dU and dUt must not overlap and must be 16-byte aligned (as cudaMalloc and PyTorch
+ * allocations are; the kernels move them in 8- and 16-byte vectors), else SM_ERR_ARG before
+ * any launch.  The solver's own state is not touched. */
 int sm_rhs(sm_solver* s, double t, const void* dU, void* dUt, void* stream);
 
 /* The interface operator alone (Sec. 3.3 steps 1-5) for the device state dU at time t:
  * writes both sides' face fluxes (layout above, 5 (N+1)^2 scalars per face) into the
- * caller-owned device arrays dF_static and dF_moving. */
+ * caller-owned device arrays dF_static and dF_moving.  All three 16-byte aligned (else
+ * SM_ERR_ARG). */
 int sm_interface(sm_solver* s, double t, const void* dU, void* dF_static, void* dF_moving, void* stream);
 
 /* Navier-Stokes solvers: the BR1-lifted gradients (Sec. 3.1) of the primitive variables
  * (rho, v1, v2, v3, p) of the device state dU at time t, into caller-owned dGrad laid out
  * [e][axis][primitive][k][j][i] (axis x, y, z), solver precision.  SM_ERR_ARG for an Euler
- * solver. */
+ * solver or arrays that are not 16-byte aligned. */
 int sm_gradients(sm_solver* s, double t, const void* dU, void* dGrad, void* stream);
 
 /* Advances the solver state by nsteps low-storage RK4 steps of size dt (five stages each,
@@ -232,7 +235,8 @@ void sm_destroy(sm_solver* s);
  * parameters, both sides' interface face fluxes) lives in one fixed 16 MiB device array
  * inside the library, and the LGL basis tables of N = 1..7 in a second fixed array; every
  * GPU that loads the library holds both until the process exits.  The caller owns dU and
- * dUt (device pointers, the solver layout and precision of desc, not overlapping).
+ * dUt (device pointers, the solver layout and precision of desc, not overlapping, 16-byte
+ * aligned; SM_ERR_ARG otherwise, before any CUDA call).
  * Plane interface, Euler, weak form, one interface (SM_ERR_UNSUPPORTED otherwise).
  *  - Sizes: the scratch needed is about 2 * faces * 5 (N+1)^2 * bytes-per-scalar plus
  *    ~10 KB (faces = nel_static[1] * nel_static[2]); larger problems are rejected with

@@ -18,6 +18,14 @@
 // p, H) / 2 and, per direction, the halved (Ja^d, Ja^d . v^g) / 2 in shared memory, so that a
 // mean is one addition; after a barrier every thread sums the two-point fluxes of the three
 // lines through its node.
+//
+// Navier-Stokes (PHYS 1, the paper's production scheme: split form with BR1): the advective
+// terms as above, the viscous terms in the weak form of the curved weak-form kernel (the
+// contravariant viscous fluxes Ja^d . F^v of the lifted gradients, contracted with Dhat), and
+// the face flux minus the BR1 mean of both sides' viscous fluxes, so that the own-flux
+// correction in Ds is the advective flux only:
+//   J dU/dt = -[ sum_d sum_l Ds_il F~#^d(U_i, U_l) ] + sum_d sum_l Dhat_il Ja^d . F^v(U_l, grad_l)
+//             - (1 / w_0) ((F*_adv - {{F^v}}) . N sJ) at face nodes.
 #pragma once
 
 #include "sm_curved.cuh"
@@ -32,18 +40,19 @@ template <int N> struct CurvedSplitCfg {
 #else
   template <typename T> __host__ __device__ static constexpr int minb() { return sizeof(T) == 4 && N == 7 ? 2 : 1; }
 #endif
-  template <typename T> static constexpr size_t smem_bytes() {
-    // primitives, metric quadruples per direction, face fluxes, the Ds table
-    return sizeof(T) * (size_t)(EPB * 6 * NN + EPB * 12 * NN + EPB * 30 * NP2 + NP * NP);
+  template <typename T, int PHYS = 0> static constexpr size_t smem_bytes() {
+    // primitives, metric quadruples per direction, face fluxes, the Ds table (PHYS 1: the
+    // contravariant viscous fluxes)
+    return sizeof(T) * (size_t)(EPB * 6 * NN + EPB * 12 * NN + EPB * 30 * NP2 + NP * NP + (PHYS ? EPB * 15 * NN : 0));
   }
 };
 
-template <int N, typename T, int RIEM, int MODE>
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
 __device__ __forceinline__ void curved_split_block(const MeshDev& m, const StageParams* __restrict__ sp,
                                                    const T* __restrict__ U, T* __restrict__ out,
                                                    T* __restrict__ G, const T* __restrict__ Fs,
                                                    const T* __restrict__ Fm, const T rkA, const T rkB,
-                                                   const T dt, const long long e0) {
+                                                   const T dt, const long long e0, const T* __restrict__ Gr = nullptr) {
   using C = CurvedSplitCfg<N>;
   constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -51,6 +60,7 @@ __device__ __forceinline__ void curved_split_block(const MeshDev& m, const Stage
   T* sM = sQ + EPB * 6 * NN;                     // [EPB][3][4][NN] halved (Ja^d, Ja^d . v^g)
   T* sS = sM + EPB * 12 * NN;                    // [EPB][6][5][NP2] outward face fluxes
   T* sD = sS + EPB * 30 * NP2;                   // [NP][NP] Ds
+  T* sW = sD + NP * NP;                          // PHYS 1: [EPB][3][5][NN] -Ja^d . F^v
   const T* c = Prec<T>::c(m);
   const T* geo = reinterpret_cast<const T*>(m.geo);
   const int tid = threadIdx.x;
@@ -90,11 +100,32 @@ __device__ __forceinline__ void curved_split_block(const MeshDev& m, const Stage
       for (int a = 0; a < 3; ++a) M[(4 * d + a) * NN] = T(0.5) * ge[(3 * d + a) * NN];
       M[(4 * d + 3) * NN] = T(0.5) * vs * ge[(10 + d) * NN];
     }
+    if (PHYS) {
+      // the viscous fluxes of the lifted gradients (turned into the element's frame) along
+      // the axes, contracted with each direction's metric vector, negated
+      T gn[15], fv[3][5];
+#pragma unroll
+      for (int kk = 0; kk < 15; ++kk) gn[kk] = Gr[(e * 15 + kk) * NN + nd];
+      rotate_grad_z(gn, fc, -fs);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) viscous_flux_axis(ub, gn, a, c, fv[a]);
+      T* W = sW + le * 15 * NN + nd;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T J0 = ge[(3 * d) * NN], J1 = ge[(3 * d + 1) * NN], J2 = ge[(3 * d + 2) * NN];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) W[(5 * d + v) * NN] = -(J0 * fv[0][v] + J1 * fv[1][v] + J2 * fv[2][v]);
+      }
+    }
   }
 
-  curved_face_fluxes<N, T, RIEM, 0>(m, sp, U, Fs, Fm, nullptr, e0, sS, tid);
+  curved_face_fluxes<N, T, RIEM, PHYS>(m, sp, U, Fs, Fm, Gr, e0, sS, tid);
 
   __syncthreads();
+  if (PHYS) {
+    contract_lines_inplace<N, T>(sW, tid);
+    __syncthreads();
+  }
   if (!active) return;
   const int i = nd % NP, j = (nd / NP) % NP, k = nd / NP2;
   const T* Qe = sQ + le * 6 * NN;
@@ -128,53 +159,59 @@ __device__ __forceinline__ void curved_split_block(const MeshDev& m, const Stage
       acc[4] += dil * (fr * hm + pm * vm);
     }
   }
+  if (PHYS) {
+    const T* W = sW + le * 15 * NN + nd;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] += W[v * NN] + W[(5 + v) * NN] + W[(10 + v) * NN];
+  }
   curved_surface_update<N, T, MODE>(m, sS + le * 30 * NP2, acc, nd, e, base, u, g, fc, fs, out, G, rkA, rkB, dt);
 }
 
 namespace {
 
-template <int N, typename T, int RIEM, int MODE>
-__global__ void __launch_bounds__(ElemCfg<N>::THREADS, CurvedSplitCfg<N>::template minb<T>())
+template <int N, typename T, int RIEM, int MODE, int PHYS>
+__global__ void __launch_bounds__(ElemCfg<N>::THREADS, PHYS ? 1 : CurvedSplitCfg<N>::template minb<T>())
 curved_split_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
                     T* __restrict__ out, T* __restrict__ G, const T* __restrict__ Fs, const T* __restrict__ Fm,
-                    const T rkA, const T rkB, const T dt) {
-  curved_split_block<N, T, RIEM, MODE>(m, sp, U, out, G, Fs, Fm, rkA, rkB, dt,
-                                       (long long)blockIdx.x * ElemCfg<N>::EPB);
+                    const T rkA, const T rkB, const T dt, const T* __restrict__ Gr) {
+  curved_split_block<N, T, RIEM, MODE, PHYS>(m, sp, U, out, G, Fs, Fm, rkA, rkB, dt,
+                                             (long long)blockIdx.x * ElemCfg<N>::EPB, Gr);
 }
 
-template <int N, typename T, int RIEM, int MODE>
+template <int N, typename T, int RIEM, int MODE, int PHYS>
 cudaError_t launch_cs(const ElemArgs& a, cudaStream_t st) {
   using C = CurvedSplitCfg<N>;
   const long long blocks = (a.m.E + C::EPB - 1) / C::EPB;
   if (blocks <= 0) return cudaSuccess;
-  curved_split_kernel<N, T, RIEM, MODE><<<(unsigned)blocks, C::THREADS, C::template smem_bytes<T>(), st>>>(
-      a.m, a.sp, (const T*)a.U, (T*)a.out, (T*)a.G, (const T*)a.Fs, (const T*)a.Fm, (T)a.rkA, (T)a.rkB, (T)a.dt);
+  curved_split_kernel<N, T, RIEM, MODE, PHYS><<<(unsigned)blocks, C::THREADS, C::template smem_bytes<T, PHYS>(), st>>>(
+      a.m, a.sp, (const T*)a.U, (T*)a.out, (T*)a.G, (const T*)a.Fs, (const T*)a.Fm, (T)a.rkA, (T)a.rkB, (T)a.dt,
+      (const T*)a.Gr);
   return cudaGetLastError();
 }
 
-template <int N, typename T, int RIEM, int MODE>
+template <int N, typename T, int RIEM, int MODE, int PHYS>
 cudaError_t prepare_cs() {
-  return cudaFuncSetAttribute(curved_split_kernel<N, T, RIEM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)CurvedSplitCfg<N>::template smem_bytes<T>());
+  return cudaFuncSetAttribute(curved_split_kernel<N, T, RIEM, MODE, PHYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)CurvedSplitCfg<N>::template smem_bytes<T, PHYS>());
 }
 
-template <int N, typename T>
+template <int N, typename T, int PHYS = 0>
 cudaError_t launch_cs_n(int riemann, int mode, const ElemArgs& a, cudaStream_t st) {
   if (riemann == 0) {
-    if (mode == ELEM_RHS) return launch_cs<N, T, 0, ELEM_RHS>(a, st);
-    if (mode == ELEM_STAGE) return launch_cs<N, T, 0, ELEM_STAGE>(a, st);
-    return launch_cs<N, T, 0, ELEM_STAGE_FIRST>(a, st);
+    if (mode == ELEM_RHS) return launch_cs<N, T, 0, ELEM_RHS, PHYS>(a, st);
+    if (mode == ELEM_STAGE) return launch_cs<N, T, 0, ELEM_STAGE, PHYS>(a, st);
+    return launch_cs<N, T, 0, ELEM_STAGE_FIRST, PHYS>(a, st);
   }
-  if (mode == ELEM_RHS) return launch_cs<N, T, 1, ELEM_RHS>(a, st);
-  if (mode == ELEM_STAGE) return launch_cs<N, T, 1, ELEM_STAGE>(a, st);
-  return launch_cs<N, T, 1, ELEM_STAGE_FIRST>(a, st);
+  if (mode == ELEM_RHS) return launch_cs<N, T, 1, ELEM_RHS, PHYS>(a, st);
+  if (mode == ELEM_STAGE) return launch_cs<N, T, 1, ELEM_STAGE, PHYS>(a, st);
+  return launch_cs<N, T, 1, ELEM_STAGE_FIRST, PHYS>(a, st);
 }
 
-template <int N, typename T>
+template <int N, typename T, int PHYS = 0>
 cudaError_t prepare_cs_n() {
-  cudaError_t r[6] = {prepare_cs<N, T, 0, ELEM_RHS>(), prepare_cs<N, T, 0, ELEM_STAGE>(),
-                      prepare_cs<N, T, 0, ELEM_STAGE_FIRST>(), prepare_cs<N, T, 1, ELEM_RHS>(),
-                      prepare_cs<N, T, 1, ELEM_STAGE>(), prepare_cs<N, T, 1, ELEM_STAGE_FIRST>()};
+  cudaError_t r[6] = {prepare_cs<N, T, 0, ELEM_RHS, PHYS>(), prepare_cs<N, T, 0, ELEM_STAGE, PHYS>(),
+                      prepare_cs<N, T, 0, ELEM_STAGE_FIRST, PHYS>(), prepare_cs<N, T, 1, ELEM_RHS, PHYS>(),
+                      prepare_cs<N, T, 1, ELEM_STAGE, PHYS>(), prepare_cs<N, T, 1, ELEM_STAGE_FIRST, PHYS>()};
   for (cudaError_t e : r)
     if (e != cudaSuccess) return e;
   return cudaSuccess;

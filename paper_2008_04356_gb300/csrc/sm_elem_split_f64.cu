@@ -2,9 +2,9 @@
 #include "sm_split.cuh"
 
 cudaError_t launch_element_split_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st) {
-  SM_SPLIT_DISPATCH(double, N, riemann, mode, a, st)
+  SM_SPLIT_DISPATCH(double, N, riemann, mode, a, st, 0)
 }
 
-cudaError_t prepare_element_split_f64(int N) { SM_SPLIT_PREPARE(double, N) }
+cudaError_t prepare_element_split_f64(int N) { SM_SPLIT_PREPARE(double, N, 0) }
 
 cudaError_t upload_dsplit_f64(const float* f, const double* d) { return upload_dsplit_here(f, d); }

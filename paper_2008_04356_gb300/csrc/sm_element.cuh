@@ -108,10 +108,10 @@ template <> __device__ __forceinline__ double dhat_c<double>(int n, int idx) { r
 // The three flux arrays of an element are in node order [v][k][j][i]: xi^1 lines are
 // contiguous (vector accesses), xi^2 and xi^3 lines have strides NP and NP^2 and are
 // numbered so that consecutive lanes take consecutive words (no bank conflicts).
-template <int N, typename T>
+template <int N, typename T, int EPB = ElemCfg<N>::EPB, int THREADS = ElemCfg<N>::THREADS>
 __device__ __forceinline__ void contract_lines_inplace(T* sF, int tid) {
   using C = ElemCfg<N>;
-  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, EPB = C::EPB, THREADS = C::THREADS;
+  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN;
   for (int w = tid; w < EPB * 5 * NP2; w += THREADS) {
     const int l2 = w / (5 * NP2);
     const int rr = w - l2 * 5 * NP2;

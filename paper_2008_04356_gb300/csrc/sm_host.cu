@@ -349,6 +349,8 @@ cudaError_t ensure_dhat_constants() {
       fs[n - 1][k] = (float)b.Dsplit[k];
     }
   }
+  if ((e = upload_split_ns_constants_f32(&f[0][0], &d[0][0], &fs[0][0], &ds[0][0])) != cudaSuccess) return e;
+  if ((e = upload_split_ns_constants_f64(&f[0][0], &d[0][0], &fs[0][0], &ds[0][0])) != cudaSuccess) return e;
   if ((e = upload_dsplit_f32(&fs[0][0], &ds[0][0])) != cudaSuccess) return e;
   if ((e = upload_dsplit_f64(&fs[0][0], &ds[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
@@ -360,6 +362,8 @@ cudaError_t ensure_dhat_constants() {
   if ((e = upload_dhat_curved_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_curved_ns_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   if ((e = upload_dhat_curved_ns_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_curved_split_ns_f32(&f[0][0], &d[0][0])) != cudaSuccess) return e;
+  if ((e = upload_dhat_curved_split_ns_f64(&f[0][0], &d[0][0])) != cudaSuccess) return e;
   g_dhat_done[dev] = true;
   return cudaSuccess;
 }
@@ -410,6 +414,9 @@ struct sm_solver {
 namespace {
 
 bool is_ns(const sm_solver* s) { return s->desc.physics == SM_NAVIER_STOKES; }
+
+// Caller device arrays are read and written with 8- and 16-byte vector accesses.
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 // After the stage parameters: everything the element kernel reads besides U.  Navier-Stokes:
 // lifting face values on the interface, the lifted gradients, then the interface fluxes with
@@ -477,6 +484,11 @@ cudaError_t enqueue_rhs_parts(sm_solver* s, double t, const void* dU, void* Fs, 
 
 cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a0, cudaStream_t st) {
   ElemArgs a = a0;
+  if (s->m.geom != 0 && is_ns(s) && s->desc.volume == SM_VOLUME_SPLIT) {
+    a.Gr = s->Gr;
+    return s->prec == SM_FP64 ? launch_curved_split_ns_f64(s->N, s->desc.riemann, mode, a, st)
+                              : launch_curved_split_ns_f32(s->N, s->desc.riemann, mode, a, st);
+  }
   if (s->m.geom != 0 && is_ns(s)) {
     a.Gr = s->Gr;
     return s->prec == SM_FP64 ? launch_curved_element_ns_f64(s->N, s->desc.riemann, mode, a, st)
@@ -488,6 +500,11 @@ cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a0, cudaStream_t
   if (s->m.geom != 0)
     return s->prec == SM_FP64 ? launch_curved_element_f64(s->N, s->desc.riemann, mode, a, st)
                               : launch_curved_element_f32(s->N, s->desc.riemann, mode, a, st);
+  if (is_ns(s) && s->desc.volume == SM_VOLUME_SPLIT) {
+    a.Gr = s->Gr;
+    return s->prec == SM_FP64 ? launch_element_split_ns_f64(s->N, s->desc.riemann, mode, a, st)
+                              : launch_element_split_ns_f32(s->N, s->desc.riemann, mode, a, st);
+  }
   if (is_ns(s)) {
     a.Gr = s->Gr;
     return s->prec == SM_FP64 ? launch_element_ns_f64(s->N, s->desc.riemann, mode, a, st)
@@ -591,8 +608,6 @@ int valid_desc(const sm_mesh_desc* d) {
   if (d->physics == SM_NAVIER_STOKES && !(d->mu >= 0.0 && d->Pr > 0.0 && d->Rgas > 0.0))
     return fail(SM_ERR_ARG, "Navier-Stokes needs mu >= 0, Pr > 0, Rgas > 0");
   if (d->volume != SM_VOLUME_WEAK && d->volume != SM_VOLUME_SPLIT) return fail(SM_ERR_ARG, "unknown volume integral");
-  if (d->volume == SM_VOLUME_SPLIT && d->physics != SM_EULER)
-    return fail(SM_ERR_UNSUPPORTED, "the split-form volume integral takes Euler physics");
   if (d->periodic_x != 0 && d->periodic_x != 1) return fail(SM_ERR_ARG, "periodic_x must be 0 or 1");
   if (d->periodic_x && (d->geom != SM_GEOM_PLANE || d->physics != SM_EULER))
     return fail(SM_ERR_UNSUPPORTED, "the second sliding interface (periodic x) takes the plane geometry and Euler physics");
@@ -761,6 +776,9 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   else if (desc->volume == SM_VOLUME_SPLIT &&
            (e = (s->prec == SM_FP64 ? prepare_element_split_f64(s->N) : prepare_element_split_f32(s->N))) != cudaSuccess)
     what = "split-form kernel attributes";
+  else if (desc->volume == SM_VOLUME_SPLIT && desc->physics == SM_NAVIER_STOKES && desc->geom == SM_GEOM_PLANE &&
+           (e = (s->prec == SM_FP64 ? prepare_element_split_ns_f64(s->N) : prepare_element_split_ns_f32(s->N))) != cudaSuccess)
+    what = "split-form Navier-Stokes kernel attributes";
   else if ((e = ensure_dhat_constants()) != cudaSuccess) what = "derivative constants";
   else if ((e = prepare_interface(s->N, s->prec)) != cudaSuccess) what = "interface kernel attributes";
   else if (desc->geom != SM_GEOM_PLANE &&
@@ -772,6 +790,9 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   else if (desc->geom != SM_GEOM_PLANE && desc->physics == SM_NAVIER_STOKES &&
            (e = (s->prec == SM_FP64 ? prepare_curved_ns_f64(s->N) : prepare_curved_ns_f32(s->N))) != cudaSuccess)
     what = "curvilinear Navier-Stokes kernel attributes";
+  else if (desc->geom != SM_GEOM_PLANE && desc->physics == SM_NAVIER_STOKES && desc->volume == SM_VOLUME_SPLIT &&
+           (e = (s->prec == SM_FP64 ? prepare_curved_split_ns_f64(s->N) : prepare_curved_split_ns_f32(s->N))) != cudaSuccess)
+    what = "curvilinear split-form Navier-Stokes kernel attributes";
   else if (desc->physics == SM_NAVIER_STOKES &&
            ((e = (s->prec == SM_FP64 ? prepare_ns_f64(s->N) : prepare_ns_f32(s->N))) != cudaSuccess ||
             (e = prepare_interface_ns(s->N, s->prec)) != cudaSuccess)) what = "Navier-Stokes kernel attributes";
@@ -851,6 +872,7 @@ int sm_get_state(sm_solver* s, void* U, int on_device, double* t, void* stream) 
 int sm_rhs(sm_solver* s, double t, const void* dU, void* dUt, void* stream) {
   if (!s || !dU || !dUt) return fail(SM_ERR_ARG, "NULL argument");
   if (dU == dUt) return fail(SM_ERR_ARG, "dU and dUt must not overlap");
+  if (!aligned16(dU) || !aligned16(dUt)) return fail(SM_ERR_ARG, "device arrays must be 16-byte aligned");
   if (!std::isfinite(t)) return fail(SM_ERR_ARG, "non-finite time");
   cudaStream_t st = (cudaStream_t)stream;
   SM_CK(enqueue_rhs_parts(s, t, dU, s->Fs, s->Fm, st), "stage params / interface");
@@ -861,6 +883,8 @@ int sm_rhs(sm_solver* s, double t, const void* dU, void* dUt, void* stream) {
 
 int sm_interface(sm_solver* s, double t, const void* dU, void* dFs, void* dFm, void* stream) {
   if (!s || !dU || !dFs || !dFm) return fail(SM_ERR_ARG, "NULL argument");
+  if (!aligned16(dU) || !aligned16(dFs) || !aligned16(dFm))
+    return fail(SM_ERR_ARG, "device arrays must be 16-byte aligned");
   if (s->desc.interface_conforming) return fail(SM_ERR_ARG, "the interface is conforming");
   if (!std::isfinite(t)) return fail(SM_ERR_ARG, "non-finite time");
   SM_CK(enqueue_rhs_parts(s, t, dU, dFs, dFm, (cudaStream_t)stream), "interface");
@@ -869,6 +893,7 @@ int sm_interface(sm_solver* s, double t, const void* dU, void* dFs, void* dFm, v
 
 int sm_gradients(sm_solver* s, double t, const void* dU, void* dGrad, void* stream) {
   if (!s || !dU || !dGrad) return fail(SM_ERR_ARG, "NULL argument");
+  if (!aligned16(dU) || !aligned16(dGrad)) return fail(SM_ERR_ARG, "device arrays must be 16-byte aligned");
   if (!is_ns(s)) return fail(SM_ERR_ARG, "gradients are lifted for Navier-Stokes solvers only");
   if (!std::isfinite(t)) return fail(SM_ERR_ARG, "non-finite time");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1383,6 +1408,7 @@ extern "C" int sm_rhs_static(const sm_mesh_desc* desc, const sm_motion* motion, 
   if (desc->periodic_x) return fail(SM_ERR_UNSUPPORTED, "sm_rhs_static computes one sliding interface only");
   if (!motion || !dU || !dUt) return fail(SM_ERR_ARG, "NULL argument");
   if (dU == dUt) return fail(SM_ERR_ARG, "dU and dUt must not overlap");
+  if (!aligned16(dU) || !aligned16(dUt)) return fail(SM_ERR_ARG, "device arrays must be 16-byte aligned");
   if (motion->omega != 0.0) return fail(SM_ERR_UNSUPPORTED, "rotation needs a rotating geometry");
   if (!std::isfinite(motion->v) || !std::isfinite(motion->delta0) || !std::isfinite(t))
     return fail(SM_ERR_ARG, "non-finite motion or time");

@@ -41,6 +41,14 @@ cudaError_t launch_curved_split_f32(int N, int riemann, int mode, const ElemArgs
 cudaError_t launch_curved_split_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
 cudaError_t prepare_curved_split_f32(int N);
 cudaError_t prepare_curved_split_f64(int N);
+// sm_curved_split_ns_f32.cu / sm_curved_split_ns_f64.cu: the same with Navier-Stokes physics
+// (advective terms split, viscous terms weak, BR1 lifted gradients a.Gr)
+cudaError_t launch_curved_split_ns_f32(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t launch_curved_split_ns_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t prepare_curved_split_ns_f32(int N);
+cudaError_t prepare_curved_split_ns_f64(int N);
+cudaError_t upload_dhat_curved_split_ns_f32(const float* f, const double* d);
+cudaError_t upload_dhat_curved_split_ns_f64(const float* f, const double* d);
 cudaError_t prepare_curved_f64(int N);
 cudaError_t upload_dhat_curved_f32(const float* f, const double* d);
 cudaError_t upload_dhat_curved_f64(const float* f, const double* d);
@@ -72,6 +80,15 @@ cudaError_t launch_element_split_f32(int N, int riemann, int mode, const ElemArg
 cudaError_t launch_element_split_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
 cudaError_t prepare_element_split_f32(int N);
 cudaError_t prepare_element_split_f64(int N);
+// sm_elem_split_ns_f32.cu / sm_elem_split_ns_f64.cu: the split form with Navier-Stokes physics
+// (advective terms split, viscous terms weak, BR1 lifted gradients a.Gr)
+cudaError_t launch_element_split_ns_f32(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t launch_element_split_ns_f64(int N, int riemann, int mode, const ElemArgs& a, cudaStream_t st);
+cudaError_t prepare_element_split_ns_f32(int N);
+cudaError_t prepare_element_split_ns_f64(int N);
+// their constant memory: the Dhat tables (viscous terms) and the Ds tables (advective terms)
+cudaError_t upload_split_ns_constants_f32(const float* dhf, const double* dhd, const float* dsf, const double* dsd);
+cudaError_t upload_split_ns_constants_f64(const float* dhf, const double* dhd, const float* dsf, const double* dsd);
 // constant-memory Ds = 2 D - M^-1 B tables of the split kernels ([7][64], N = 1..7)
 cudaError_t upload_dsplit_f32(const float* f, const double* d);
 cudaError_t upload_dsplit_f64(const float* f, const double* d);

@@ -25,6 +25,16 @@
 // line's primitives in registers, evaluate the NP (NP - 1) / 2 pair fluxes once and
 // accumulate both ends; after a second barrier every node sums its three directions with
 // the metric terms and applies the surface integral and the RK update.
+//
+// Navier-Stokes (PHYS 1; the paper's production scheme, split form with BR1): the advective
+// terms take the split form above, the viscous terms keep the weak form of the weak-form
+// kernel, and the face flux is the Riemann flux minus the BR1 mean of both sides' viscous
+// fluxes, so that the own-flux correction folded into Ds is the advective flux only:
+//   J dU/dt = -[ sum_d |Ja^d| sum_l Ds_il F#^d(U_i, U_l) ] + sum_d |Ja^d| sum_l Dhat_il F^v_d(U_l, grad_l)
+//             - (1 / w_0) ((F*_adv - {{F^v}}) . N sJ) at face nodes,
+// with the lifted gradients of the BR1 lifting kernel.  Every node stores its viscous fluxes
+// negated in a third shared array, whose lines are contracted with Dhat beside the split
+// lines.
 #pragma once
 
 #include "sm_element.cuh"
@@ -41,8 +51,8 @@ template <int N> struct SplitCfg {
 #else
   static constexpr int MINB = N <= 2 ? 2 : (N == 7 ? 1 : (N == 6 ? 2 : (N == 5 ? 5 : 3)));
 #endif
-  template <typename T> static constexpr size_t smem_bytes() {
-    return sizeof(T) * (size_t)(EPB * 6 * NN + EPB * 15 * NN + EPB * 30 * NP2);
+  template <typename T, int PHYS = 0> static constexpr size_t smem_bytes() {
+    return sizeof(T) * (size_t)(EPB * 6 * NN + EPB * 15 * NN + EPB * 30 * NP2 + (PHYS ? EPB * 15 * NN : 0));
   }
 };
 
@@ -154,18 +164,19 @@ __device__ __forceinline__ void split_volume_lines(const MeshDev& m, const T* sQ
   }
 }
 
-template <int N, typename T, int RIEM, int MODE>
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
 __device__ __forceinline__ void element_block_split(const MeshDev& m, const StageParams* __restrict__ sp,
                                                     const T* __restrict__ U, T* __restrict__ out, T* __restrict__ G,
                                                     const T* __restrict__ Fs, const T* __restrict__ Fm, const T rkA,
                                                     const T rkB, const T dt, const long long e0, T* __restrict__ Ts,
-                                                    T* __restrict__ Tm) {
+                                                    T* __restrict__ Tm, const T* __restrict__ Gr = nullptr) {
   using C = SplitCfg<N>;
   constexpr int NP2 = C::NP2, NN = C::NN, EPB = C::EPB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sQ = reinterpret_cast<T*>(smem_raw);        // [EPB][6][NN] halved primitives
   T* sV = sQ + EPB * 6 * NN;                     // [EPB][3][5][NN] two-point volume terms
   T* sS = sV + EPB * 15 * NN;                    // [EPB][6][5][NP2] outward face fluxes
+  T* sW = sS + EPB * 30 * NP2;                   // PHYS 1: [EPB][3][5][NN] -F^v along the axes of xi^1..3
 
   const T* c = Prec<T>::c(m);
   const int tid = threadIdx.x;
@@ -190,12 +201,26 @@ __device__ __forceinline__ void element_block_split(const MeshDev& m, const Stag
     Q[3 * NN] = T(0.5) * q.u[2];
     Q[4 * NN] = T(0.5) * q.p;
     Q[5 * NN] = T(0.5) * ((u[4] + q.p) * q.ir);
+    if (PHYS) {
+      // viscous fluxes of the lifted gradients along the axes of xi^1 (y), xi^2 (z), xi^3 (x)
+      T gn[15], fv[5];
+#pragma unroll
+      for (int kk = 0; kk < 15; ++kk) gn[kk] = Gr[(e * 15 + kk) * NN + nd];
+      T* W = sW + le * 15 * NN + nd;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        viscous_flux_axis(u, gn, d == 0 ? 1 : (d == 1 ? 2 : 0), c, fv);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) W[(5 * d + v) * NN] = -fv[v];
+      }
+    }
   }
 
-  element_face_fluxes<N, T, RIEM, 0>(m, sp, U, Fs, Fm, nullptr, e0, sS, tid);
+  element_face_fluxes<N, T, RIEM, PHYS>(m, sp, U, Fs, Fm, Gr, e0, sS, tid);
 
   __syncthreads();
   split_volume_lines<N, T>(m, sQ, sV, e0, tid);
+  if (PHYS) contract_lines_inplace<N, T>(sW, tid);
   __syncthreads();
   if (!active) return;
   const int blk = e >= m.Es;
@@ -205,85 +230,90 @@ __device__ __forceinline__ void element_block_split(const MeshDev& m, const Stag
     const T* V = sV + le * 15 * NN + nd;
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] = a0 * V[v * NN] + a1 * V[(5 + v) * NN] + a2 * V[(10 + v) * NN];
+    if (PHYS) {
+      const T* W = sW + le * 15 * NN + nd;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v] += a0 * W[v * NN] + a1 * W[(5 + v) * NN] + a2 * W[(10 + v) * NN];
+    }
   }
   element_surface_update<N, T, MODE>(m, sS + le * 30 * NP2, acc, nd, e, base, u, g, out, G, rkA, rkB, dt, Ts, Tm);
 }
 
-template <int N, typename T, int RIEM, int MODE>
-__global__ void __launch_bounds__(SplitCfg<N>::THREADS, sizeof(T) == 4 ? SplitCfg<N>::MINB : 1)
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
+__global__ void __launch_bounds__(SplitCfg<N>::THREADS, (sizeof(T) == 4 && PHYS == 0) ? SplitCfg<N>::MINB : 1)
 dg_element_split_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
                         T* __restrict__ out, T* __restrict__ G, const T* __restrict__ Fs,
                         const T* __restrict__ Fm, const T rkA, const T rkB, const T dt, T* __restrict__ Ts,
-                        T* __restrict__ Tm) {
-  element_block_split<N, T, RIEM, MODE>(m, sp, U, out, G, Fs, Fm, rkA, rkB, dt,
-                                        (long long)blockIdx.x * SplitCfg<N>::EPB, Ts, Tm);
+                        T* __restrict__ Tm, const T* __restrict__ Gr) {
+  element_block_split<N, T, RIEM, MODE, PHYS>(m, sp, U, out, G, Fs, Fm, rkA, rkB, dt,
+                                              (long long)blockIdx.x * SplitCfg<N>::EPB, Ts, Tm, Gr);
 }
 
-template <int N, typename T, int RIEM, int MODE>
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
 static cudaError_t launch_split_t(const ElemArgs& a, cudaStream_t st) {
   using C = SplitCfg<N>;
   const long long blocks = (a.m.E + C::EPB - 1) / C::EPB;
   if (blocks <= 0) return cudaSuccess;
-  dg_element_split_kernel<N, T, RIEM, MODE><<<(unsigned)blocks, C::THREADS, C::template smem_bytes<T>(), st>>>(
+  dg_element_split_kernel<N, T, RIEM, MODE, PHYS><<<(unsigned)blocks, C::THREADS, C::template smem_bytes<T, PHYS>(), st>>>(
       a.m, a.sp, (const T*)a.U, (T*)a.out, (T*)a.G, (const T*)a.Fs, (const T*)a.Fm, (T)a.rkA, (T)a.rkB, (T)a.dt,
-      (T*)a.Ts, (T*)a.Tm);
+      (T*)a.Ts, (T*)a.Tm, (const T*)a.Gr);
   return cudaGetLastError();
 }
 
-template <int N, typename T, int RIEM, int MODE>
+template <int N, typename T, int RIEM, int MODE, int PHYS = 0>
 static cudaError_t prepare_split_t() {
-  cudaError_t e = cudaFuncSetAttribute(dg_element_split_kernel<N, T, RIEM, MODE>,
+  cudaError_t e = cudaFuncSetAttribute(dg_element_split_kernel<N, T, RIEM, MODE, PHYS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SplitCfg<N>::template smem_bytes<T>());
+                                       (int)SplitCfg<N>::template smem_bytes<T, PHYS>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(dg_element_split_kernel<N, T, RIEM, MODE>,
+  return cudaFuncSetAttribute(dg_element_split_kernel<N, T, RIEM, MODE, PHYS>,
                               cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutDefault);
 }
 
-template <int N, typename T>
+template <int N, typename T, int PHYS = 0>
 static cudaError_t launch_split_n(int riemann, int mode, const ElemArgs& a, cudaStream_t st) {
   if (riemann == 0) {
-    if (mode == ELEM_RHS) return launch_split_t<N, T, 0, ELEM_RHS>(a, st);
-    if (mode == ELEM_STAGE) return launch_split_t<N, T, 0, ELEM_STAGE>(a, st);
-    return launch_split_t<N, T, 0, ELEM_STAGE_FIRST>(a, st);
+    if (mode == ELEM_RHS) return launch_split_t<N, T, 0, ELEM_RHS, PHYS>(a, st);
+    if (mode == ELEM_STAGE) return launch_split_t<N, T, 0, ELEM_STAGE, PHYS>(a, st);
+    return launch_split_t<N, T, 0, ELEM_STAGE_FIRST, PHYS>(a, st);
   }
-  if (mode == ELEM_RHS) return launch_split_t<N, T, 1, ELEM_RHS>(a, st);
-  if (mode == ELEM_STAGE) return launch_split_t<N, T, 1, ELEM_STAGE>(a, st);
-  return launch_split_t<N, T, 1, ELEM_STAGE_FIRST>(a, st);
+  if (mode == ELEM_RHS) return launch_split_t<N, T, 1, ELEM_RHS, PHYS>(a, st);
+  if (mode == ELEM_STAGE) return launch_split_t<N, T, 1, ELEM_STAGE, PHYS>(a, st);
+  return launch_split_t<N, T, 1, ELEM_STAGE_FIRST, PHYS>(a, st);
 }
 
-template <int N, typename T>
+template <int N, typename T, int PHYS = 0>
 static cudaError_t prepare_split_n() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = prepare_split_t<N, T, 0, ELEM_RHS>()) != cudaSuccess) e = r;
-  if ((r = prepare_split_t<N, T, 0, ELEM_STAGE>()) != cudaSuccess) e = r;
-  if ((r = prepare_split_t<N, T, 0, ELEM_STAGE_FIRST>()) != cudaSuccess) e = r;
-  if ((r = prepare_split_t<N, T, 1, ELEM_RHS>()) != cudaSuccess) e = r;
-  if ((r = prepare_split_t<N, T, 1, ELEM_STAGE>()) != cudaSuccess) e = r;
-  if ((r = prepare_split_t<N, T, 1, ELEM_STAGE_FIRST>()) != cudaSuccess) e = r;
+  if ((r = prepare_split_t<N, T, 0, ELEM_RHS, PHYS>()) != cudaSuccess) e = r;
+  if ((r = prepare_split_t<N, T, 0, ELEM_STAGE, PHYS>()) != cudaSuccess) e = r;
+  if ((r = prepare_split_t<N, T, 0, ELEM_STAGE_FIRST, PHYS>()) != cudaSuccess) e = r;
+  if ((r = prepare_split_t<N, T, 1, ELEM_RHS, PHYS>()) != cudaSuccess) e = r;
+  if ((r = prepare_split_t<N, T, 1, ELEM_STAGE, PHYS>()) != cudaSuccess) e = r;
+  if ((r = prepare_split_t<N, T, 1, ELEM_STAGE_FIRST, PHYS>()) != cudaSuccess) e = r;
   return e;
 }
 
-#define SM_SPLIT_DISPATCH(T, N, riemann, mode, a, st)            \
-  switch (N) {                                                   \
-    case 1: return launch_split_n<1, T>(riemann, mode, a, st);   \
-    case 2: return launch_split_n<2, T>(riemann, mode, a, st);   \
-    case 3: return launch_split_n<3, T>(riemann, mode, a, st);   \
-    case 4: return launch_split_n<4, T>(riemann, mode, a, st);   \
-    case 5: return launch_split_n<5, T>(riemann, mode, a, st);   \
-    case 6: return launch_split_n<6, T>(riemann, mode, a, st);   \
-    case 7: return launch_split_n<7, T>(riemann, mode, a, st);   \
-    default: return cudaErrorInvalidValue;                       \
+#define SM_SPLIT_DISPATCH(T, N, riemann, mode, a, st, PHYS)            \
+  switch (N) {                                                         \
+    case 1: return launch_split_n<1, T, PHYS>(riemann, mode, a, st);   \
+    case 2: return launch_split_n<2, T, PHYS>(riemann, mode, a, st);   \
+    case 3: return launch_split_n<3, T, PHYS>(riemann, mode, a, st);   \
+    case 4: return launch_split_n<4, T, PHYS>(riemann, mode, a, st);   \
+    case 5: return launch_split_n<5, T, PHYS>(riemann, mode, a, st);   \
+    case 6: return launch_split_n<6, T, PHYS>(riemann, mode, a, st);   \
+    case 7: return launch_split_n<7, T, PHYS>(riemann, mode, a, st);   \
+    default: return cudaErrorInvalidValue;                             \
   }
 
-#define SM_SPLIT_PREPARE(T, N)                  \
-  switch (N) {                                  \
-    case 1: return prepare_split_n<1, T>();     \
-    case 2: return prepare_split_n<2, T>();     \
-    case 3: return prepare_split_n<3, T>();     \
-    case 4: return prepare_split_n<4, T>();     \
-    case 5: return prepare_split_n<5, T>();     \
-    case 6: return prepare_split_n<6, T>();     \
-    case 7: return prepare_split_n<7, T>();     \
-    default: return cudaErrorInvalidValue;      \
+#define SM_SPLIT_PREPARE(T, N, PHYS)                  \
+  switch (N) {                                        \
+    case 1: return prepare_split_n<1, T, PHYS>();     \
+    case 2: return prepare_split_n<2, T, PHYS>();     \
+    case 3: return prepare_split_n<3, T, PHYS>();     \
+    case 4: return prepare_split_n<4, T, PHYS>();     \
+    case 5: return prepare_split_n<5, T, PHYS>();     \
+    case 6: return prepare_split_n<6, T, PHYS>();     \
+    case 7: return prepare_split_n<7, T, PHYS>();     \
+    default: return cudaErrorInvalidValue;            \
   }

@@ -74,20 +74,16 @@ def _init(L, slidemesh, p):
 
 
 @pytest.mark.parametrize("case", [
-    "split_ns", "periodic_cylinder", "periodic_ns", "periodic_bad", "volume_bad", "geom_bad",
+    "periodic_cylinder", "periodic_ns", "periodic_bad", "volume_bad", "geom_bad",
     "cone_angle", "cone_axis", "cone_flow", "annular_radius", "annular_flow", "plane_rotation_flow",
 ])
 def test_shape_and_option_checks_without_gpu(libpath, case):
     """Descriptions the library does not build are refused by sm_init_mesh before any CUDA
-    call: the split form with Navier-Stokes, the second interface off the plane Euler case,
+    call: the second interface off the plane Euler case,
     out-of-range options, and geometry that the annulus and the cone cannot map."""
     from paper_2008_04356_gb300 import slidemesh, synth
     L = slidemesh.lib()
-    if case == "split_ns":
-        p = synth.config_shear_x(N=3)
-        p.volume = synth.VOLUME_SPLIT
-        want, msg = -7, b"split-form"
-    elif case == "periodic_cylinder":
+    if case == "periodic_cylinder":
         p = synth.config_cylinder(N=3)
         p.periodic_x = 1
         want, msg = -7, b"periodic x"
@@ -160,3 +156,16 @@ def test_no_alloc_entry_point_checks_without_gpu(libpath, case):
         a, want = None, -1
     rc = L.sm_rhs_static(ctypes.byref(slidemesh.mesh_desc(p)), ctypes.byref(mo), 0.0, a, b, None)
     assert rc == want, (rc, L.sm_last_error())
+
+
+def test_static_rhs_refuses_misaligned_arrays_without_gpu(libpath):
+    """sm_rhs_static checks its arrays' 16-byte alignment before any CUDA call (the pointers
+    here are never dereferenced)."""
+    from paper_2008_04356_gb300 import slidemesh, synth
+    L = slidemesh.lib()
+    p = synth.config_box(N=3)
+    mo = slidemesh.SmMotion(p.v, 0.0, 0.0)
+    rc = L.sm_rhs_static(ctypes.byref(slidemesh.mesh_desc(p)), ctypes.byref(mo), 0.0, 0x10008, 0x20000, None)
+    assert rc == -1 and b"aligned" in L.sm_last_error()
+    rc = L.sm_rhs_static(ctypes.byref(slidemesh.mesh_desc(p)), ctypes.byref(mo), 0.0, 0x10000, 0x20004, None)
+    assert rc == -1

@@ -428,3 +428,26 @@ def test_interface_heavy_full_size_sampled(sm):
     got = Ut[torch.from_numpy(elems).cuda()].cpu().numpy()
     assert rel_l2(got, ref) < FP32_TOL
     assert rel_max(got, ref) < 1e-4
+
+
+@pytest.mark.parametrize("prec", [synth.FP32, synth.FP64])
+def test_misaligned_device_arrays_are_refused(sm, prec):
+    """The kernels move caller arrays in 8- and 16-byte vectors: a state or output that is
+    not 16-byte aligned is refused with SM_ERR_ARG before any launch."""
+    p = ragged_box(3, synth.RUSANOV, prec=prec)
+    dt = torch.float64 if prec == synth.FP64 else torch.float32
+    sol = sm.Solver(p)
+    n = p.nelem * 5 * (p.N + 1) ** 3
+    buf = torch.zeros(n + 4, dtype=dt, device="cuda")
+    out = torch.empty(n, dtype=dt, device="cuda")
+    L = sm.lib()
+    st = torch.cuda.current_stream().cuda_stream
+    for off in (1, 2, 3):
+        if (off * buf.element_size()) % 16 == 0:
+            continue
+        rc = L.sm_rhs(sol.h, 0.1, buf[off:].data_ptr(), out.data_ptr(), st)
+        assert rc == -1 and b"aligned" in L.sm_last_error()
+        rc = L.sm_rhs(sol.h, 0.1, out.data_ptr(), buf[off:].data_ptr(), st)
+        assert rc == -1
+    torch.cuda.synchronize()
+    sol.close()

@@ -154,13 +154,6 @@ def test_split_free_stream_preserved_gpu(sm, N):
         assert (U1 - U0).abs().max().item() < tol, (N, prec)
 
 
-def test_split_rejects_navier_stokes(sm):
-    p = synth.config_shear_x(N=3)
-    p.volume = synth.VOLUME_SPLIT
-    with pytest.raises(sm.SlidemeshError):
-        sm.Solver(p)
-
-
 def test_split_interface_heavy_full_size_sampled(sm):
     """2 x 4 x 256 x 256 elements, N = 5, FP32, Roe/HH: the launch configuration the
     benchmark times for the split form; sampled elements against the oracle."""

@@ -105,3 +105,13 @@ def test_static_rhs_refuses_scratch_beyond_its_maximum(sm):
     assert rc == -1
     msg = L.sm_last_error().decode()
     assert "scratch" in msg and "bytes" in msg
+
+
+def test_static_rhs_refuses_misaligned_arrays(sm):
+    p, _ = _problems()
+    L = sm.lib()
+    desc = sm.mesh_desc(p)
+    mo = sm.SmMotion(p.v, 0.0, p.delta0)
+    # refused before any CUDA call: the pointers are never dereferenced
+    rc = L.sm_rhs_static(ctypes.byref(desc), ctypes.byref(mo), 0.0, 0x10008, 0x20000, None)
+    assert rc == -1 and b"aligned" in L.sm_last_error()
