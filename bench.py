@@ -437,9 +437,10 @@ CONE_WORKLOAD = ("rotating conical sliding interface about the axis, Euler: half
 
 
 def shape_problem(workload: str, volume: str, riemann, prec: int):
-    """The curved-element workload at full size: the cylinder with Navier-Stokes (weak form
-    only), or the annulus or the cone with Euler, weak or split form (the split form with
-    Roe/HH unless Rusanov is asked for)."""
+    """The curved-element workload at full size: the cylinder with Navier-Stokes, or the
+    annulus or the cone with Euler; weak or split form (the split form with Roe/HH unless
+    Rusanov is asked for; on the cylinder it is the paper's production scheme, split form
+    with BR1)."""
     from paper_2008_04356_gb300 import synth
     if workload == "cone":
         p = synth.config_cone(N=7, nel=(24, 48, 16), omega=0.4, alpha=math.pi / 6, flow="pulse", precision=prec)
@@ -451,8 +452,6 @@ def shape_problem(workload: str, volume: str, riemann, prec: int):
     else:
         raise ValueError(workload)
     if volume == "split":
-        if workload == "cylinder":
-            raise ValueError("the split form is built for Euler; the cylinder workload is Navier-Stokes")
         p.volume = synth.VOLUME_SPLIT
         p.riemann = synth.RUSANOV if riemann == "rusanov" else synth.ROE_HH
     return p

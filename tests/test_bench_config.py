@@ -33,9 +33,10 @@ def test_euler_shapes_split_form(workload, geom, riemann, expect):
     assert p.volume == synth.VOLUME_SPLIT and p.riemann == expect
 
 
-def test_split_cylinder_rejected():
-    with pytest.raises(ValueError):
-        bench.shape_problem("cylinder", "split", None, synth.FP32)
+def test_split_cylinder_is_navier_stokes_split_form():
+    p = bench.shape_problem("cylinder", "split", None, synth.FP32)
+    assert p.geom == synth.GEOM_CYLINDER and p.physics == synth.NAVIER_STOKES
+    assert p.volume == synth.VOLUME_SPLIT and p.riemann == synth.ROE_HH and p.mu > 0.0
 
 
 def test_unknown_workload_rejected():
