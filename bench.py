@@ -528,7 +528,10 @@ def run_cylinder(args, rank, world, local):
         "kernels": {"stage_params": {"launches": kcnt[0], "ms": kms[0]},
                     "lifting_and_interface": {"launches": kcnt[1], "ms": kms[1], "avg_ms": kms[1] / max(kcnt[1], 1)},
                     "curved_element": {"launches": kcnt[2], "ms": kms[2], "avg_ms": elem_ms}},
-        "gpu_launches": (3 if annular else 5) * 5 * args.steps,
+        # per step: the five stages' parameters in one launch, then per stage the interface
+        # kernel and the element kernel (Euler) or interface lifting, lifting, viscous
+        # interface flux and element kernel (Navier-Stokes)
+        "gpu_launches": (1 + (2 if annular else 4) * 5) * args.steps,
         "clocks": clk,
         "diag": {"n_delta": d["n_delta"], "s_delta": d["s_delta"], "finite": d["status"] == 0,
                  "totals": d["totals"]},
@@ -744,7 +747,9 @@ def main():
                                           "frac_hbm": iface_bytes / (iface_ms * 1e-3) / 1e9 / hbm},
                     "dg_element": {"launches": kcnt[2], "ms": kms[2], "avg_ms": elem_ms}},
         "e2e": e2e,
-        "gpu_launches": 15 * args.steps,
+        # per step: the five stages' parameters in one launch, then per stage the interface
+        # kernel and the element kernel
+        "gpu_launches": 11 * args.steps,
         "clocks": clk,
         "diag": {"n_delta": d["n_delta"], "s_delta": d["s_delta"], "finite": d["status"] == 0},
     }

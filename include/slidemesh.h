@@ -205,15 +205,16 @@ int sm_interface(sm_solver* s, double t, const void* dU, void* dF_static, void* 
 int sm_gradients(sm_solver* s, double t, const void* dU, void* dGrad, void* stream);
 
 /* Advances the solver state by nsteps low-storage RK4 steps of size dt (five stages each,
- * stage time t + c_k dt computed on the device as fma(c_k, dt, t)).  Asynchronous on
- * stream; the steps are replayed from a CUDA graph captured per (dt, buffer parity).
- * The solver time advances by dt per step. */
+ * stage time t + c_k dt computed on the device as fma(c_k, dt, t); the five stages'
+ * interface configurations and mortar operators (Sec. 4.3, 3.2) are built in one launch at
+ * the start of each step).  Asynchronous on stream; the steps are replayed from a CUDA graph
+ * captured per (dt, buffer parity).  The solver time advances by dt per step. */
 int sm_step(sm_solver* s, double dt, int nsteps, void* stream);
 
 /* The same stage sequence as sm_step, launched kernel by kernel (no graph) with a CUDA
  * event pair around every launch on stream; synchronises.  ms_out[3] receives the summed
- * device time of the mapper, interface and element kernels, launches_out[3] their launch
- * counts (either may be NULL).  For measurement only: the state advances exactly as with
+ * device time of the mapper (one launch per step), interface and element kernels,
+ * launches_out[3] their launch counts (either may be NULL).  For measurement only: the state advances exactly as with
  * sm_step. */
 int sm_step_profiled(sm_solver* s, double dt, int nsteps, void* stream, double* ms_out, int* launches_out);
 

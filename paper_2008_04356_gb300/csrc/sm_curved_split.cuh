@@ -170,7 +170,7 @@ __device__ __forceinline__ void curved_split_block(const MeshDev& m, const Stage
 namespace {
 
 template <int N, typename T, int RIEM, int MODE, int PHYS>
-__global__ void __launch_bounds__(ElemCfg<N>::THREADS, PHYS ? 1 : CurvedSplitCfg<N>::template minb<T>())
+__global__ void __launch_bounds__(ElemCfg<N>::THREADS, CurvedSplitCfg<N>::template minb<T>())
 curved_split_kernel(const MeshDev m, const StageParams* __restrict__ sp, const T* __restrict__ U,
                     T* __restrict__ out, T* __restrict__ G, const T* __restrict__ Fs, const T* __restrict__ Fm,
                     const T rkA, const T rkB, const T dt, const T* __restrict__ Gr) {

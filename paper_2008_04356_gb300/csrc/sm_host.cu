@@ -389,7 +389,9 @@ struct sm_solver {
   void* G = nullptr;
   void* Fs = nullptr;
   void* Fm = nullptr;
-  StageParams* sp = nullptr;
+  StageParams* sp = nullptr;   // five blocks: the stages of a step (block 0 for sm_rhs & co.)
+  int sp_last = 0;              // the block of the last evaluated stage
+  unsigned* ticket_d = nullptr; // counter of the step-parameter launch
   double* t_d = nullptr;
   double* red_d = nullptr;      // partial sums [nblk][5] + outputs [3][5]
   int4* topo_d = nullptr;       // per-element neighbour table (2 int4 per element)
@@ -422,34 +424,34 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 // lifting face values on the interface, the lifted gradients, then the interface fluxes with
 // their viscous part; Euler: the interface fluxes.
 // from_traces: the interface kernel reads the compact traces Ts / Tm (of U[cur]) instead of U.
-cudaError_t enqueue_flux_inputs(sm_solver* s, const void* dU, void* Fs, void* Fm, cudaStream_t st,
+cudaError_t enqueue_flux_inputs(sm_solver* s, const StageParams* sp, const void* dU, void* Fs, void* Fm, cudaStream_t st,
                                 bool from_traces = false) {
   cudaError_t e = cudaSuccess;
   const bool sliding = !s->desc.interface_conforming;
   if (is_ns(s) && s->m.geom != 0) {
     const bool f64 = s->prec == SM_FP64;
-    if (sliding && (e = f64 ? launch_curved_interface_lift_f64(s->N, s->m, s->sp, dU, s->Ls, s->Lm, st)
-                            : launch_curved_interface_lift_f32(s->N, s->m, s->sp, dU, s->Ls, s->Lm, st)) != cudaSuccess)
+    if (sliding && (e = f64 ? launch_curved_interface_lift_f64(s->N, s->m, sp, dU, s->Ls, s->Lm, st)
+                            : launch_curved_interface_lift_f32(s->N, s->m, sp, dU, s->Ls, s->Lm, st)) != cudaSuccess)
       return e;
-    e = f64 ? launch_curved_lift_f64(s->N, s->m, s->sp, dU, s->Gr, s->Ls, s->Lm, st)
-            : launch_curved_lift_f32(s->N, s->m, s->sp, dU, s->Gr, s->Ls, s->Lm, st);
+    e = f64 ? launch_curved_lift_f64(s->N, s->m, sp, dU, s->Gr, s->Ls, s->Lm, st)
+            : launch_curved_lift_f32(s->N, s->m, sp, dU, s->Gr, s->Ls, s->Lm, st);
     if (e != cudaSuccess || !sliding) return e;
-    return f64 ? launch_curved_interface_ns_f64(s->N, s->desc.riemann, s->m, s->sp, dU, s->Gr, Fs, Fm, st)
-               : launch_curved_interface_ns_f32(s->N, s->desc.riemann, s->m, s->sp, dU, s->Gr, Fs, Fm, st);
+    return f64 ? launch_curved_interface_ns_f64(s->N, s->desc.riemann, s->m, sp, dU, s->Gr, Fs, Fm, st)
+               : launch_curved_interface_ns_f32(s->N, s->desc.riemann, s->m, sp, dU, s->Gr, Fs, Fm, st);
   }
   if (is_ns(s)) {
-    if (sliding && (e = launch_interface_lift(s->N, s->prec, s->m, s->sp, dU, s->Ls, s->Lm, st)) != cudaSuccess) return e;
-    e = s->prec == SM_FP64 ? launch_lift_f64(s->N, s->m, s->sp, dU, s->Gr, s->Ls, s->Lm, st)
-                           : launch_lift_f32(s->N, s->m, s->sp, dU, s->Gr, s->Ls, s->Lm, st);
+    if (sliding && (e = launch_interface_lift(s->N, s->prec, s->m, sp, dU, s->Ls, s->Lm, st)) != cudaSuccess) return e;
+    e = s->prec == SM_FP64 ? launch_lift_f64(s->N, s->m, sp, dU, s->Gr, s->Ls, s->Lm, st)
+                           : launch_lift_f32(s->N, s->m, sp, dU, s->Gr, s->Ls, s->Lm, st);
     if (e != cudaSuccess) return e;
-    if (sliding) e = launch_interface_ns(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, s->Gr, Fs, Fm, st);
+    if (sliding) e = launch_interface_ns(s->N, s->prec, s->desc.riemann, s->m, sp, dU, s->Gr, Fs, Fm, st);
     return e;
   }
   if (sliding && s->m.geom != 0)
-    return s->prec == SM_FP64 ? launch_curved_interface_f64(s->N, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st)
-                              : launch_curved_interface_f32(s->N, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st);
+    return s->prec == SM_FP64 ? launch_curved_interface_f64(s->N, s->desc.riemann, s->m, sp, dU, Fs, Fm, st)
+                              : launch_curved_interface_f32(s->N, s->desc.riemann, s->m, sp, dU, Fs, Fm, st);
   if (sliding)
-    e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, Fs, Fm, st, from_traces ? s->Ts : nullptr,
+    e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, sp, dU, Fs, Fm, st, from_traces ? s->Ts : nullptr,
                          from_traces ? s->Tm : nullptr);
   if (e == cudaSuccess && sliding && s->m.Ts2) {
     // the second interface (periodic x), solved as the x-mirrored first one from its traces
@@ -458,7 +460,7 @@ cudaError_t enqueue_flux_inputs(sm_solver* s, const void* dU, void* Fs, void* Fm
       s->traces_ok = false;           // Ts2 / Tm2 now hold the traces of dU
       if (e != cudaSuccess) return e;
     }
-    e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, s->sp, dU, const_cast<void*>(s->m.Fs2),
+    e = launch_interface(s->N, s->prec, s->desc.riemann, s->m, sp, dU, const_cast<void*>(s->m.Fs2),
                          const_cast<void*>(s->m.Fm2), st, s->m.Ts2, s->m.Tm2);
   }
   return e;
@@ -479,7 +481,8 @@ cudaError_t ensure_traces(sm_solver* s, cudaStream_t st) {
 cudaError_t enqueue_rhs_parts(sm_solver* s, double t, const void* dU, void* Fs, void* Fm, cudaStream_t st) {
   cudaError_t e = launch_stage_params(s->m, s->np, s->sp, s->t_d, t, 0.0, 0.0, 0, st);
   if (e != cudaSuccess) return e;
-  return enqueue_flux_inputs(s, dU, Fs, Fm, st);
+  s->sp_last = 0;
+  return enqueue_flux_inputs(s, s->sp, dU, Fs, Fm, st);
 }
 
 cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a0, cudaStream_t st) {
@@ -517,13 +520,16 @@ cudaError_t launch_elem(sm_solver* s, int mode, const ElemArgs& a0, cudaStream_t
                             : launch_element_f32(s->N, s->desc.riemann, mode, a, st);
 }
 
+// One RK step: the five stages' parameters in one launch, then per stage the interface
+// inputs and the element kernel.
 cudaError_t enqueue_step(sm_solver* s, double dt, int cur, cudaStream_t st) {
   int c = cur;
+  cudaError_t e = launch_step_params(s->m, s->np, s->sp, s->t_d, RK_C, dt, s->ticket_d, st);
+  if (e != cudaSuccess) return e;
   for (int k = 0; k < 5; ++k) {
-    cudaError_t e = launch_stage_params(s->m, s->np, s->sp, s->t_d, 0.0, RK_C[k], dt, k == 4 ? 2 : 1, st);
-    if (e != cudaSuccess) return e;
-    if ((e = enqueue_flux_inputs(s, s->U[c], s->Fs, s->Fm, st, use_traces(s))) != cudaSuccess) return e;
-    ElemArgs a{s->m, s->sp, s->U[c], s->U[1 - c], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
+    const StageParams* sp = s->sp + k;
+    if ((e = enqueue_flux_inputs(s, sp, s->U[c], s->Fs, s->Fm, st, use_traces(s))) != cudaSuccess) return e;
+    ElemArgs a{s->m, sp, s->U[c], s->U[1 - c], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
     a.Ts = s->Ts;
     a.Tm = s->Tm;
     e = launch_elem(s, k == 0 ? ELEM_STAGE_FIRST : ELEM_STAGE, a, st);
@@ -561,7 +567,7 @@ void free_solver(sm_solver* s) {
   if (!s) return;
   clear_graphs(s);
   if (s->cap) cudaStreamDestroy(s->cap);
-  void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->t_d, s->red_d, s->topo_d,
+  void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->ticket_d, s->t_d, s->red_d, s->topo_d,
                   s->Gr, s->Ls, s->Lm, s->Ts, s->Tm, s->Ts2, s->Tm2, s->Fs2, s->Fm2, s->geo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -706,7 +712,8 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   SM_ALLOC(s->G, sbytes);
   SM_ALLOC(s->Fs, fbytes);
   SM_ALLOC(s->Fm, fbytes);
-  SM_ALLOC(s->sp, sizeof(StageParams));
+  SM_ALLOC(s->sp, 5 * sizeof(StageParams));
+  SM_ALLOC(s->ticket_d, sizeof(unsigned));
   SM_ALLOC(s->t_d, sizeof(double));
   SM_ALLOC(s->red_d, sizeof(double) * (s->red_blocks * 5 + 15));
   SM_ALLOC(s->topo_d, sizeof(int4) * 2 * (size_t)m.E);
@@ -771,7 +778,8 @@ int sm_init_mesh(const sm_mesh_desc* desc, sm_solver** out) {
   else if ((e = cudaMemset(s->U[0], 0, sbytes)) != cudaSuccess) what = "clear U";
   else if ((e = cudaMemset(s->Fs, 0, fbytes)) != cudaSuccess || (e = cudaMemset(s->Fm, 0, fbytes)) != cudaSuccess) what = "clear F";
   else if ((e = cudaMemset(s->t_d, 0, sizeof(double))) != cudaSuccess) what = "clear t";
-  else if ((e = cudaMemset(s->sp, 0, sizeof(StageParams))) != cudaSuccess) what = "clear stage params";
+  else if ((e = cudaMemset(s->sp, 0, 5 * sizeof(StageParams))) != cudaSuccess) what = "clear stage params";
+  else if ((e = cudaMemset(s->ticket_d, 0, sizeof(unsigned))) != cudaSuccess) what = "clear step counter";
   else if ((e = (s->prec == SM_FP64 ? prepare_element_f64(s->N) : prepare_element_f32(s->N))) != cudaSuccess) what = "element kernel attributes";
   else if (desc->volume == SM_VOLUME_SPLIT &&
            (e = (s->prec == SM_FP64 ? prepare_element_split_f64(s->N) : prepare_element_split_f32(s->N))) != cudaSuccess)
@@ -898,6 +906,7 @@ int sm_gradients(sm_solver* s, double t, const void* dU, void* dGrad, void* stre
   if (!std::isfinite(t)) return fail(SM_ERR_ARG, "non-finite time");
   cudaStream_t st = (cudaStream_t)stream;
   SM_CK(launch_stage_params(s->m, s->np, s->sp, s->t_d, t, 0.0, 0.0, 0, st), "stage parameters");
+  s->sp_last = 0;
   if (s->m.geom != 0) {
     const bool f64 = s->prec == SM_FP64;
     if (!s->desc.interface_conforming)
@@ -926,6 +935,7 @@ int sm_step(sm_solver* s, double dt, int nsteps, void* stream) {
     SM_CK(cudaGraphLaunch(exec, st), "graph launch");
     s->cur ^= 1;
     s->t_host += dt;
+    s->sp_last = 4;
   }
   return SM_OK;
 }
@@ -941,28 +951,37 @@ int sm_step_profiled(sm_solver* s, double dt, int nsteps, void* stream, double* 
   int rc = SM_OK;
   if (nsteps > 0 && ensure_traces(s, st) != cudaSuccess) rc = fail(SM_ERR_CUDA, "gather interface traces");
   for (int n = 0; n < nsteps && rc == SM_OK; ++n) {
+    // the step's five stage-parameter blocks in one launch, then per stage the interface
+    // inputs and the element kernel, with events around each part
+    cudaError_t e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = launch_step_params(s->m, s->np, s->sp, s->t_d, RK_C, dt, s->ticket_d, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float a0 = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a0, ev[0], ev[1]);
+    if (e != cudaSuccess) { rc = fail(SM_ERR_CUDA, "profiled step", e); break; }
+    ms[0] += a0;
+    cnt[0] += 1;
     for (int k = 0; k < 5; ++k) {
-      cudaError_t e = cudaEventRecord(ev[0], st);
-      if (e == cudaSuccess) e = launch_stage_params(s->m, s->np, s->sp, s->t_d, 0.0, RK_C[k], dt, k == 4 ? 2 : 1, st);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-      if (e == cudaSuccess) e = enqueue_flux_inputs(s, s->U[s->cur], s->Fs, s->Fm, st, use_traces(s));
+      const StageParams* sp = s->sp + k;
+      e = cudaEventRecord(ev[1], st);
+      if (e == cudaSuccess) e = enqueue_flux_inputs(s, sp, s->U[s->cur], s->Fs, s->Fm, st, use_traces(s));
       if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
-      ElemArgs a{s->m, s->sp, s->U[s->cur], s->U[1 - s->cur], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
+      ElemArgs a{s->m, sp, s->U[s->cur], s->U[1 - s->cur], s->G, s->Fs, s->Fm, RK_A[k], RK_B[k], dt};
       a.Ts = s->Ts;
       a.Tm = s->Tm;
       if (e == cudaSuccess) e = launch_elem(s, k == 0 ? ELEM_STAGE_FIRST : ELEM_STAGE, a, st);
       if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
       if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
-      float a0 = 0, a1 = 0, a2 = 0;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&a0, ev[0], ev[1]);
+      float a1 = 0, a2 = 0;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&a1, ev[1], ev[2]);
       if (e == cudaSuccess) e = cudaEventElapsedTime(&a2, ev[2], ev[3]);
       if (e != cudaSuccess) { rc = fail(SM_ERR_CUDA, "profiled step", e); break; }
-      ms[0] += a0; ms[1] += a1; ms[2] += a2;
-      cnt[0] += 1; cnt[1] += s->desc.interface_conforming ? 0 : 1; cnt[2] += 1;
+      ms[1] += a1; ms[2] += a2;
+      cnt[1] += s->desc.interface_conforming ? 0 : 1; cnt[2] += 1;
       s->cur ^= 1;
     }
-    if (rc == SM_OK) s->t_host += dt;
+    if (rc == SM_OK) { s->t_host += dt; s->sp_last = 4; }
   }
   for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
   if (ms_out) for (int k = 0; k < 3; ++k) ms_out[k] = ms[k];
@@ -982,8 +1001,9 @@ int sm_diag(sm_solver* s, sm_diag_out* out, void* stream) {
   long long n = 0;
   double sfrac = 0.0, tt = 0.0;
   SM_CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st), "diag copy");
-  SM_CK(cudaMemcpyAsync(&n, &s->sp->n, sizeof(n), cudaMemcpyDeviceToHost, st), "diag copy n");
-  SM_CK(cudaMemcpyAsync(&sfrac, &s->sp->s, sizeof(sfrac), cudaMemcpyDeviceToHost, st), "diag copy s");
+  const StageParams* spl = s->sp + s->sp_last;
+  SM_CK(cudaMemcpyAsync(&n, &spl->n, sizeof(n), cudaMemcpyDeviceToHost, st), "diag copy n");
+  SM_CK(cudaMemcpyAsync(&sfrac, &spl->s, sizeof(sfrac), cudaMemcpyDeviceToHost, st), "diag copy s");
   SM_CK(cudaMemcpyAsync(&tt, s->t_d, sizeof(tt), cudaMemcpyDeviceToHost, st), "diag copy t");
   SM_CK(cudaStreamSynchronize(st), "diag sync");
   out->n_delta = n;

@@ -220,21 +220,34 @@ template <int N, int TFV> struct IfFusedCfg {
   static constexpr int ITEMS_B = 32 * NBB * NP;
   static constexpr int THREADS = ((ITEMS_A + 31) / 32) * 32;
   // resident CTAs per SM asked of the register allocator (about 80 registers a thread)
-  static constexpr int MINB = 65536 / (THREADS * 80) > 0 ? 65536 / (THREADS * 80) : 1;
+#ifndef SM_IF_FUSED_REGS
+#define SM_IF_FUSED_REGS 80
+#endif
+  static constexpr int MINB = 65536 / (THREADS * SM_IF_FUSED_REGS) > 0 ? 65536 / (THREADS * SM_IF_FUSED_REGS) : 1;
   static constexpr int TB = 5 * NP2;                             // one face's block (floats)
-  static constexpr int FS = TB + (36 - TB % 32) % 32;            // = 4 mod 32, 16-byte rows
+#ifndef SM_IF_FUSED_PAD
+#define SM_IF_FUSED_PAD 1
+#endif
+  // face block stride: = 4 mod 32 (16-byte rows, conflict-free phase B stores), or unpadded
+  static constexpr int FS = SM_IF_FUSED_PAD ? TB + (36 - TB % 32) % 32 : TB;
   static constexpr int MS = TB + (34 - TB % 32) % 32;            // = 2 mod 32
   static constexpr int MR = sm_pair_row(NP);
   static constexpr int MT = sm_pair_stride(NP);
   static constexpr int TBUF = 4 * MT + 2 * (TF + 1) * FS;        // one prefetch buffer (floats)
   static constexpr int SFSZ = ((NM * MS + 3) / 4) * 4;           // mortar fluxes
   static constexpr int OSZ = 2 * TF * FS;                        // output blocks
-  static constexpr int NBUF = 3;                                 // trace buffers: 2 tiles ahead
+#ifndef SM_IF_FUSED_NBUF
+#define SM_IF_FUSED_NBUF 3
+#endif
+  static constexpr int NBUF = SM_IF_FUSED_NBUF;                  // trace buffers: NBUF - 1 tiles ahead
   static constexpr size_t smem_floats = (size_t)NBUF * TBUF + SFSZ + OSZ;
   static constexpr size_t smem_bytes = sizeof(float) * smem_floats;
 };
 // default tile width of the single-solve FP32 launch (the batch autotuner picks 8 or 16)
-template <int N> struct IfFusedTF { static constexpr int TF = 8; };
+#ifndef SM_IF_FUSED_TF
+#define SM_IF_FUSED_TF 8
+#endif
+template <int N> struct IfFusedTF { static constexpr int TF = SM_IF_FUSED_TF; };
 
 __device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);

@@ -6,6 +6,11 @@
 // Per-stage mapper + mortar operators (sm_mapper.cu).
 cudaError_t launch_stage_params(const MeshDev& m, int np, StageParams* sp, double* t_dev, double t_arg,
                                 double ck, double dt, int mode, cudaStream_t st);
+// The five stage-parameter blocks of one RK step (sp5[0..4], stage times fma(ck[k], dt, t))
+// in one launch, which then advances the stored time t_dev by dt; ticket: a zeroed counter.
+struct StepCoeffs { double c[5]; };
+cudaError_t launch_step_params(const MeshDev& m, int np, StageParams* sp5, double* t_dev, const double* ck, double dt,
+                               unsigned* ticket, cudaStream_t st);
 cudaError_t launch_map_batch(const double* d_delta, int count, double l, int n_par, long long* d_n,
                              double* d_s, int* d_pairs, cudaStream_t st);
 cudaError_t launch_mortar_ops(const BasisDev* b, int np, double sigma, double* d_out, cudaStream_t st);

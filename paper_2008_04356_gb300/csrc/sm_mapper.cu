@@ -9,6 +9,25 @@ __global__ void __launch_bounds__(64) stage_params_kernel(MeshDev m, int np, Sta
   stage_params_body(m, np, sp, t_dev, t_arg, ck, dt, mode);
 }
 
+// The five stages of one RK step in one launch: CTA k writes the parameters of stage k into
+// sp + k for the stage time fma(c_k, dt, t), t the stored step time; the last CTA to finish
+// (counted on ticket, which it resets) advances the stored time by dt, after every CTA has
+// read it.
+__global__ void __launch_bounds__(64) step_params_kernel(MeshDev m, int np, StageParams* sp, double* t_dev,
+                                                         StepCoeffs c, double dt, unsigned* ticket) {
+  const int k = blockIdx.x;
+  stage_params_body(m, np, sp + k, t_dev, 0.0, c.c[k], dt, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
+      *t_dev = __dadd_rn(*t_dev, dt);
+      *ticket = 0u;
+      __threadfence();
+    }
+  }
+}
+
 __global__ void map_batch_kernel(const double* delta, int count, double l, int n_par, long long* n_out,
                                  double* s_out, int* pairs) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,6 +62,14 @@ __global__ void __launch_bounds__(64) mortar_ops_kernel(const BasisDev* b, int n
 cudaError_t launch_stage_params(const MeshDev& m, int np, StageParams* sp, double* t_dev, double t_arg,
                                 double ck, double dt, int mode, cudaStream_t st) {
   stage_params_kernel<<<1, 64, 0, st>>>(m, np, sp, t_dev, t_arg, ck, dt, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_params(const MeshDev& m, int np, StageParams* sp5, double* t_dev, const double* ck, double dt,
+                               unsigned* ticket, cudaStream_t st) {
+  StepCoeffs c;
+  for (int k = 0; k < 5; ++k) c.c[k] = ck[k];
+  step_params_kernel<<<5, 64, 0, st>>>(m, np, sp5, t_dev, c, dt, ticket);
   return cudaGetLastError();
 }
 
