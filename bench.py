@@ -5,8 +5,9 @@ A step is one low-storage RK4 step (five stages) of the interface-heavy single s
 two blocks of 4 x 256 x 256 hexahedra (524,288 elements, 65,536 sliding faces per side),
 N = 5 (113.2 M DOF), FP32 state with FP64 mapping and mortar matrices, moving block at
 v = 0.37, smooth random initial field of 8 seeded Fourier modes per primitive variable.
-Every stage runs the mapper/mortar-matrix kernel, the fused interface kernel and the
-element kernel (volume, surface, RK update), replayed from a CUDA graph.
+Every RK step runs the step-parameter kernel once (mapper and mortar matrices of its five
+stages) and every stage the fused interface kernel and the element kernel (volume, surface,
+RK update), replayed from a CUDA graph.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload interface-heavy|serving|cylinder] [--precision fp32|fp64]

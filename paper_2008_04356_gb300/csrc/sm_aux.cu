@@ -104,7 +104,10 @@ __global__ void gather_traces_kernel(const MeshDev m, int np, const T* __restric
     const bool upper = (side == 0) == (ifc == 0);     // the element's xi^3 = +1 layer
     const long long e = encode_elem(m, side, ix, iy, iz);
     const T val = U[(e * 5 + v) * nn + (upper ? np2 * (np - 1) : 0) + ab];
-    (side ? Tm : Ts)[w] = (ifc == 1 && v == 1) ? -val : val;
+    // FP32 with an even row length: rows interleaved in pairs (trace_node)
+    const int i = ab % np, q = ab / np;
+    const int node = (sizeof(T) == 4 && (np & 1) == 0) ? (q >> 1) * 2 * np + 2 * i + (q & 1) : ab;
+    (side ? Tm : Ts)[w - ab + node] = (ifc == 1 && v == 1) ? -val : val;
   }
 }
 

@@ -74,9 +74,8 @@ sliding_interface_batch_kernel(const BatchSolveDev* __restrict__ bs, const int* 
   if constexpr (B::FUSED) {
     using C = IfFusedCfg<N, TL>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* sBuf = reinterpret_cast<float*>(smem_raw);   // [NBUF][TBUF] trace buffers
-    float* sF = sBuf + C::NBUF * C::TBUF;
-    float* sO = sF + C::SFSZ;
+    float* smem = reinterpret_cast<float*>(smem_raw);   // table and trace buffers, mortar fluxes
+    float* sF = smem + C::NTAB * C::TAB + C::NBUF * C::TBUF;
     // a work item's solve, its buffers at this stage and its tile coordinates
     auto locate = [&](int item, int* ty, int* tz) -> const BatchSolveDev& {
       const int s = find_solve(s_off, nsolve, item);
@@ -86,23 +85,18 @@ sliding_interface_batch_kernel(const BatchSolveDev* __restrict__ bs, const int* 
       return b;
     };
     fused_pipeline<N, TL>(
-        blockIdx.x, gridDim.x, total, sBuf,
-        [&](int item, float* dst) {
+        blockIdx.x, gridDim.x, total, smem,
+        [&](int item, float* tab, float* tr) {
           int ty, tz;
           const BatchSolveDev& b = locate(item, &ty, &tz);
           const int c = b.cur ^ (stage & 1);
           fused_tile_stage<N, TL>(b.m, b.sp, (const float*)b.U[c], (const float*)b.Ts, (const float*)b.Tm, ty, tz,
-                                  dst, tid);
+                                  tab, tr, tid);
         },
-        [&](int item, const float* sB) {
+        [&](int item, const float* tab, const float* tr) {
           int ty, tz;
           const BatchSolveDev& b = locate(item, &ty, &tz);
-          fused_tile_compute<N, RIEM, TL>(b.m, b.sp, (float*)b.Fs, (float*)b.Fm, ty, tz, sB, sF, sO, tid);
-        },
-        [&](int item) {
-          int ty, tz;
-          const BatchSolveDev& b = locate(item, &ty, &tz);
-          fused_tile_store<N, TL>(b.m, b.sp, (float*)b.Fs, (float*)b.Fm, ty, tz, sO, tid);
+          fused_tile_compute<N, RIEM, TL>(b.m, b.sp, (float*)b.Fs, (float*)b.Fm, ty, tz, tab, tr, sF, tid);
         });
   } else {
     for (int item = blockIdx.x; item < total; item += gridDim.x) {

@@ -38,11 +38,11 @@ struct StageParams {
   double sig_s, sig_m;
   double mat[8][SM_MAXNP * SM_MAXNP];
   float mat_f[8][SM_MAXNP * SM_MAXNP];
-  // the FP32 operators as the float pairs the FP32 interface kernel reads, four tables of
-  // sm_pair_stride(np) floats: table g = 0, 1 forward pairs of mortar i_sub = g,
-  // [i][j] = (Ps_g[j][i], Pm_(3-g)[j][i]); table g = 2, 3 back pairs of side g - 2,
-  // [j][i] = (B_lo[i][j], B_hi[i][j]); rows of sm_pair_row(np) pairs
-  alignas(16) float pair_f[4 * 144];
+  // the FP32 operators as the FP32 interface kernel reads them (np even): the entries of
+  // rows 2 h and 2 h + 1 of matrix k at column c, each duplicated into a float pair (its
+  // operand for two node rows at once), as one float4:
+  // pair_f[4 ((k np/2 + h) np + c) + {0, 1, 2, 3}] = mat_f[k] at (2h, c), (2h, c), (2h+1, c), (2h+1, c)
+  alignas(16) float pair_f[16 * SM_MAXNP * SM_MAXNP];
   // cylindrical interface: cos, sin of the rotor angle phi = -delta, and of the angles
   // w Theta - phi that carry a stator face seen through w periodic wraps into the rotor's
   // frame, for w = w0 and w0 + 1 (w0 = floor((-n-1) / n_par), the smallest wrap count)
@@ -53,10 +53,15 @@ struct StageParams {
   float arot_f[2][2];
 };
 
-// Layout of StageParams::pair_f: pairs per row (even) and floats per table (16 mod 32, so
-// that two tables read by one warp fall in different banks).
-__host__ __device__ constexpr int sm_pair_row(int np) { return np + (np & 1); }
-__host__ __device__ constexpr int sm_pair_stride(int np) { return ((2 * sm_pair_row(np) * np + 31) / 32) * 32 + 16; }
+// Offset of node (i, q) (i along the sliding direction, q across it) in one variable's block
+// of a compact interface trace: rows q in order (i fastest), except for FP32 states with an
+// even number of nodes per row, whose rows are interleaved in pairs (2 qp, 2 qp + 1) so that
+// the FP32 interface kernel loads the same node of two rows as one float pair:
+// (q / 2) 2 np + 2 i + q mod 2.
+template <typename T, int NP>
+__host__ __device__ constexpr int trace_node(int i, int q) {
+  return (sizeof(T) == 4 && NP % 2 == 0) ? (q >> 1) * 2 * NP + 2 * i + (q & 1) : i + NP * q;
+}
 
 // Per-precision constants of the discrete operator, precomputed on the host so that the
 // kernels do no FP64 arithmetic in FP32 mode.
@@ -357,6 +362,62 @@ __device__ __forceinline__ void rusanov_outward(const T uin[5], const T uout[5],
   const T a = fmax(fabs(wi) + ci, fabs(wo) + co);
 #pragma unroll
   for (int k = 0; k < 5; ++k) F[k] = T(0.5) * (Fi[k] + Fo[k]) - T(0.5) * a * (uout[k] - uin[k]);
+}
+
+// ---- packed FP32 arithmetic (fma/add/mul.rn.f32x2: two IEEE operations per instruction) ----
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b as fma(b, -1, a): exact product, one rounding, the same as the subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, p2(-1.0f), a); }
+
+struct Prim2 { float2 ir, u[3], p; };
+
+// Primitives of two states at once (the FP32 reciprocal of Prec<float>::rcp per component).
+__device__ __forceinline__ Prim2 primitives2(const float2 (&U)[5], const float gm1) {
+  Prim2 q;
+  q.ir = make_float2(Prec<float>::rcp(U[0].x), Prec<float>::rcp(U[0].y));
+  q.u[0] = mul2(U[1], q.ir);
+  q.u[1] = mul2(U[2], q.ir);
+  q.u[2] = mul2(U[3], q.ir);
+  float2 ke = mul2(U[1], q.u[0]);
+  ke = fma2(U[2], q.u[1], ke);
+  ke = fma2(U[3], q.u[2], ke);
+  q.p = mul2(p2(gm1), fma2(p2(-0.5f), ke, U[4]));
+  return q;
+}
+
+// Rusanov flux of two independent face nodes at once along the outward normal n = sgn e_ax
+// of the element that holds uin, ALE form with the normal grid speed vgn (each component the
+// same IEEE operations as a one-node evaluation of these formulas):
+//   F* = (F(uin).n + F(uout).n) / 2 - a (uout - uin) / 2,
+//   a = max(|v_in.n - vgn| + c_in, |v_out.n - vgn| + c_out).
+__device__ __forceinline__ void rusanov_outward2(const float2 (&uin)[5], const float2 (&uout)[5], const int ax,
+                                                 const float sgn, const float vgn, const float gamma,
+                                                 float2 (&F)[5]) {
+  const Prim2 qi = primitives2(uin, gamma - 1.0f), qo = primitives2(uout, gamma - 1.0f);
+  const float2 sg = p2(sgn);
+  const float2 uni = mul2(sg, ax == 0 ? qi.u[0] : (ax == 1 ? qi.u[1] : qi.u[2]));
+  const float2 uno = mul2(sg, ax == 0 ? qo.u[0] : (ax == 1 ? qo.u[1] : qo.u[2]));
+  const float2 wi = sub2(uni, p2(vgn)), wo = sub2(uno, p2(vgn));
+  const float2 pni = mul2(sg, qi.p), pno = mul2(sg, qo.p);
+  float2 t[5];
+  t[0] = add2(mul2(uin[0], wi), mul2(uout[0], wo));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float2 fi = k == ax ? fma2(uin[1 + k], wi, pni) : mul2(uin[1 + k], wi);
+    const float2 fo = k == ax ? fma2(uout[1 + k], wo, pno) : mul2(uout[1 + k], wo);
+    t[1 + k] = add2(fi, fo);
+  }
+  t[4] = add2(fma2(qi.p, uni, mul2(uin[4], wi)), fma2(qo.p, uno, mul2(uout[4], wo)));
+  const float2 ai = mul2(mul2(p2(gamma), qi.p), qi.ir), ao = mul2(mul2(p2(gamma), qo.p), qo.ir);
+  const float cix = Prec<float>::sqrt_(ai.x), ciy = Prec<float>::sqrt_(ai.y);
+  const float cox = Prec<float>::sqrt_(ao.x), coy = Prec<float>::sqrt_(ao.y);
+  const float2 mha = make_float2(-0.5f * fmaxf(fabsf(wi.x) + cix, fabsf(wo.x) + cox),
+                                 -0.5f * fmaxf(fabsf(wi.y) + ciy, fabsf(wo.y) + coy));
+#pragma unroll
+  for (int k = 0; k < 5; ++k) F[k] = fma2(mha, sub2(uout[k], uin[k]), mul2(p2(0.5f), t[k]));
 }
 
 // Cyclic rotation of the momentum components that brings physical axis ax (0 = x, 1 = y,

@@ -92,9 +92,15 @@ __device__ __forceinline__ void store_line(T* p, const T (&r)[NP]) {
 // element kernels has its own copy, filled once per device through upload_dhat_here().
 static __constant__ float c_dhat_f[7][SM_MAXNP * SM_MAXNP];
 static __constant__ double c_dhat_d[7][SM_MAXNP * SM_MAXNP];
+// the FP32 entries duplicated into float pairs (operands of the paired line contractions)
+static __constant__ float2 c_dhat_f2[7][SM_MAXNP * SM_MAXNP];
 
 static inline cudaError_t upload_dhat_here(const float* f, const double* d) {
   cudaError_t e = cudaMemcpyToSymbol(c_dhat_f, f, sizeof(float) * 7 * SM_MAXNP * SM_MAXNP);
+  if (e != cudaSuccess) return e;
+  float2 f2[7 * SM_MAXNP * SM_MAXNP];
+  for (int r = 0; r < 7 * SM_MAXNP * SM_MAXNP; ++r) f2[r] = make_float2(f[r], f[r]);
+  e = cudaMemcpyToSymbol(c_dhat_f2, f2, sizeof(f2));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_dhat_d, d, sizeof(double) * 7 * SM_MAXNP * SM_MAXNP);
 }
@@ -126,6 +132,35 @@ __device__ __forceinline__ void contract_lines_inplace(T* sF, int tid) {
       ov[a] = s;
     }
     store_line<T, NP>(line, ov);
+  }
+  if constexpr (sizeof(T) == 4 && NP % 2 == 0) {
+    // FP32, even line length: the xi^2 and xi^3 lines of nodes i and i + 1 (i even) are
+    // adjacent in memory, so a thread takes both as float pairs (one 8-byte access per node)
+    // and contracts them with packed multiply-adds (the same per-line operations in order).
+#pragma unroll
+    for (int d = 1; d < 3; ++d) {
+      constexpr int NPH = NP2 / 2;
+      const int stride2 = d == 1 ? NP / 2 : NP2 / 2;
+      for (int w = tid; w < EPB * 5 * NPH; w += THREADS) {
+        const int l2 = w / (5 * NPH);
+        const int rr = w - l2 * 5 * NPH;
+        const int v = rr / NPH, q = 2 * (rr - v * NPH);
+        // xi^2 lines (i, k), (i+1, k): base i + NP^2 k; xi^3 lines (i, j), (i+1, j): base i + NP j
+        const int base = d == 1 ? (q % NP) + NP2 * (q / NP) : q;
+        float2* line = reinterpret_cast<float2*>(sF + l2 * 15 * NN + (5 * d + v) * NN + base);
+        float2 rv[NP];
+#pragma unroll
+        for (int l = 0; l < NP; ++l) rv[l] = line[l * stride2];
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int l = 0; l < NP; ++l) s2 = __ffma2_rn(c_dhat_f2[N - 1][a * SM_MAXNP + l], rv[l], s2);
+          line[a * stride2] = s2;
+        }
+      }
+    }
+    return;
   }
 #pragma unroll
   for (int d = 1; d < 3; ++d) {
@@ -345,7 +380,7 @@ __device__ __forceinline__ void element_surface_update(const MeshDev& m, const T
         f = p.iz * m.ny + p.iy;
       }
       if (ix == (blk ? 0 : m.nxs - 1)) {
-        T* dst = (blk ? Tm : Ts) + (long long)f * 5 * NP2 + i + NP * j;
+        T* dst = (blk ? Tm : Ts) + (long long)f * 5 * NP2 + trace_node<T, NP>(i, j);
 #pragma unroll
         for (int v = 0; v < 5; ++v) dst[v * NP2] = un[v];
       }
@@ -363,7 +398,7 @@ __device__ __forceinline__ void element_surface_update(const MeshDev& m, const T
         f = p.iz * m.ny + p.iy;
       }
       if (ix == (blk ? m.nxm - 1 : 0)) {
-        T* dst = reinterpret_cast<T*>(blk ? m.Tm2 : m.Ts2) + (long long)f * 5 * NP2 + i + NP * j;
+        T* dst = reinterpret_cast<T*>(blk ? m.Tm2 : m.Ts2) + (long long)f * 5 * NP2 + trace_node<T, NP>(i, j);
 #pragma unroll
         for (int v = 0; v < 5; ++v) dst[v * NP2] = v == 1 ? -un[v] : un[v];
       }

@@ -1,5 +1,5 @@
-// Single-solve launch of the fused sliding-interface kernel (bodies in sm_iface.cuh): the
-// register-fused tile for FP32 states at odd N, the staged tile otherwise.
+// Single-solve launch of the fused sliding-interface kernel (bodies in sm_iface.cuh): for FP32
+// states at odd N the warp-owned rows, the staged tile otherwise.
 #include "sm_iface.cuh"
 
 namespace {
@@ -16,10 +16,6 @@ int fused_sms() {
   }
   return sms[dev];
 }
-// resident CTAs per SM of the FP32 interface kernel <N, RIEM, TF> (occupancy calculator,
-// once per instantiation; the shared-memory attribute is set by prepare_interface first)
-template <int N, int RIEM, int TF>
-int fused_ctas_per_sm();
 
 template <int N, typename T, int RIEM>
 __global__ void __launch_bounds__(IfCfg<N>::THREADS, sizeof(T) == 4 ? IfCfg<N>::MINB : 1)
@@ -28,23 +24,14 @@ sliding_interface_kernel(const MeshDev m, const StageParams* __restrict__ sp, co
   interface_tile<N, T, RIEM, IfCfg<N>::TF>(m, sp, U, Fs, Fm, blockIdx.x, blockIdx.y, nullptr, Ts, Tm);
 }
 
-// FP32, odd N: the register-fused tile
 template <int N, int RIEM, int TF>
-__global__ void __launch_bounds__(IfFusedCfg<N, TF>::THREADS, IfFusedCfg<N, TF>::MINB)
-sliding_interface_fused_kernel(const MeshDev m, const StageParams* __restrict__ sp, const float* __restrict__ U,
-                               float* __restrict__ Fs, float* __restrict__ Fm, const float* __restrict__ Ts,
-                               const float* __restrict__ Tm) {
-  interface_fused_loop<N, RIEM, TF>(m, sp, U, Fs, Fm, Ts, Tm);
-}
-
-template <int N, int RIEM, int TF>
-int fused_ctas_per_sm() {
+int warp_ctas_per_sm() {
   static int n = 0;
   if (n == 0) {
-    using F = IfFusedCfg<N, TF>;
+    using W = IfWarpCfg<N, TF>;
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sliding_interface_fused_kernel<N, RIEM, TF>, F::THREADS,
-                                                      F::smem_bytes) != cudaSuccess || v <= 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sliding_interface_warp_kernel<N, RIEM, TF>, W::THREADS,
+                                                      W::smem_bytes) != cudaSuccess || v <= 0)
       v = 1;
     n = v;
   }
@@ -55,12 +42,12 @@ template <int N, typename T, int RIEM>
 cudaError_t launch_if_t(const MeshDev& m, const StageParams* sp, const void* U, void* Fs, void* Fm, cudaStream_t st,
                         const void* Ts, const void* Tm) {
   if constexpr (sizeof(T) == 4 && N % 2 == 1) {
-    using F = IfFusedCfg<N, IfFusedTF<N>::TF>;
-    const long long tiles = (long long)((m.ny + F::TF - 1) / F::TF) * m.nz;
+    using W = IfWarpCfg<N, SM_IF_WARP_TF>;
+    const long long tiles = (long long)((m.ny + W::TF - 1) / W::TF) * m.nz;
     if (tiles <= 0) return cudaSuccess;
-    const long long cap = (long long)fused_ctas_per_sm<N, RIEM, F::TF>() * fused_sms();
+    const long long cap = (long long)warp_ctas_per_sm<N, RIEM, W::TF>() * fused_sms();
     const long long grid = tiles < cap ? tiles : cap;
-    sliding_interface_fused_kernel<N, RIEM, F::TF><<<(unsigned)grid, F::THREADS, F::smem_bytes, st>>>(
+    sliding_interface_warp_kernel<N, RIEM, W::TF><<<(unsigned)grid, W::THREADS, W::smem_bytes, st>>>(
         m, sp, (const float*)U, (float*)Fs, (float*)Fm, (const float*)Ts, (const float*)Tm);
     return cudaGetLastError();
   } else {
@@ -75,12 +62,15 @@ cudaError_t launch_if_t(const MeshDev& m, const StageParams* sp, const void* U, 
 template <int N, typename T>
 cudaError_t prepare_if_t() {
   if constexpr (sizeof(T) == 4 && N % 2 == 1) {
-    using F = IfFusedCfg<N, IfFusedTF<N>::TF>;
-    cudaError_t f0 = cudaFuncSetAttribute(sliding_interface_fused_kernel<N, 0, F::TF>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem_bytes);
-    cudaError_t f1 = cudaFuncSetAttribute(sliding_interface_fused_kernel<N, 1, F::TF>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem_bytes);
-    return f0 != cudaSuccess ? f0 : f1;
+    using W = IfWarpCfg<N, SM_IF_WARP_TF>;
+    const cudaError_t r[2] = {
+        cudaFuncSetAttribute(sliding_interface_warp_kernel<N, 0, W::TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)W::smem_bytes),
+        cudaFuncSetAttribute(sliding_interface_warp_kernel<N, 1, W::TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)W::smem_bytes)};
+    for (cudaError_t e : r)
+      if (e != cudaSuccess) return e;
+    return cudaSuccess;
   } else {
     using C = IfCfg<N>;
     cudaError_t e0 = cudaFuncSetAttribute(sliding_interface_kernel<N, T, 0>,

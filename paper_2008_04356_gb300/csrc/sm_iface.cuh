@@ -188,74 +188,58 @@ __device__ __forceinline__ void interface_tile_euler(const MeshDev& m, const Sta
   }
 }
 
-// Register-fused Euler tile (FP32 state, N odd): the three steps of Sec. 3.3 with few
-// shared-memory round trips, in persistent CTAs that prefetch the traces of the next two
-// tiles with 16-byte cp.async while they compute the current one.  Per tile (TF static faces of one
-// perpendicular line plus one halo face per side):
-//   A. two threads per (mortar, row q), each for half of the row's NP mortar nodes: both
-//      sides' traces of all five variables are projected onto those nodes (Eq.
-//      projection_domain_mortar) into registers, as float pairs (static, moving) updated by
-//      packed FMAs, and the Riemann flux of each node follows at once, times the surface
-//      element;
-//   B. two threads per (side, face, row q), each for half of the row's face nodes: the
-//      face's two mortar flux rows are projected back (Eq. projection_mortar_domain; pairs
-//      (lower, upper mortar) summed at the end) into shared output blocks, which the CTA
-//      then copies to the face flux arrays with coalesced 16-byte stores.
-// A mortar's arithmetic does not depend on the tile it sits in (the halo mortar is computed
-// by both neighbouring tiles with the same operations), so results are independent of TF.
-// Lanes of a warp: in A 16 consecutive mortars x the two halves of one row (both halves
-// read the same trace values), in B 8 faces x 2 sides x 2 halves of one row; face blocks
-// at 4 mod 32 words, mortar blocks at 2 mod 32 and the operator tables 16 apart keep the
-// accesses of a warp in distinct banks.
+// Register-fused Euler tile (FP32 state, N odd) of the batched launch: the three steps of
+// Sec. 3.3 with few shared-memory round trips, in persistent CTAs that prefetch the traces
+// of the next work item with 16-byte cp.async while they compute the current one.  Per tile
+// (TF static faces of one perpendicular line plus one halo face per side):
+//   staging: the tile's static faces i0 .. i0+TF and moving faces i0-n-1 .. i0+TF-n-1 are
+//      (up to the periodic wrap of the line) contiguous runs of the compact trace arrays,
+//      copied as such, with the operator tables;
+//   A. one thread per (mortar, row pair, node pair): both sides' traces of all five
+//      variables are projected onto two mortar nodes (Eq. projection_domain_mortar) for two
+//      rows at once, and the Riemann fluxes of the two nodes follow, times the surface
+//      element (mortar_rows);
+//   B. one thread per (side, face, row pair, node pair): the face's two mortar flux rows are
+//      projected back (Eq. projection_mortar_domain) and stored to the face flux arrays
+//      (face_rows).
+// The work runs on float pairs over a pair of rows (q, q+1): the compact traces interleave
+// the rows of a pair (trace_node) and the operator tables hold every entry duplicated, two
+// rows per 16-byte entry, so the operands of the packed multiply-adds (fma.rn.f32x2) of two
+// nodes come in 16-byte loads, and the Riemann flux of the two rows is one paired
+// evaluation.  A mortar's arithmetic does not depend on the tile it sits in (the halo mortar
+// is computed by both neighbouring tiles with the same operations), so results are
+// independent of TF and identical to those of the single-solve kernel (warp-owned rows).
+#ifndef SM_IF_FUSED_REGS
+#define SM_IF_FUSED_REGS 96
+#endif
+// Each prefetch buffer carries its tile's operator tables (the tiles of a batched launch
+// belong to different solves).
 template <int N, int TFV> struct IfFusedCfg {
-  static_assert(N % 2 == 1, "the fused interface tile takes odd N (16-byte face blocks)");
+  static_assert(N % 2 == 1, "the fused interface tile takes odd N (rows in pairs)");
   static_assert(TFV % 8 == 0, "the fused interface tile takes TF = 8 k");
   static constexpr int NP = N + 1, NP2 = NP * NP, NN = NP * NP * NP;
+  static constexpr int NH = NP / 2;                              // row pairs = node pairs per row
   static constexpr int TF = TFV;
   static constexpr int NM = 2 * TF + 1;
-  static constexpr int H0 = NP / 2;                              // node halves of a row
-  static constexpr int NBA = 2 * TF / 16;                        // 16-mortar blocks (A)
-  static constexpr int NBB = TF / 8;                             // 8-face blocks (B)
-  static constexpr int ITEMS_A = 32 * NBA * NP + 2 * NP;         // + the halo mortar
-  static constexpr int ITEMS_B = 32 * NBB * NP;
-  static constexpr int THREADS = ((ITEMS_A + 31) / 32) * 32;
-  // resident CTAs per SM asked of the register allocator (about 80 registers a thread)
-#ifndef SM_IF_FUSED_REGS
-#define SM_IF_FUSED_REGS 80
-#endif
-  static constexpr int MINB = 65536 / (THREADS * SM_IF_FUSED_REGS) > 0 ? 65536 / (THREADS * SM_IF_FUSED_REGS) : 1;
+  static constexpr int ITEMS_A = NM * NH * NH;
+  static constexpr int ITEMS_B = 2 * TF * NH * NH;
+  static constexpr int THREADS = (((ITEMS_A > ITEMS_B ? ITEMS_A : ITEMS_B) + 31) / 32) * 32;
   static constexpr int TB = 5 * NP2;                             // one face's block (floats)
-#ifndef SM_IF_FUSED_PAD
-#define SM_IF_FUSED_PAD 1
-#endif
-  // face block stride: = 4 mod 32 (16-byte rows, conflict-free phase B stores), or unpadded
-  static constexpr int FS = SM_IF_FUSED_PAD ? TB + (36 - TB % 32) % 32 : TB;
-  static constexpr int MS = TB + (34 - TB % 32) % 32;            // = 2 mod 32
-  static constexpr int MR = sm_pair_row(NP);
-  static constexpr int MT = sm_pair_stride(NP);
-  static constexpr int TBUF = 4 * MT + 2 * (TF + 1) * FS;        // one prefetch buffer (floats)
+  static constexpr int MS = TB + (36 - TB % 32) % 32;            // mortar flux block stride, 4 mod 32
+  static constexpr int TAB = 16 * NP2;                           // duplicated operator tables
+  static constexpr int TBUF = 2 * (TF + 1) * TB;                 // one tile's traces (floats)
   static constexpr int SFSZ = ((NM * MS + 3) / 4) * 4;           // mortar fluxes
-  static constexpr int OSZ = 2 * TF * FS;                        // output blocks
-#ifndef SM_IF_FUSED_NBUF
-#define SM_IF_FUSED_NBUF 3
-#endif
-  static constexpr int NBUF = SM_IF_FUSED_NBUF;                  // trace buffers: NBUF - 1 tiles ahead
-  static constexpr size_t smem_floats = (size_t)NBUF * TBUF + SFSZ + OSZ;
+  static constexpr int NBUF = 2;                                 // the tile and the next one
+  static constexpr int NTAB = NBUF;                              // table copies
+  // resident CTAs per SM asked of the register allocator
+  static constexpr int MINB = 65536 / (THREADS * SM_IF_FUSED_REGS) > 0 ? 65536 / (THREADS * SM_IF_FUSED_REGS) : 1;
+  static constexpr size_t smem_floats = (size_t)NTAB * TAB + NBUF * TBUF + SFSZ;
   static constexpr size_t smem_bytes = sizeof(float) * smem_floats;
 };
-// default tile width of the single-solve FP32 launch (the batch autotuner picks 8 or 16)
-#ifndef SM_IF_FUSED_TF
-#define SM_IF_FUSED_TF 8
-#endif
-template <int N> struct IfFusedTF { static constexpr int TF = SM_IF_FUSED_TF; };
 
 __device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -265,228 +249,271 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int K> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
 }
-// Issues the asynchronous copies of one tile into buffer sB: the operator pair tables and the
-// traces of static faces i0 + r and moving faces i0 - n - 1 + r (mod n_par), r = 0..TFe,
-// from the compact arrays Ts / Tm or, when they are NULL, from the element node layers of U
-// (xi^3 = +1 static, xi^3 = -1 moving).
+
+// Copies the 16-byte chunks of cnt consecutive face blocks of a line of ny faces, starting at
+// face f0 (0 <= f0 < ny) and wrapping to face 0 at the end of the line, from the compact
+// arrays (line base src) into cnt consecutive smem blocks at dst; all threads take part.
+template <int TB, int THREADS>
+__device__ __forceinline__ void stage_run(float* dst, const float* __restrict__ src, const int f0, const int cnt,
+                                          const int ny, const int tid) {
+  const int n1 = min(cnt, ny - f0) * (TB / 4), n = cnt * (TB / 4);
+  const float* s1 = src + (long long)f0 * TB;
+  for (int c = tid; c < n; c += THREADS) cp_async_16(dst + 4 * c, c < n1 ? s1 + 4 * c : src + 4 * (c - n1));
+}
+
+// Issues the asynchronous copies of one tile: the duplicated operator tables into sTab (when
+// not NULL) and into sT the traces of static faces i0 + r and moving faces i0 - n - 1 + r
+// (mod n_par), r = 0..TFe, from the compact arrays Ts / Tm or, when they are NULL, from the
+// element node layers of U (xi^3 = +1 static, xi^3 = -1 moving; rows interleaved on the way).
 template <int N, int TF>
 __device__ __forceinline__ void fused_tile_stage(const MeshDev& m, const StageParams* __restrict__ sp,
                                                  const float* __restrict__ U, const float* __restrict__ Ts,
                                                  const float* __restrict__ Tm, const int tile_x, const int iz,
-                                                 float* sB, const int tid) {
+                                                 float* sTab, float* sT, const int tid) {
   using C = IfFusedCfg<N, TF>;
-  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, THREADS = C::THREADS;
-  constexpr int FS = C::FS, MT = C::MT, TB = C::TB;
+  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, THREADS = C::THREADS, TB = C::TB, TAB = C::TAB;
   const int ny = m.ny;
   const int i0 = tile_x * TF;
   const int TFe = min(TF, ny - i0);
   const int nmod = sp->n_mod;
-  for (int w = tid; w < MT; w += THREADS) cp_async_16(sB + 4 * w, sp->pair_f + 4 * w);
-  float* sT = sB + 4 * MT;
-  const int nslot = 2 * (TFe + 1);
+  if (sTab)
+    for (int w = tid; w < TAB / 4; w += THREADS) cp_async_16(sTab + 4 * w, sp->pair_f + 4 * w);
+  const int fm0 = i0 - nmod - 1 < 0 ? i0 - nmod - 1 + ny : i0 - nmod - 1;
   if (Ts) {
-    // compact traces: a face's 5 (N+1)^2 values are contiguous, TB / 4 chunks of 16 bytes;
-    // thread = (chunk, slot group)
-    constexpr int NC = TB / 4;
-    constexpr int G = THREADS / NC;
-    if (tid < G * NC) {
-      const int c = tid % NC;
-      for (int slot = tid / NC; slot < nslot; slot += G) {
-        const int side = slot > TFe, r = slot - side * (TFe + 1);
-        int f = side ? i0 - nmod - 1 + r : i0 + r;
-        f = f < 0 ? f + ny : (f >= ny ? f - ny : f);
-        cp_async_16(sT + (side * (TF + 1) + r) * FS + 4 * c, (side ? Tm : Ts) + ((long long)iz * ny + f) * TB + 4 * c);
-      }
-    }
+    const long long line = (long long)iz * ny * TB;
+    stage_run<TB, THREADS>(sT, Ts + line, i0, TFe + 1, ny, tid);
+    stage_run<TB, THREADS>(sT + (TF + 1) * TB, Tm + line, fm0, TFe + 1, ny, tid);
   } else {
-    constexpr int NV = NP2 / 2;
-    for (int w = tid; w < nslot * 5 * NV; w += THREADS) {
-      const int k = w % NV;
-      const int rest = w / NV;
+    const int nslot = 2 * (TFe + 1);
+    for (int w = tid; w < nslot * TB; w += THREADS) {
+      const int ab = w % NP2;
+      const int rest = w / NP2;
       const int v = rest % 5;
       const int sr = rest / 5;
       const int side = sr >= TFe + 1, r = sr - side * (TFe + 1);
-      int f = side ? i0 - nmod - 1 + r : i0 + r;
-      f = f < 0 ? f + ny : (f >= ny ? f - ny : f);
+      int f = side ? fm0 + r : i0 + r;
+      f = f >= ny ? f - ny : f;
       const float* src = U + encode_elem(m, side, side ? 0 : m.nxs - 1, f, iz) * 5 * NN + (side ? 0 : NP2 * N) +
-                         (long long)v * NN + 2 * k;
-      cp_async_8(sT + (side * (TF + 1) + r) * FS + v * NP2 + 2 * k, src);
+                         (long long)v * NN + ab;
+      cp_async_4(sT + (side * (TF + 1) + r) * TB + v * NP2 + trace_node<float, NP>(ab % NP, ab / NP), src);
     }
   }
 }
 
-// Phase A for the NH mortar nodes j0 .. j0+NH-1 of row q of mortar mi.
-template <int N, int RIEM, int TF, int NH>
-__device__ __forceinline__ void fused_mortar_nodes(const float* sB, float* sF, const int mi, const int q,
-                                                   const int j0, const float sJ, const float gamma) {
+// Phase A for one mortar (lower part of its static face if isub = 0, upper part if 1), rows
+// 2 qp and 2 qp + 1, mortar nodes 2 jp and 2 jp + 1: ts / tm point at the row pair of the
+// static / moving face's trace, variables VIN floats apart (rows interleaved, trace_node);
+// the mortar fluxes times the surface element go to out (the mortar's row pair, variables
+// VOUT floats apart).
+template <int N, int RIEM, int VIN, int VOUT>
+__device__ __forceinline__ void mortar_rows(const float* sTab, const float* tsp, const float* tmp, float* outp,
+                                            const int isub, const int jp, const float sJ, const float gamma) {
+  constexpr int NP = N + 1, NH = NP / 2;
+  static_assert(VIN % 4 == 0 && VOUT % 4 == 0, "16-byte rows");
+  const float4* ts = reinterpret_cast<const float4*>(tsp);
+  const float4* tm = reinterpret_cast<const float4*>(tmp);
+  // the static lower mortar meets the moving face's upper part and vice versa:
+  // tables Ps_isub (slot isub) and Pm_(1-isub) (slot 3 - isub), rows j = 2 jp, 2 jp + 1
+  const float4* PT = reinterpret_cast<const float4*>(sTab);
+  const float4* ps = PT + (isub * NH + jp) * NP;
+  const float4* pm = PT + ((3 - isub) * NH + jp) * NP;
+  float2 s0[5], s1[5], m0[5], m1[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) s0[v] = s1[v] = m0[v] = m1[v] = make_float2(0.f, 0.f);
+  // static side, then moving side: nodes 2 ih and 2 ih + 1 of both rows per 16-byte load
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const float4* t = side ? tm : ts;
+    const float4* P = side ? pm : ps;
+    float2* o0 = side ? m0 : s0;
+    float2* o1 = side ? m1 : s1;
+#pragma unroll
+    for (int ih = 0; ih < NH; ++ih) {
+      float4 x4[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) x4[v] = t[v * (VIN / 4) + ih];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 a = P[2 * ih + h];
+        const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const float2 x = h ? make_float2(x4[v].z, x4[v].w) : make_float2(x4[v].x, x4[v].y);
+          o0[v] = fma2(a0, x, o0[v]);
+          o1[v] = fma2(a1, x, o1[v]);
+        }
+      }
+    }
+  }
+  float2 F0[5], F1[5];
+  if constexpr (RIEM == 0) {
+    // static outward normal +x, no normal grid speed on the interface: both rows at once
+    rusanov_outward2(s0, m0, 0, 1.0f, 0.0f, gamma, F0);
+    rusanov_outward2(s1, m1, 0, 1.0f, 0.0f, gamma, F1);
+  } else {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      float QL[5], QR[5], f[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const float2 l = h < 2 ? s0[v] : s1[v], r = h < 2 ? m0[v] : m1[v];
+        QL[v] = (h & 1) ? l.y : l.x;
+        QR[v] = (h & 1) ? r.y : r.x;
+      }
+      riemann_axis<float, 0, 1>(QL, QR, 0.f, gamma, f);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        float2& o = h < 2 ? F0[v] : F1[v];
+        if (h & 1) o.y = f[v];
+        else o.x = f[v];
+      }
+    }
+  }
+  float4* out = reinterpret_cast<float4*>(outp) + jp;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const float2 g0 = mul2(p2(sJ), F0[v]), g1 = mul2(p2(sJ), F1[v]);
+    out[v * (VOUT / 4)] = make_float4(g0.x, g0.y, g1.x, g1.y);
+  }
+}
+
+// Phase A for mortar mi of a staged tile (layout of fused_tile_stage).
+template <int N, int RIEM, int TF>
+__device__ __forceinline__ void fused_mortar_rows(const float* sTab, const float* sT, float* sF, const int mi,
+                                                  const int qp, const int jp, const float sJ, const float gamma) {
   using C = IfFusedCfg<N, TF>;
-  constexpr int NP = C::NP, NP2 = C::NP2, FS = C::FS, MS = C::MS, MR = C::MR, MT = C::MT;
+  constexpr int NP = C::NP, NP2 = C::NP2, TB = C::TB, MS = C::MS;
   const int isub = mi & 1, rs = mi >> 1, rm = rs + isub;
-  const float* sT = sB + 4 * MT;
-  const float* ts = sT + rs * FS + q * NP;
-  const float* tm = sT + (TF + 1 + rm) * FS + q * NP;
-  // the static lower mortar meets the moving face's upper part and vice versa
-  const float2* PF = reinterpret_cast<const float2*>(sB + isub * MT) + j0;
-  float2 acc[5][NH];
+  mortar_rows<N, RIEM, NP2, NP2>(sTab, sT + rs * TB + qp * 2 * NP, sT + (TF + 1 + rm) * TB + qp * 2 * NP,
+                                 sF + mi * MS + qp * 2 * NP, isub, jp, sJ, gamma);
+}
+
+// Phase B for one face on one side, rows 2 qp and 2 qp + 1, face nodes 2 ip and 2 ip + 1: the
+// face's lower and upper mortar flux rows (flo / fhi: the row pair, variables VIN floats
+// apart) projected back and stored to the face flux array at dst (the face's block).
+template <int N, int VIN>
+__device__ __forceinline__ void face_rows(const float* sTab, const float* flop, const float* fhip,
+                                          float* __restrict__ dst, const int side, const int qp, const int ip) {
+  constexpr int NP = N + 1, NP2 = NP * NP, NH = NP / 2;
+  static_assert(VIN % 4 == 0, "16-byte rows");
+  const float4* flo = reinterpret_cast<const float4*>(flop);
+  const float4* fhi = reinterpret_cast<const float4*>(fhip);
+  // tables B_lo, B_hi of the side (slots 4 + 2 side, 5 + 2 side), rows i = 2 ip, 2 ip + 1
+  const float4* PT = reinterpret_cast<const float4*>(sTab);
+  const float4* bl = PT + ((4 + 2 * side) * NH + ip) * NP;
+  const float4* bh = PT + ((5 + 2 * side) * NH + ip) * NP;
+  float2 a0[5], a1[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v)
+  for (int v = 0; v < 5; ++v) a0[v] = a1[v] = make_float2(0.f, 0.f);
+  // lower mortar, then upper mortar: nodes 2 jh and 2 jh + 1 of both rows per 16-byte load
 #pragma unroll
-    for (int j = 0; j < NH; ++j) acc[v][j] = make_float2(0.f, 0.f);
+  for (int part = 0; part < 2; ++part) {
+    const float4* f = part ? fhi : flo;
+    const float4* B = part ? bh : bl;
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    float2 pp[NH];
+    for (int jh = 0; jh < NH; ++jh) {
+      float4 x4[5];
 #pragma unroll
-    for (int j = 0; j < NH; ++j) pp[j] = PF[i * MR + j];
+      for (int v = 0; v < 5; ++v) x4[v] = f[v * (VIN / 4) + jh];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const float2 ab = make_float2(ts[v * NP2 + i], tm[v * NP2 + i]);
+      for (int h = 0; h < 2; ++h) {
+        const float4 l = B[2 * jh + h];
+        const float2 l0 = make_float2(l.x, l.y), l1 = make_float2(l.z, l.w);
 #pragma unroll
-      for (int j = 0; j < NH; ++j) acc[v][j] = __ffma2_rn(pp[j], ab, acc[v][j]);
+        for (int v = 0; v < 5; ++v) {
+          const float2 x = h ? make_float2(x4[v].z, x4[v].w) : make_float2(x4[v].x, x4[v].y);
+          a0[v] = fma2(l0, x, a0[v]);
+          a1[v] = fma2(l1, x, a1[v]);
+        }
+      }
     }
   }
-  float* out = sF + mi * MS + q * NP + j0;
+  // rows q = 2 qp (.x) and 2 qp + 1 (.y) of nodes i = 2 ip, 2 ip + 1, outward sign of the side
+  const float sg = side ? -1.0f : 1.0f;
 #pragma unroll
-  for (int j = 0; j < NH; ++j) {
-    float QL[5], QR[5], F[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) { QL[v] = acc[v][j].x; QR[v] = acc[v][j].y; }
-    riemann_axis<float, 0, RIEM>(QL, QR, 0.f, gamma, F);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) out[v * NP2 + j] = F[v] * sJ;
+  for (int v = 0; v < 5; ++v) {
+    float* d = dst + v * NP2 + 2 * qp * NP + 2 * ip;
+    *reinterpret_cast<float2*>(d) = make_float2(sg * a0[v].x, sg * a1[v].x);
+    *reinterpret_cast<float2*>(d + NP) = make_float2(sg * a0[v].y, sg * a1[v].y);
   }
 }
 
-// Phase B for the NH face nodes i0n .. i0n+NH-1 of row q of face r on one side, into the
-// face's shared output block o (the row's first node).
-template <int N, int TF, int NH>
-__device__ __forceinline__ void fused_face_nodes(const float* sB, const float* sF, float* o, const int r,
-                                                 const int side, const int q, const int i0n) {
+// Phase B for face r of a staged tile on one side.
+template <int N, int TF>
+__device__ __forceinline__ void fused_face_rows(const float* sTab, const float* sF, float* __restrict__ dst,
+                                                const int r, const int side, const int qp, const int ip) {
   using C = IfFusedCfg<N, TF>;
-  constexpr int NP = C::NP, NP2 = C::NP2, MS = C::MS, MR = C::MR, MT = C::MT;
-  const float* flo = sF + (2 * r + side) * MS + q * NP;
-  const float* fhi = flo + MS;
-  const float2* PB = reinterpret_cast<const float2*>(sB + (2 + side) * MT) + i0n;
-  float2 acc[5][NH];
-#pragma unroll
-  for (int v = 0; v < 5; ++v)
-#pragma unroll
-    for (int i = 0; i < NH; ++i) acc[v][i] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    float2 bb[NH];
-#pragma unroll
-    for (int i = 0; i < NH; ++i) bb[i] = PB[j * MR + i];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const float2 ab = make_float2(flo[v * NP2 + j], fhi[v * NP2 + j]);
-#pragma unroll
-      for (int i = 0; i < NH; ++i) acc[v][i] = __ffma2_rn(bb[i], ab, acc[v][i]);
-    }
-  }
-#pragma unroll
-  for (int v = 0; v < 5; ++v)
-#pragma unroll
-    for (int i = 0; i < NH; ++i) {
-      const float x = acc[v][i].x + acc[v][i].y;
-      o[v * NP2 + i0n + i] = side ? -x : x;
-    }
+  constexpr int NP = C::NP, NP2 = C::NP2, MS = C::MS;
+  face_rows<N, NP2>(sTab, sF + (2 * r + side) * MS + qp * 2 * NP, sF + (2 * r + 1 + side) * MS + qp * 2 * NP, dst,
+                    side, qp, ip);
 }
 
-// Phases A and B of one tile whose buffer sB has landed (see fused_tile_stage), into the
-// output blocks sO; ends with a barrier, after which sB and sF are free.
+// Phases A and B of one tile whose tables sTab and traces sT have landed (see
+// fused_tile_stage), the face fluxes stored to Fs / Fm; one barrier between the phases (the
+// caller's next barrier ends the use of sTab, sT and sF).
 template <int N, int RIEM, int TF>
 __device__ __forceinline__ void fused_tile_compute(const MeshDev& m, const StageParams* __restrict__ sp,
                                                    float* __restrict__ Fs, float* __restrict__ Fm, const int tile_x,
-                                                   const int iz, const float* sB, float* sF, float* sO, const int tid) {
+                                                   const int iz, const float* sTab, const float* sT, float* sF,
+                                                   const int tid) {
   using C = IfFusedCfg<N, TF>;
-  constexpr int NP = C::NP, NP2 = C::NP2, H0 = C::H0, FS = C::FS, TB = C::TB;
+  constexpr int NH = C::NH, NM = C::NM, TB = C::TB;
   const int ny = m.ny;
   const int i0 = tile_x * TF;
   const int TFe = min(TF, ny - i0);
   const int nme = 2 * TFe + 1;
   const int nmod = sp->n_mod;
 
-  // A. projections of both sides and the mortar Riemann fluxes (static outward normal +x)
+  // A. item = mortar fastest, then node pair, then row pair
   const float sJ = m.cf[MC_SJ_IF];
   const float gamma = m.cf[MC_GAMMA];
-  if (tid < C::ITEMS_A) {
-    int mi, q, h;
-    if (tid < 32 * C::NBA * NP) {
-      const int rest = tid >> 5;
-      mi = 16 * (rest / NP) + (tid & 15);
-      q = rest % NP;
-      h = (tid >> 4) & 1;
-    } else {
-      const int hw = tid - 32 * C::NBA * NP;   // the halo mortar 2 TF
-      mi = 2 * TF;
-      q = hw % NP;
-      h = hw / NP;
-    }
-    // both halves in one call (H0 = H1): the two half-warps run the same instructions
-    if (mi < nme) fused_mortar_nodes<N, RIEM, TF, H0>(sB, sF, mi, q, h * H0, sJ, gamma);
+  for (int w = tid; w < C::ITEMS_A; w += C::THREADS) {
+    const int mi = w % NM;
+    const int rest = w / NM;
+    const int jp = rest % NH, qp = rest / NH;
+    if (mi < nme) fused_mortar_rows<N, RIEM, TF>(sTab, sT, sF, mi, qp, jp, sJ, gamma);
   }
   __syncthreads();
 
-  // B. back-projection: static face i0 + r from mortars (2r, 2r+1); moving face i0 - n + r
-  // from mortars 2r+1 (its lower part) and 2r+2 (its upper part), with the opposite sign
-  if (tid < C::ITEMS_B) {
-    const int rest = tid >> 5;
-    const int r = 8 * (rest / NP) + (tid & 7);
-    const int q = rest % NP;
-    const int side = (tid >> 3) & 1, h = (tid >> 4) & 1;
-    if (r < TFe) fused_face_nodes<N, TF, H0>(sB, sF, sO + (side * TF + r) * FS + q * NP, r, side, q, h * H0);
-  }
-  __syncthreads();
-}
-
-// Copies the tile's face flux blocks from sO to the face flux arrays (16-byte stores).
-template <int N, int TF>
-__device__ __forceinline__ void fused_tile_store(const MeshDev& m, const StageParams* __restrict__ sp,
-                                                 float* __restrict__ Fs, float* __restrict__ Fm, const int tile_x,
-                                                 const int iz, const float* sO, const int tid) {
-  using C = IfFusedCfg<N, TF>;
-  constexpr int FS = C::FS, TB = C::TB, THREADS = C::THREADS, NC = TB / 4;
-  const int ny = m.ny;
-  const int i0 = tile_x * TF;
-  const int TFe = min(TF, ny - i0);
-  const int nmod = sp->n_mod;
-  for (int w = tid; w < 2 * TFe * NC; w += THREADS) {
-    const int slot = w / NC, c = w - slot * NC;
-    const int side = slot >= TFe, r = slot - side * TFe;
+  // B. static face i0 + r from mortars (2r, 2r+1); moving face i0 - n + r from mortars 2r+1
+  // (its lower part) and 2r+2 (its upper part), with the opposite sign.  item = face fastest,
+  // then side, then node pair, then row pair
+  const long long line = (long long)iz * ny;
+  for (int w = tid; w < C::ITEMS_B; w += C::THREADS) {
+    const int r = w % TF;
+    int rest = w / TF;
+    const int side = rest & 1;
+    rest >>= 1;
+    const int ip = rest % NH, qp = rest / NH;
+    if (r >= TFe) continue;
     int f = side ? i0 - nmod + r : i0 + r;
     f = f < 0 ? f + ny : (f >= ny ? f - ny : f);
-    const float4 x = *reinterpret_cast<const float4*>(sO + (side * TF + r) * FS + 4 * c);
-    *reinterpret_cast<float4*>((side ? Fm : Fs) + ((long long)iz * ny + f) * TB + 4 * c) = x;
+    fused_face_rows<N, TF>(sTab, sF, (side ? Fm : Fs) + (line + f) * TB, r, side, qp, ip);
   }
 }
 
-// Persistent tile pipeline: tiles first, first + stride, ... < total, with the traces of the
-// next NBUF - 1 tiles in flight while a tile computes.  stage(item, buffer) issues a tile's
-// copies; run(item, buffer) computes it (ending with a barrier) and store(item) writes it.
-template <int N, int TF, class Stage, class Run, class Store>
-__device__ __forceinline__ void fused_pipeline(const int first, const int stride, const int total, float* sBuf,
-                                               Stage stage, Run run, Store store) {
+// Persistent tile pipeline: tiles first, first + stride, ... < total, with the next tile's
+// copies in flight while a tile computes (two buffers).  stage(item, tables or NULL, traces)
+// issues a tile's copies; run(item, tables, traces) computes and stores it.  One barrier per
+// tile before the computation: the tile has landed and every thread is done with the
+// previous tile, whose buffers the next copies then reuse.
+template <int N, int TF, class Stage, class Run>
+__device__ __forceinline__ void fused_pipeline(const int first, const int stride, const int total, float* smem,
+                                               Stage stage, Run run) {
   using C = IfFusedCfg<N, TF>;
-  constexpr int NBUF = C::NBUF;
-#pragma unroll
-  for (int k = 0; k < NBUF - 1; ++k) {
-    const int it = first + k * stride;
-    if (it < total) stage(it, sBuf + k * C::TBUF);
-    cp_async_commit();
-  }
-  // tile first + k stride sits in buffer k mod NBUF
+  float* sTab = smem;                        // [NTAB][TAB]
+  float* sTr = smem + C::NTAB * C::TAB;      // [NBUF][TBUF]
+  if (first < total) stage(first, sTab, sTr);
+  cp_async_commit();
   int slot = 0;
   for (int t = first; t < total; t += stride) {
-    // the buffer of the previous tile (free: its computation ended with a barrier) receives
-    // tile t + (NBUF-1) stride; then this tile's group is the oldest of NBUF pending ones
-    const int tp = t + (NBUF - 1) * stride;
-    if (tp < total) stage(tp, sBuf + (slot == 0 ? NBUF - 1 : slot - 1) * C::TBUF);
-    cp_async_commit();
-    cp_async_wait<NBUF - 1>();
+    cp_async_wait<0>();
     __syncthreads();
-    run(t, sBuf + slot * C::TBUF);
-    store(t);
-    slot = slot + 1 == NBUF ? 0 : slot + 1;
+    const int tn = t + stride;
+    if (tn < total) stage(tn, sTab + (slot ^ 1) * C::TAB, sTr + (slot ^ 1) * C::TBUF);
+    cp_async_commit();
+    run(t, sTab + slot * C::TAB, sTr + slot * C::TBUF);
+    slot ^= 1;
   }
   cp_async_wait<0>();
 }
@@ -502,33 +529,162 @@ __device__ __forceinline__ void divmod_small(const int t, const int n, const flo
   *r = rr;
 }
 
-// The tiles of one solve: (n_par / TF) x n_perp, tile index = tile_x + ntx iz.
+// Warp-owned rows (FP32, odd N, one solve): the tile's faces split by row pairs, warp w of a
+// CTA owning rows 2 w and 2 w + 1 of every face of the CTA's tiles.  The rows of a face are
+// independent through projection, Riemann solve and back-projection (the interface slides
+// along xi^1 only), so each warp stages its rows of a tile, computes phases A and B and
+// stores them with warp-level synchronisation only, and prefetches its rows of the next tile
+// meanwhile: no block-wide barrier after the operator tables have landed.  Per warp, in
+// shared memory: two trace buffers [side][TF+1 faces][5][2 NP] and the mortar fluxes
+// [2 TF + 1][5][2 NP] (stride MSW = 4 mod 32 words).  Same arithmetic per node as the
+// staged tile (mortar_rows, face_rows), so the results are bit-identical.
+#ifndef SM_IF_WARP_TF
+#define SM_IF_WARP_TF 4
+#endif
+#ifndef SM_IF_WARP_REGS
+#define SM_IF_WARP_REGS 128
+#endif
+template <int N, int TFV> struct IfWarpCfg {
+  static_assert(N % 2 == 1, "the warp-owned interface rows take odd N (rows in pairs)");
+  static constexpr int NP = N + 1, NP2 = NP * NP, NN = NP * NP * NP;
+  static constexpr int NH = NP / 2;                      // row pairs = warps per CTA
+  static constexpr int TF = TFV;
+  static constexpr int NM = 2 * TF + 1;
+  static constexpr int WPB = NH;
+  static constexpr int THREADS = 32 * WPB;
+  static constexpr int RB = 5 * 2 * NP;                  // one face's row pair, all variables
+  static constexpr int TBUFW = 2 * (TF + 1) * RB;        // one buffer of a warp (floats)
+  static constexpr int MSW = RB + (36 - RB % 32) % 32;   // mortar flux stride, 4 mod 32
+  static constexpr int SFW = ((NM * MSW + 3) / 4) * 4;
+  static constexpr int PER_WARP = 2 * TBUFW + SFW;
+  static constexpr int TAB = 16 * NP2;
+  static constexpr size_t smem_floats = (size_t)TAB + (size_t)WPB * PER_WARP;
+  static constexpr size_t smem_bytes = sizeof(float) * smem_floats;
+  // resident CTAs per SM asked of the register allocator
+  static constexpr int MINB = 65536 / (THREADS * SM_IF_WARP_REGS) > 0 ? 65536 / (THREADS * SM_IF_WARP_REGS) : 1;
+};
+
+// Issues the copies of one warp's rows (row pair qp) of tile (tile_x, iz) into buf
+// [side][r][v][2 NP]: static faces i0 + r and moving faces i0 - n - 1 + r (mod n_par),
+// r = 0..TFe, from the compact arrays (16-byte pieces: a variable's row pair is 2 NP
+// contiguous floats) or from the element node layers of U (rows interleaved on the way).
+template <int N, int TF>
+__device__ __forceinline__ void warp_rows_stage(const MeshDev& m, const int nmod, const float* __restrict__ U,
+                                                const float* __restrict__ Ts, const float* __restrict__ Tm,
+                                                const int tile_x, const int iz, const int qp, float* buf,
+                                                const int lane) {
+  using C = IfWarpCfg<N, TF>;
+  constexpr int NP = C::NP, NP2 = C::NP2, NN = C::NN, TB = 5 * NP2;
+  const int ny = m.ny;
+  const int i0 = tile_x * TF;
+  const int TFe = min(TF, ny - i0);
+  const int nf = TFe + 1;
+  const int fm0 = i0 - nmod - 1 < 0 ? i0 - nmod - 1 + ny : i0 - nmod - 1;
+  if (Ts) {
+    constexpr int CH = 2 * NP / 4;                       // 16-byte pieces of a variable's row pair
+    const long long line = (long long)iz * ny;
+    for (int c = lane; c < 2 * nf * 5 * CH; c += 32) {
+      const int ch = c % CH;
+      int rest = c / CH;
+      const int v = rest % 5;
+      rest /= 5;
+      const int side = rest >= nf, r = rest - side * nf;
+      int f = side ? fm0 + r : i0 + r;
+      f = f >= ny ? f - ny : f;
+      const float* src = (side ? Tm : Ts) + (line + f) * TB + v * NP2 + qp * 2 * NP + 4 * ch;
+      cp_async_16(buf + ((side * (TF + 1) + r) * 5 + v) * 2 * NP + 4 * ch, src);
+    }
+  } else {
+    for (int c = lane; c < 2 * nf * 5 * 2 * NP; c += 32) {
+      const int node = c % (2 * NP);                     // i + NP (q & 1): row-major in the layer
+      int rest = c / (2 * NP);
+      const int v = rest % 5;
+      rest /= 5;
+      const int side = rest >= nf, r = rest - side * nf;
+      int f = side ? fm0 + r : i0 + r;
+      f = f >= ny ? f - ny : f;
+      const int i = node % NP, q1 = node / NP;
+      const float* src = U + encode_elem(m, side, side ? 0 : m.nxs - 1, f, iz) * 5 * NN + (side ? 0 : NP2 * N) +
+                         (long long)v * NN + (2 * qp + q1) * NP + i;
+      cp_async_4(buf + ((side * (TF + 1) + r) * 5 + v) * 2 * NP + 2 * i + q1, src);
+    }
+  }
+}
+
 template <int N, int RIEM, int TF>
-__device__ __forceinline__ void interface_fused_loop(const MeshDev& m, const StageParams* __restrict__ sp,
-                                                     const float* __restrict__ U, float* __restrict__ Fs,
-                                                     float* __restrict__ Fm, const float* __restrict__ Ts,
-                                                     const float* __restrict__ Tm) {
-  using C = IfFusedCfg<N, TF>;
+__global__ void __launch_bounds__(IfWarpCfg<N, TF>::THREADS, IfWarpCfg<N, TF>::MINB)
+sliding_interface_warp_kernel(const MeshDev m, const StageParams* __restrict__ sp, const float* __restrict__ U,
+                              float* __restrict__ Fs, float* __restrict__ Fm, const float* __restrict__ Ts,
+                              const float* __restrict__ Tm) {
+  using C = IfWarpCfg<N, TF>;
+  constexpr int NP = C::NP, NH = C::NH, NM = C::NM, RB = C::RB, MSW = C::MSW, TB = 5 * C::NP2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sBuf = reinterpret_cast<float*>(smem_raw);   // [NBUF][TBUF] trace buffers
-  float* sF = sBuf + C::NBUF * C::TBUF;               // [NM][MS] mortar fluxes
-  float* sO = sF + C::SFSZ;                           // [2][TF][FS] output blocks
-  const int tid = threadIdx.x;
-  const int ntx = (m.ny + TF - 1) / TF;
+  float* sTab = reinterpret_cast<float*>(smem_raw);
+  const int qp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* wb = sTab + C::TAB + qp * C::PER_WARP;          // [2][TBUFW] traces
+  float* sF = wb + 2 * C::TBUFW;                         // [NM][MSW] mortar fluxes
+  const int ny = m.ny;
+  const int ntx = (ny + TF - 1) / TF;
   const float inv = 1.0f / (float)ntx;
-  int rx = 0, rz = 0;   // coordinates of the tile being computed
-  fused_pipeline<N, TF>(
-      blockIdx.x, gridDim.x, ntx * m.nz, sBuf,
-      [&](int t, float* dst) {
-        int x, z;
-        divmod_small(t, ntx, inv, &z, &x);
-        fused_tile_stage<N, TF>(m, sp, U, Ts, Tm, x, z, dst, tid);
-      },
-      [&](int t, const float* sB) {
-        divmod_small(t, ntx, inv, &rz, &rx);
-        fused_tile_compute<N, RIEM, TF>(m, sp, Fs, Fm, rx, rz, sB, sF, sO, tid);
-      },
-      [&](int t) { fused_tile_store<N, TF>(m, sp, Fs, Fm, rx, rz, sO, tid); });
+  const int total = ntx * m.nz;
+  const int nmod = sp->n_mod;
+  const float sJ = m.cf[MC_SJ_IF];
+  const float gamma = m.cf[MC_GAMMA];
+  for (int w = threadIdx.x; w < C::TAB / 4; w += C::THREADS) cp_async_16(sTab + 4 * w, sp->pair_f + 4 * w);
+  int t = blockIdx.x;
+  if (t < total) {
+    int x, z;
+    divmod_small(t, ntx, inv, &z, &x);
+    warp_rows_stage<N, TF>(m, nmod, U, Ts, Tm, x, z, qp, wb, lane);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();                                       // tables and every warp's first rows
+  int slot = 0;
+  for (; t < total; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    if (tn < total) {
+      int x, z;
+      divmod_small(tn, ntx, inv, &z, &x);
+      warp_rows_stage<N, TF>(m, nmod, U, Ts, Tm, x, z, qp, wb + (slot ^ 1) * C::TBUFW, lane);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();                                  // this tile's rows (the next may be in flight)
+    __syncwarp();
+    int tile_x, iz;
+    divmod_small(t, ntx, inv, &iz, &tile_x);
+    const int i0 = tile_x * TF;
+    const int TFe = min(TF, ny - i0);
+    const int nme = 2 * TFe + 1;
+    const float* buf = wb + slot * C::TBUFW;
+    // A. item = mortar fastest, then node pair
+    for (int w = lane; w < NM * NH; w += 32) {
+      const int mi = w % NM, jp = w / NM;
+      if (mi < nme) {
+        const int isub = mi & 1, rs = mi >> 1, rm = rs + isub;
+        mortar_rows<N, RIEM, 2 * NP, 2 * NP>(sTab, buf + rs * RB, buf + (TF + 1 + rm) * RB, sF + mi * MSW, isub, jp,
+                                             sJ, gamma);
+      }
+    }
+    __syncwarp();
+    // B. static face i0 + r from mortars (2r, 2r+1), moving face i0 - n + r from (2r+1, 2r+2);
+    // item = face fastest, then side, then node pair
+    const long long line = (long long)iz * ny;
+    for (int w = lane; w < 2 * TF * NH; w += 32) {
+      const int r = w % TF;
+      const int rest = w / TF;
+      const int side = rest & 1, ip = rest >> 1;
+      if (r < TFe) {
+        int f = side ? i0 - nmod + r : i0 + r;
+        f = f < 0 ? f + ny : (f >= ny ? f - ny : f);
+        face_rows<N, 2 * NP>(sTab, sF + (2 * r + side) * MSW, sF + (2 * r + 1 + side) * MSW,
+                             (side ? Fm : Fs) + (line + f) * TB, side, qp, ip);
+      }
+    }
+    __syncwarp();                                        // buf and sF free for the next tile
+    slot ^= 1;
+  }
+  cp_async_wait<0>();
 }
 
 // Interface tile modes: Euler flux, Navier-Stokes flux (BR1 viscous mean of both sides'

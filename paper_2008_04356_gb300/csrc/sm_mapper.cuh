@@ -134,17 +134,14 @@ __device__ __forceinline__ void stage_params_body(const MeshDev& m, int np, Stag
     }
     __syncthreads();
   }
-  // the FP32 pair tables (zero in the padding)
-  const int mr = sm_pair_row(np), mt = sm_pair_stride(np);
-  for (int r = threadIdx.x; r < 4 * mt; r += blockDim.x) {
-    const int g = r / mt, rem = r - g * mt, pr = rem >> 1, h = rem & 1;
-    const int row = pr / mr, col = pr - row * mr;
-    float v = 0.f;
-    if (row < np && col < np) {
-      const int k = g == 0 ? (h ? 3 : 0) : (g == 1 ? (h ? 2 : 1) : 4 + 2 * (g - 2) + h);
-      v = sp->mat_f[k][col * np + row];
+  // the FP32 operators duplicated into float pairs, rows in pairs: [k][h][col][2 rows x 2]
+  if (np % 2 == 0) {
+    const int nh = np / 2;
+    for (int r = threadIdx.x; r < 8 * nh * np; r += blockDim.x) {
+      const int col = r % np, kh = r / np, h = kh % nh, k = kh / nh;
+      const float v0 = sp->mat_f[k][2 * h * np + col], v1 = sp->mat_f[k][(2 * h + 1) * np + col];
+      *reinterpret_cast<float4*>(sp->pair_f + 4 * r) = make_float4(v0, v0, v1, v1);
     }
-    sp->pair_f[r] = v;
   }
 }
 

@@ -113,8 +113,8 @@ def test_interface_fp64(sm, N, riemann):
 @pytest.mark.parametrize("riemann", [synth.RUSANOV, synth.ROE_HH])
 @pytest.mark.parametrize("N", [1, 2, 3, 5, 7])
 def test_interface_fp32(sm, N, riemann):
-    """FP32 interface fluxes (register-fused tile at odd N, staged tile at even N) against
-    the oracle: tiles of 8 faces with a ragged last tile (11, 17, 40), a single short tile
+    """FP32 interface fluxes (warp-owned row pairs in tiles of 4 faces at odd N, staged tile
+    of 8 faces at even N) against the oracle: ragged last tiles (11, 17, 40), a single tile
     (4), one face (1), partner offsets that wrap both ways, and the conforming instant."""
     for ny, delta0, t in ((11, 0.3337, 0.21), (4, 0.0, 0.0), (17, -2.71, 0.05), (1, 0.4, 0.0), (40, 5.123, 0.3)):
         p = ragged_box(N, riemann, ny=ny, delta0=delta0, prec=synth.FP32)
