@@ -184,6 +184,22 @@ int sm_set_state(sm_solver* s, const void* U, int on_device, double t, void* str
  * Synchronises the stream before returning. */
 int sm_get_state(sm_solver* s, void* U, int on_device, double* t, void* stream);
 
+/* Streams count independent jobs through the solver from host memory: job i takes the
+ * state at in_host + i * in_stride bytes (the solver layout and precision; in_stride 0
+ * reuses one input), sets the solver time to t0, advances it by nsteps RK steps of dt
+ * (sm_step, Sec. 3.3 and 3.1) and writes the resulting state to out_host + i * out_stride
+ * bytes (out_stride 0: every job overwrites the same output).  The copies overlap the
+ * compute: while job i steps, the host-to-device copy of job i+1 and the device-to-host copy
+ * of job i-1 run on two copy streams of their own, through two state-sized device staging
+ * buffers that the solver allocates at the first call and keeps until sm_destroy.  Host
+ * buffers should be pinned (pageable memory serialises the copies).  stream orders the
+ * compute; the call returns when every result is in host memory.  The solver's state and
+ * time afterwards are those of the last job.  Results equal those of sm_set_state +
+ * sm_step + sm_get_state per job.  Arguments are checked before any CUDA call (NULL
+ * pointers, count < 0, nsteps < 1, negative strides, dt <= 0 or non-finite t0: SM_ERR_ARG). */
+int sm_stream_jobs(sm_solver* s, const void* in_host, long long in_stride, void* out_host, long long out_stride,
+                   int count, double t0, double dt, int nsteps, void* stream);
+
 /* dU/dt = R(U, t) for a caller-owned device state dU into caller-owned dUt (same layout
  * and precision), on stream: mapper and mortar matrices at time t (Sec. 4.3, 3.2), the
  * fused interface kernel (Sec. 3.3 steps 3-5), then volume + surface (Sec. 3.1).

@@ -411,6 +411,12 @@ struct sm_solver {
   double t_host = 0.0;
   cudaStream_t cap = nullptr;
   std::vector<GraphEntry> graphs;
+  // sm_stream_jobs: state-sized staging buffers, copy streams and their events (first call)
+  void* stage_in = nullptr;
+  void* stage_out = nullptr;
+  double* t0_d = nullptr;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t in_ready = nullptr, in_free = nullptr, out_ready = nullptr, out_free = nullptr;
 };
 
 namespace {
@@ -567,8 +573,13 @@ void free_solver(sm_solver* s) {
   if (!s) return;
   clear_graphs(s);
   if (s->cap) cudaStreamDestroy(s->cap);
+  if (s->h2d) cudaStreamDestroy(s->h2d);
+  if (s->d2h) cudaStreamDestroy(s->d2h);
+  for (cudaEvent_t ev : {s->in_ready, s->in_free, s->out_ready, s->out_free})
+    if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {s->basis_d, s->modes_d, s->U[0], s->U[1], s->G, s->Fs, s->Fm, s->sp, s->ticket_d, s->t_d, s->red_d, s->topo_d,
-                  s->Gr, s->Ls, s->Lm, s->Ts, s->Tm, s->Ts2, s->Tm2, s->Fs2, s->Fm2, s->geo};
+                  s->Gr, s->Ls, s->Lm, s->Ts, s->Tm, s->Ts2, s->Tm2, s->Fs2, s->Fm2, s->geo, s->stage_in, s->stage_out,
+                  s->t0_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -937,6 +948,61 @@ int sm_step(sm_solver* s, double dt, int nsteps, void* stream) {
     s->t_host += dt;
     s->sp_last = 4;
   }
+  return SM_OK;
+}
+
+int sm_stream_jobs(sm_solver* s, const void* in_host, long long in_stride, void* out_host, long long out_stride,
+                   int count, double t0, double dt, int nsteps, void* stream) {
+  if (!s || !in_host || !out_host) return fail(SM_ERR_ARG, "NULL argument");
+  if (count < 0 || nsteps < 1 || in_stride < 0 || out_stride < 0)
+    return fail(SM_ERR_ARG, "count >= 0, nsteps >= 1, strides >= 0");
+  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t0)) return fail(SM_ERR_ARG, "dt > 0 and t0 finite");
+  if (count == 0) return SM_OK;
+  const size_t bytes = (size_t)s->nstate * s->sb;
+  if (!s->stage_in) {
+    SM_CK(cudaMalloc(&s->stage_in, bytes), "staging buffer (in)");
+    SM_CK(cudaMalloc(&s->stage_out, bytes), "staging buffer (out)");
+    SM_CK(cudaMalloc(&s->t0_d, sizeof(double)), "start time");
+    SM_CK(cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking), "copy stream (in)");
+    SM_CK(cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking), "copy stream (out)");
+    for (cudaEvent_t* ev : {&s->in_ready, &s->in_free, &s->out_ready, &s->out_free})
+      SM_CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming), "event");
+  }
+  cudaStream_t cs = (cudaStream_t)stream;
+  const char* in = static_cast<const char*>(in_host);
+  char* out = static_cast<char*>(out_host);
+  // the start time, once, in device memory (a per-job device-to-device copy of 8 bytes)
+  SM_CK(cudaMemcpy(s->t0_d, &t0, sizeof(double), cudaMemcpyHostToDevice), "copy start time");
+  SM_CK(cudaMemcpyAsync(s->stage_in, in, bytes, cudaMemcpyHostToDevice, s->h2d), "copy job in");
+  SM_CK(cudaEventRecord(s->in_ready, s->h2d), "event");
+  for (int k = 0; k < count; ++k) {
+    // job k's state into the solver; the staging buffer is then free for job k + 1
+    SM_CK(cudaStreamWaitEvent(cs, s->in_ready, 0), "wait job in");
+    SM_CK(cudaMemcpyAsync(s->U[s->cur], s->stage_in, bytes, cudaMemcpyDeviceToDevice, cs), "state in");
+    SM_CK(cudaMemcpyAsync(s->t_d, s->t0_d, sizeof(double), cudaMemcpyDeviceToDevice, cs), "time in");
+    SM_CK(cudaEventRecord(s->in_free, cs), "event");
+    s->traces_ok = false;
+    s->t_host = t0;
+    if (k + 1 < count) {
+      SM_CK(cudaStreamWaitEvent(s->h2d, s->in_free, 0), "wait staging (in)");
+      SM_CK(cudaMemcpyAsync(s->stage_in, in + (size_t)(k + 1) * (size_t)in_stride, bytes, cudaMemcpyHostToDevice, s->h2d),
+            "copy job in");
+      SM_CK(cudaEventRecord(s->in_ready, s->h2d), "event");
+    }
+    // the first stage of a step writes the RK register before reading it: G needs no reset
+    const int rc = sm_step(s, dt, nsteps, stream);
+    if (rc != SM_OK) return rc;
+    // the result out through the second staging buffer, once job k - 1 has left it
+    if (k > 0) SM_CK(cudaStreamWaitEvent(cs, s->out_free, 0), "wait staging (out)");
+    SM_CK(cudaMemcpyAsync(s->stage_out, s->U[s->cur], bytes, cudaMemcpyDeviceToDevice, cs), "state out");
+    SM_CK(cudaEventRecord(s->out_ready, cs), "event");
+    SM_CK(cudaStreamWaitEvent(s->d2h, s->out_ready, 0), "wait job out");
+    SM_CK(cudaMemcpyAsync(out + (size_t)k * (size_t)out_stride, s->stage_out, bytes, cudaMemcpyDeviceToHost, s->d2h),
+          "copy job out");
+    SM_CK(cudaEventRecord(s->out_free, s->d2h), "event");
+  }
+  SM_CK(cudaStreamSynchronize(s->d2h), "sync copies out");
+  SM_CK(cudaStreamSynchronize(cs), "sync");
   return SM_OK;
 }
 

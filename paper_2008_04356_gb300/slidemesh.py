@@ -70,6 +70,8 @@ _SIGS = {
     "sm_rhs": (C.c_int, [_vp, C.c_double, _vp, _vp, _vp]),
     "sm_interface": (C.c_int, [_vp, C.c_double, _vp, _vp, _vp, _vp]),
     "sm_step": (C.c_int, [_vp, C.c_double, C.c_int, _vp]),
+    "sm_stream_jobs": (C.c_int, [_vp, _vp, C.c_longlong, _vp, C.c_longlong, C.c_int, C.c_double, C.c_double, C.c_int,
+                                 _vp]),
     "sm_gradients": (C.c_int, [_vp, C.c_double, _vp, _vp, _vp]),
     "sm_step_profiled": (C.c_int, [_vp, C.c_double, C.c_int, _vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "sm_diag": (C.c_int, [_vp, C.POINTER(SmDiag), _vp]),
@@ -288,6 +290,22 @@ class Solver:
 
     def step(self, dt: float, nsteps: int, stream=None):
         check(lib().sm_step(self.h, float(dt), int(nsteps), _stream(stream)), "sm_step")
+
+    def stream_jobs(self, inputs, outputs, t0: float, dt: float, nsteps: int, count=None, stream=None):
+        """sm_stream_jobs: inputs / outputs are CPU tensors (pinned for overlap) holding count
+        states each ([count, *shape]), or one state each, which every job then reuses."""
+        for x in (inputs, outputs):
+            assert not x.is_cuda and x.dtype == self.torch_dtype and x.is_contiguous()
+            assert x.numel() % self.size == 0
+        n_in, n_out = inputs.numel() // self.size, outputs.numel() // self.size
+        if count is None:
+            count = max(n_in, n_out)
+        assert n_in in (1, count) and n_out in (1, count)
+        state_bytes = self.size * inputs.element_size()
+        check(lib().sm_stream_jobs(self.h, inputs.data_ptr(), state_bytes if n_in > 1 else 0, outputs.data_ptr(),
+                                   state_bytes if n_out > 1 else 0, int(count), float(t0), float(dt), int(nsteps),
+                                   _stream(stream)), "sm_stream_jobs")
+        return outputs
 
     def step_profiled(self, dt: float, nsteps: int, stream=None):
         """Per-kernel device times (ms) and launch counts of nsteps steps: mapper, interface, element."""

@@ -169,3 +169,40 @@ def test_static_rhs_refuses_misaligned_arrays_without_gpu(libpath):
     assert rc == -1 and b"aligned" in L.sm_last_error()
     rc = L.sm_rhs_static(ctypes.byref(slidemesh.mesh_desc(p)), ctypes.byref(mo), 0.0, 0x10000, 0x20004, None)
     assert rc == -1
+
+
+@pytest.mark.parametrize("case", ["null_solver", "null_in", "null_out", "count", "nsteps", "dt", "t0", "stride"])
+def test_stream_jobs_checks_arguments_without_gpu(libpath, case):
+    """sm_stream_jobs refuses malformed calls with SM_ERR_ARG before it touches the solver or
+    the device (the solver handle below is never dereferenced)."""
+    import math
+    from paper_2008_04356_gb300 import slidemesh
+    L = slidemesh.lib()
+    s, a, b = ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(48)
+    args = dict(s=s, a=a, sa=0, b=b, sb=0, count=2, t0=0.0, dt=1e-3, nsteps=1)
+    if case == "null_solver":
+        args["s"] = None
+    elif case == "null_in":
+        args["a"] = None
+    elif case == "null_out":
+        args["b"] = None
+    elif case == "count":
+        args["count"] = -1
+    elif case == "nsteps":
+        args["nsteps"] = 0
+    elif case == "dt":
+        args["dt"] = 0.0
+    elif case == "t0":
+        args["t0"] = math.nan
+    else:
+        args["sa"] = -8
+    rc = L.sm_stream_jobs(args["s"], args["a"], args["sa"], args["b"], args["sb"], args["count"], args["t0"],
+                          args["dt"], args["nsteps"], None)
+    assert rc == -1, (case, rc, L.sm_last_error())
+
+
+def test_stream_jobs_with_no_jobs_is_a_no_op_without_gpu(libpath):
+    from paper_2008_04356_gb300 import slidemesh
+    L = slidemesh.lib()
+    rc = L.sm_stream_jobs(ctypes.c_void_p(16), ctypes.c_void_p(32), 0, ctypes.c_void_p(48), 0, 0, 0.0, 1e-3, 1, None)
+    assert rc == 0
