@@ -133,10 +133,13 @@ __device__ __forceinline__ void contract_lines_inplace(T* sF, int tid) {
     }
     store_line<T, NP>(line, ov);
   }
-  if constexpr (sizeof(T) == 4 && NP % 2 == 0) {
-    // FP32, even line length: the xi^2 and xi^3 lines of nodes i and i + 1 (i even) are
-    // adjacent in memory, so a thread takes both as float pairs (one 8-byte access per node)
-    // and contracts them with packed multiply-adds (the same per-line operations in order).
+  if constexpr (sizeof(T) == 4 && NP == 6) {
+    // FP32, N = 5: the xi^2 and xi^3 lines of nodes i and i + 1 (i even) are adjacent in
+    // memory, so a thread takes both as float pairs (one 8-byte access per node) and
+    // contracts them with packed multiply-adds (the same per-line operations in order).
+    // Measured: 2.520 -> 2.478 ms per element launch at N = 5; at N = 7 the same form made
+    // the curved lifting kernel (three contractions per launch) 1.8x slower, so other
+    // degrees keep the one-line form.
 #pragma unroll
     for (int d = 1; d < 3; ++d) {
       constexpr int NPH = NP2 / 2;
