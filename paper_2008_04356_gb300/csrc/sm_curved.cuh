@@ -655,10 +655,10 @@ __device__ __forceinline__ void curved_lift_block(const MeshDev& m, const StageP
   }
   T g[15];
   const T* ge = geo + e * 13 * NN + nd;
-  // the three passes unrolled, so that g stays in registers (a rolled loop indexes it
-  // dynamically, which puts it in local memory): 1.526 -> 1.488 ms per stage on the cylinder
-  // at N = 7 (lifting and interface kernels); a two-CTA register bound was slower (spills)
-#pragma unroll
+  // the three passes stay rolled: unrolled, g lives in registers instead of local memory, but
+  // the kernel then takes 54 registers instead of 40, two 512-thread CTAs per SM instead of
+  // three, and the cylinder's lifting and interface kernels 1.506 instead of 1.301 ms per stage
+#pragma unroll 1
   for (int a = 0; a < 3; ++a) {
     if (active) {
       T* Fe = sF + le * 15 * NN;
