@@ -951,26 +951,13 @@ int sm_step(sm_solver* s, double dt, int nsteps, void* stream) {
   return SM_OK;
 }
 
-int sm_stream_jobs(sm_solver* s, const void* in_host, long long in_stride, void* out_host, long long out_stride,
-                   int count, double t0, double dt, int nsteps, void* stream) {
-  if (!s || !in_host || !out_host) return fail(SM_ERR_ARG, "NULL argument");
-  if (count < 0 || nsteps < 1 || in_stride < 0 || out_stride < 0)
-    return fail(SM_ERR_ARG, "count >= 0, nsteps >= 1, strides >= 0");
-  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t0)) return fail(SM_ERR_ARG, "dt > 0 and t0 finite");
-  if (count == 0) return SM_OK;
+namespace {
+
+// The copies and steps of sm_stream_jobs (staging buffers and copy streams in place).
+int stream_jobs_enqueue(sm_solver* s, const char* in, long long in_stride, char* out, long long out_stride, int count,
+                        double t0, double dt, int nsteps, void* stream) {
   const size_t bytes = (size_t)s->nstate * s->sb;
-  if (!s->stage_in) {
-    SM_CK(cudaMalloc(&s->stage_in, bytes), "staging buffer (in)");
-    SM_CK(cudaMalloc(&s->stage_out, bytes), "staging buffer (out)");
-    SM_CK(cudaMalloc(&s->t0_d, sizeof(double)), "start time");
-    SM_CK(cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking), "copy stream (in)");
-    SM_CK(cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking), "copy stream (out)");
-    for (cudaEvent_t* ev : {&s->in_ready, &s->in_free, &s->out_ready, &s->out_free})
-      SM_CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming), "event");
-  }
   cudaStream_t cs = (cudaStream_t)stream;
-  const char* in = static_cast<const char*>(in_host);
-  char* out = static_cast<char*>(out_host);
   // the start time, once, in device memory (a per-job device-to-device copy of 8 bytes)
   SM_CK(cudaMemcpy(s->t0_d, &t0, sizeof(double), cudaMemcpyHostToDevice), "copy start time");
   SM_CK(cudaMemcpyAsync(s->stage_in, in, bytes, cudaMemcpyHostToDevice, s->h2d), "copy job in");
@@ -1001,8 +988,38 @@ int sm_stream_jobs(sm_solver* s, const void* in_host, long long in_stride, void*
           "copy job out");
     SM_CK(cudaEventRecord(s->out_free, s->d2h), "event");
   }
-  SM_CK(cudaStreamSynchronize(s->d2h), "sync copies out");
-  SM_CK(cudaStreamSynchronize(cs), "sync");
+  return SM_OK;
+}
+
+}  // namespace
+
+int sm_stream_jobs(sm_solver* s, const void* in_host, long long in_stride, void* out_host, long long out_stride,
+                   int count, double t0, double dt, int nsteps, void* stream) {
+  if (!s || !in_host || !out_host) return fail(SM_ERR_ARG, "NULL argument");
+  if (count < 0 || nsteps < 1 || in_stride < 0 || out_stride < 0)
+    return fail(SM_ERR_ARG, "count >= 0, nsteps >= 1, strides >= 0");
+  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t0)) return fail(SM_ERR_ARG, "dt > 0 and t0 finite");
+  if (count == 0) return SM_OK;
+  const size_t bytes = (size_t)s->nstate * s->sb;
+  if (!s->stage_in) {
+    SM_CK(cudaMalloc(&s->stage_in, bytes), "staging buffer (in)");
+    SM_CK(cudaMalloc(&s->stage_out, bytes), "staging buffer (out)");
+    SM_CK(cudaMalloc(&s->t0_d, sizeof(double)), "start time");
+    SM_CK(cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking), "copy stream (in)");
+    SM_CK(cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking), "copy stream (out)");
+    for (cudaEvent_t* ev : {&s->in_ready, &s->in_free, &s->out_ready, &s->out_free})
+      SM_CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming), "event");
+  }
+  const int rc = stream_jobs_enqueue(s, static_cast<const char*>(in_host), in_stride, static_cast<char*>(out_host),
+                                     out_stride, count, t0, dt, nsteps, stream);
+  // every copy has finished before the call returns, also after a failure: none may touch
+  // the caller's host buffers later
+  const cudaError_t e1 = cudaStreamSynchronize(s->h2d);
+  const cudaError_t e2 = cudaStreamSynchronize(s->d2h);
+  const cudaError_t e3 = cudaStreamSynchronize((cudaStream_t)stream);
+  if (rc != SM_OK) return rc;
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    return fail(SM_ERR_CUDA, "sync", e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3));
   return SM_OK;
 }
 

@@ -98,3 +98,20 @@ def test_streamed_jobs_match_the_oracle(sm):
     err = F.increment_error(U0, out.double().numpy().reshape(U0.shape), U)
     assert err < F.INCREMENT_TOL, err
     sol.close()
+
+
+def test_streamed_jobs_on_the_rotating_cylinder_with_navier_stokes(sm):
+    """The same bit-equality on the curved, rotating, Navier-Stokes path (lifting kernels in
+    every stage), two distinct jobs."""
+    p = synth.config_cylinder(N=3, precision=synth.FP32, physics=synth.NAVIER_STOKES)
+    sol = sm.Solver(p)
+    dt, nsteps, t0 = synth.cfl_dt(p), 2, 0.0
+    sol.init_state()
+    U0, _ = sol.get_state(out=torch.empty(tuple(sol.shape()), dtype=sol.torch_dtype))
+    host_in = torch.stack([U0, U0 * torch.tensor([1.0, 1.02, 1.0, 0.98, 1.01]).view(1, 5, 1)]).contiguous().pin_memory()
+    ref, t_ref = one_at_a_time(sol, host_in, t0, dt, nsteps)
+    out = torch.zeros_like(host_in).pin_memory()
+    sol.stream_jobs(host_in, out, t0, dt, nsteps)
+    assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1])
+    assert not torch.equal(out[0], out[1])
+    sol.close()
