@@ -259,9 +259,9 @@ void sm_destroy(sm_solver* s);
  *    ~10 KB (faces = nel_static[1] * nel_static[2]); larger problems are rejected with
  *    SM_ERR_ARG and a message naming both sizes (use sm_rhs for them).
  *  - The first call on a device sets that device up (looks up both arrays' device
- *    addresses, writes the basis tables with a synchronous copy, sets kernel attributes).
- *    After it, a call enqueues kernel launches on stream and copies nothing between host
- *    and device.
+ *    addresses, writes the basis tables with a synchronous copy, sets kernel attributes);
+ *    make that first call before any stream capture.  After it, a call enqueues kernel
+ *    launches on stream and copies nothing between host and device.
  *  - It calls no cudaMalloc, cudaFree or other allocating routine.
  *  - All calls share the one scratch array, whose contents persist from the last call:
  *    every byte a call reads is written by that same call first, so nothing needs
