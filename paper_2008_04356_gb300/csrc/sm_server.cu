@@ -2,10 +2,13 @@
 //
 // A worker thread owns the device work.  Requests wait in arrival order; a request is
 // admitted when a slot is free and its device memory fits in the budget next to the
-// resident solves.  Every iteration advances all resident solves together by the same
-// number of RK steps (FP32 Euler plane-interface solves through one batch with shared
-// launches, the others one at a time), at most a few steps so that new arrivals join
-// quickly, then retires the finished ones and frees their memory.  A solve's time to
+// resident solves.  Every iteration advances the batchable solves (FP32 Euler plane
+// interface) together by the same number of RK steps through one batch with shared launches,
+// at most a few steps so that new arrivals join quickly; every other solve runs on a stream
+// of its own, one chunk of steps at a time, and is only polled between iterations, so that a
+// slow solve (FP64, Navier-Stokes, curvilinear, split form, two interfaces) never holds the
+// batch back (except at a retirement: freeing device memory waits for the whole device).
+// Finished solves are retired and their memory freed.  A solve's time to
 // solution ends at a CUDA event recorded right after its last step, mapped onto the host
 // clock through an anchor event recorded when the worker starts.  Built on the library's
 // own C-ABI.
@@ -38,6 +41,11 @@ struct Job {
   int remaining = 0;
   cudaEvent_t done_ev = nullptr;   // recorded after the solve's last step
   bool done_recorded = false;
+  // solves outside the batch: their own stream, the chunk in flight and its end event
+  cudaStream_t stream = nullptr;
+  cudaEvent_t chunk_ev = nullptr;
+  int in_flight = 0;
+  int failed = SM_OK;
   std::vector<unsigned char> state;
 };
 
@@ -87,7 +95,8 @@ struct sm_server {
   void finish(Job* j, int status, cudaStream_t st);
 };
 
-void sm_server::finish(Job* j, int status, cudaStream_t st) {
+void sm_server::finish(Job* j, int status, cudaStream_t batch_stream) {
+  const cudaStream_t st = j->stream ? j->stream : batch_stream;
   // time to solution: the event after the last step on the device clock, else the host clock
   float ms = 0.0f;
   if (status == SM_OK && j->done_recorded && anchor && cudaEventElapsedTime(&ms, anchor, j->done_ev) == cudaSuccess)
@@ -116,6 +125,10 @@ void sm_server::finish(Job* j, int status, cudaStream_t st) {
   }
   if (j->solver) sm_destroy(j->solver);
   j->solver = nullptr;
+  if (j->chunk_ev) cudaEventDestroy(j->chunk_ev);
+  j->chunk_ev = nullptr;
+  if (j->stream) cudaStreamDestroy(j->stream);
+  j->stream = nullptr;
   std::lock_guard<std::mutex> lk(mu);
   j->res.status = status;
   used -= j->bytes;
@@ -164,13 +177,18 @@ void sm_server::run() {
     if (busy_since < 0.0) busy_since = now();
     for (Job* j : admit) {
       j->res.t_admit = now();
-      int rc = sm_init_mesh(&j->req.desc, &j->solver);
+      const bool solo = !batchable(j->req.desc);
+      int rc = SM_OK;
+      if (solo && (cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                   cudaEventCreateWithFlags(&j->chunk_ev, cudaEventDisableTiming) != cudaSuccess))
+        rc = SM_ERR_CUDA;
+      if (rc == SM_OK) rc = sm_init_mesh(&j->req.desc, &j->solver);
       if (rc == SM_OK) rc = sm_set_motion(j->solver, &j->req.motion);
-      if (rc == SM_OK) rc = sm_init_state(j->solver, (void*)st);
+      if (rc == SM_OK) rc = sm_init_state(j->solver, (void*)(solo ? j->stream : st));
       if (rc == SM_OK && cudaEventCreate(&j->done_ev) != cudaSuccess) { j->done_ev = nullptr; rc = SM_ERR_CUDA; }
       if (rc != SM_OK) { finish(j, rc, st); continue; }
       active.push_back(j);
-      batch_dirty = true;
+      if (!solo) batch_dirty = true;
     }
     {
       std::lock_guard<std::mutex> lk(mu);
@@ -193,15 +211,27 @@ void sm_server::run() {
         if (rc != SM_OK) {
           if (batch) sm_batch_destroy(batch);
           batch = nullptr;
-          for (Job* j : active) finish(j, rc, st);
-          active.clear();
+          std::vector<Job*> solo;
+          for (Job* j : active) {
+            if (batchable(j->req.desc)) finish(j, rc, st);
+            else solo.push_back(j);
+          }
+          active.swap(solo);
+          batch_dirty = false;
           continue;
         }
       }
       batch_dirty = false;
     }
+    // batched solves: one chunk of k steps through the batch, waited for
     int k = 8;
-    for (Job* j : active) k = std::min(k, j->remaining);
+    bool any_batched = false;
+    for (Job* j : active)
+      if (batchable(j->req.desc) && j->remaining > 0) {
+        k = std::min(k, j->remaining);
+        any_batched = true;
+      }
+    if (!any_batched) k = 0;
     int rc = SM_OK;
     if (k > 0) {
       if (batch) rc = sm_batch_step(batch, k, (void*)st);
@@ -209,35 +239,72 @@ void sm_server::run() {
       for (Job* j : active)
         if (rc == SM_OK && batchable(j->req.desc) && j->remaining == k)
           j->done_recorded = cudaEventRecord(j->done_ev, st) == cudaSuccess;
-      for (Job* j : active)
-        if (rc == SM_OK && !batchable(j->req.desc)) {
-          rc = sm_step(j->solver, j->req.dt, k, (void*)st);
-          if (rc == SM_OK && j->remaining == k) j->done_recorded = cudaEventRecord(j->done_ev, st) == cudaSuccess;
+    }
+    // the other solves: on their own streams, at most one chunk in flight each, polled
+    bool solo_waiting = false;
+    for (Job* j : active) {
+      if (batchable(j->req.desc) || j->failed != SM_OK) continue;
+      if (j->in_flight) {
+        const cudaError_t q = cudaEventQuery(j->chunk_ev);
+        if (q == cudaSuccess) {
+          j->remaining -= j->in_flight;
+          j->res.steps += j->in_flight;
+          j->in_flight = 0;
+        } else if (q != cudaErrorNotReady) {
+          j->failed = SM_ERR_CUDA;
+          continue;
         }
+      }
+      if (!j->in_flight && j->remaining > 0) {
+        const int kj = std::min(8, j->remaining);
+        int r2 = sm_step(j->solver, j->req.dt, kj, (void*)j->stream);
+        if (r2 == SM_OK && j->remaining == kj) j->done_recorded = cudaEventRecord(j->done_ev, j->stream) == cudaSuccess;
+        if (r2 == SM_OK && cudaEventRecord(j->chunk_ev, j->stream) != cudaSuccess) r2 = SM_ERR_CUDA;
+        if (r2 != SM_OK) j->failed = r2;
+        else j->in_flight = kj;
+      }
+      if (j->in_flight) solo_waiting = true;
+    }
+    if (k > 0) {
       if (rc == SM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SM_ERR_CUDA;
       std::lock_guard<std::mutex> lk(mu);
       stats.batched_steps += k;
+    } else if (solo_waiting) {
+      // nothing batched to wait for: let the solo chunks run, admit arrivals meanwhile
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait_for(lk, std::chrono::microseconds(200));
     }
     std::vector<Job*> still;
     for (Job* j : active) {
-      j->remaining -= k;
-      j->res.steps += k;
-      if (rc != SM_OK || j->remaining <= 0) {
-        finish(j, rc, st);
-        batch_dirty = true;
-      } else {
-        still.push_back(j);
+      if (batchable(j->req.desc)) {
+        j->remaining -= k;
+        j->res.steps += k;
+        if (rc != SM_OK || j->remaining <= 0) {
+          finish(j, rc, st);
+          batch_dirty = true;
+          continue;
+        }
+      } else if (j->failed != SM_OK || (j->remaining <= 0 && !j->in_flight)) {
+        if (j->failed != SM_OK && j->stream) cudaStreamSynchronize(j->stream);
+        finish(j, j->failed, st);
+        continue;
       }
+      still.push_back(j);
     }
     active.swap(still);
   }
   if (batch) sm_batch_destroy(batch);
   batch = nullptr;
   for (Job* j : active) {
+    if (j->stream) cudaStreamSynchronize(j->stream);
     if (j->solver) sm_destroy(j->solver);
     j->solver = nullptr;
     if (j->done_ev) cudaEventDestroy(j->done_ev);
     j->done_ev = nullptr;
+    if (j->chunk_ev) cudaEventDestroy(j->chunk_ev);
+    j->chunk_ev = nullptr;
+    if (j->stream) cudaStreamDestroy(j->stream);
+    j->stream = nullptr;
   }
   active.clear();
   if (anchor) cudaEventDestroy(anchor);

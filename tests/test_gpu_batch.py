@@ -165,3 +165,33 @@ def test_server_fp64_requests_match_sm_step(sm):
     s.step(dt, 9)
     u, _ = s.get_state()
     assert np.frombuffer(r["state"], dtype=np.float64).tobytes() == u.cpu().numpy().tobytes()
+
+
+def test_server_runs_slow_solves_beside_the_batch(sm):
+    """FP64 requests step on streams of their own, beside the FP32 batch: every result is
+    the one-solve result bit for bit, and short FP32 requests submitted together with a long
+    FP64 one finish before it."""
+    long_p = synth.config_box(N=5, k=6)                      # FP64, 2 x 6^3 elements
+    long_dt, long_n = synth.cfl_dt(long_p), 400
+    short = _stream(seed=3, n=4)
+    srv = sm.Server(hbm_budget_bytes=8 << 30, max_slots=8)
+    t_long = srv.submit(long_p, long_dt, long_n, keep_state=True)
+    t_short = [srv.submit(p, dt, n, keep_state=True) for p, dt, n in short]
+    srv.wait(300)
+    r_long = srv.poll(t_long)
+    r_short = [srv.poll(t) for t in t_short]
+    srv.close()
+    assert r_long["status"] == 0 and all(r["status"] == 0 for r in r_short)
+    assert r_long["steps"] == long_n
+    assert max(r["t_done"] for r in r_short) < r_long["t_done"]
+    s = fresh(sm, long_p)
+    s.step(long_dt, long_n)
+    u, _ = s.get_state()
+    assert np.frombuffer(r_long["state"], dtype=np.float64).tobytes() == u.cpu().numpy().tobytes()
+    for (p, dt, n), r in zip(short, r_short):
+        alone = sm.Server(hbm_budget_bytes=8 << 30, max_slots=1)
+        t = alone.submit(p, dt, n, keep_state=True)
+        alone.wait(120)
+        ra = alone.poll(t)
+        alone.close()
+        assert ra["state"] == r["state"]
