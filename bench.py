@@ -587,13 +587,25 @@ def main():
     clocks.start()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the timed steps in five consecutive chunks, an event after each: per-chunk step times
+    # give the spread (median, min, max) beside the whole-region value
+    nrep = 5 if args.steps >= 5 else 1
+    cuts = [args.steps * r // nrep for r in range(nrep + 1)]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(nrep - 1)]
     e0.record(stream)
-    sol.step(dt, args.steps)
+    for r in range(nrep):
+        sol.step(dt, cuts[r + 1] - cuts[r])
+        if r < nrep - 1:
+            evs[r].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
+    marks = [e0] + evs + [e1]
+    rep_ms = sorted(marks[r].elapsed_time(marks[r + 1]) / (cuts[r + 1] - cuts[r]) for r in range(nrep))
+    repeats = {"chunks": nrep, "ms_per_step_median": rep_ms[nrep // 2], "ms_per_step_min": rep_ms[0],
+               "ms_per_step_max": rep_ms[-1]}
     value = rep.value(p.ndof * 5 * args.steps, ms * 1e-3)
     face_rate = rep.value(p.n_faces * 5 * args.steps, ms * 1e-3)
     d = sol.diag()
@@ -719,8 +731,8 @@ def main():
         return
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "repeats": repeats, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": p.nelem, "N": p.N, "dof": p.ndof,
                    "sliding_faces_per_side": p.n_faces, "state_bytes": p.ndof * 5 * 4,
                    "riemann": "roe_hh" if riem == "roe" else "rusanov",
