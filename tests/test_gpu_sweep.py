@@ -43,7 +43,7 @@ def sm():
 
 @pytest.mark.parametrize("N", range(1, 8))
 def test_free_stream_and_conservation_sweep(sm, N):
-    for k in (4, 8, 16, 32) if N <= 5 else (4, 8, 16):
+    for k in (4, 8, 16, 32):
         for prec, tol in ((synth.FP64, 1e-13), (synth.FP32, 1e-5)):
             p = synth.config_box(N=N, k=k, flow="free", v=0.5, precision=prec)
             p.delta0 = 0.0137
