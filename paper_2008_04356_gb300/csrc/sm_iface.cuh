@@ -542,7 +542,7 @@ __device__ __forceinline__ void divmod_small(const int t, const int n, const flo
 #define SM_IF_WARP_TF 4
 #endif
 #ifndef SM_IF_WARP_REGS
-#define SM_IF_WARP_REGS 128
+#define SM_IF_WARP_REGS 168
 #endif
 template <int N, int TFV> struct IfWarpCfg {
   static_assert(N % 2 == 1, "the warp-owned interface rows take odd N (rows in pairs)");
