@@ -1,10 +1,12 @@
 // Host side of the C-ABI (include/slidemesh.h): solver set-up, stage sequencing and CUDA
 // graph replay of whole Runge-Kutta steps.
 //
-// Per stage k of a step (Carpenter-Kennedy five-stage RK4, Sec. 3.1):
-//   1. stage_params: t_k = fma(c_k, dt, t), Delta(t_k), (n, s), mortar operators (Sec. 4.3, 3.2)
-//   2. sliding_interface: both sides' interface face fluxes (Sec. 3.3 steps 3-5)
-//   3. dg_element: volume + surface integral and G = A_k G + dt R, U' = U + B_k G
+// Per step of a single solve (Carpenter-Kennedy five-stage RK4, Sec. 3.1): one step_params
+// launch builds, for all five stages k, t_k = fma(c_k, dt, t), Delta(t_k), (n, s) and the
+// mortar operators (Sec. 4.3, 3.2); then per stage k
+//   1. sliding_interface: both sides' interface face fluxes (Sec. 3.3 steps 3-5)
+//   2. dg_element: volume + surface integral and G = A_k G + dt R, U' = U + B_k G.
+// Batched solves take one stage_params launch per stage over the group.
 // U ping-pongs between two buffers because neighbour traces are read from the state of the
 // previous stage while the element kernel writes the new one.
 #include <cmath>
