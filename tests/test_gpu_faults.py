@@ -1,8 +1,8 @@
 """Failure handling of the serving loop, with the failure made on the host (no GPU fault):
 
 * a request whose initial data is not finite (a NaN density in its flow parameters) ends
-  with SM_ERR_NONFINITE, while the solves stepped in the same batched launches complete with
-  exactly the state they reach alone;
+  with SM_ERR_NONFINITE, while the solves stepped in the same batched launches (or beside it,
+  when it runs outside the batch) complete with exactly the state they reach alone;
 * malformed requests (degree outside 1..7, non-positive time step, a request that can never
   fit the memory budget) are refused at submission with their status, and the server keeps
   serving;
@@ -62,6 +62,31 @@ def test_nonfinite_request_is_isolated(sm):
         alone.close()
         assert ra["state"] == r["state"]                   # bit for bit
         assert np.all(np.isfinite(np.frombuffer(r["state"], dtype=np.float32)))
+
+
+def test_nonfinite_solo_request_is_isolated(sm):
+    """The same for a request outside the batch (FP64, on a stream of its own): its NaN ends
+    it with SM_ERR_NONFINITE and the batched FP32 solves beside it are unaffected."""
+    reqs = requests()
+    bad = synth.config_box(N=3)                               # FP64
+    dt_bad = synth.cfl_dt(bad)
+    bad.fpar = (float("nan"),) + tuple(bad.fpar[1:])
+    srv = sm.Server(hbm_budget_bytes=4 << 30, max_slots=8)
+    tbad = srv.submit(bad, dt_bad, 12)
+    tickets = [srv.submit(p, dt, n, keep_state=True) for p, dt, n in reqs]
+    srv.wait(300)
+    rbad = srv.poll(tbad)
+    res = [srv.poll(t) for t in tickets]
+    srv.close()
+    assert rbad["status"] == SM_ERR_NONFINITE
+    assert all(r["status"] == 0 for r in res)
+    for (p, dt, n), r in zip(reqs, res):
+        alone = sm.Server(hbm_budget_bytes=4 << 30, max_slots=1)
+        t = alone.submit(p, dt, n, keep_state=True)
+        alone.wait(120)
+        ra = alone.poll(t)
+        alone.close()
+        assert ra["state"] == r["state"]                   # bit for bit
 
 
 def test_malformed_requests_are_refused_and_serving_continues(sm):
