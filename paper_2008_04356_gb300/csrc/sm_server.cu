@@ -4,14 +4,14 @@
 // admitted when a slot is free and its device memory fits in the budget next to the
 // resident solves.  Every iteration advances the batchable solves (FP32 Euler plane
 // interface) together by the same number of RK steps through one batch with shared launches,
-// at most a few steps so that new arrivals join quickly; every other solve runs on a stream
-// of its own, one chunk of steps at a time, and is only polled between iterations, so that a
-// slow solve (FP64, Navier-Stokes, curvilinear, split form, two interfaces) never holds the
-// batch back (except at a retirement: freeing device memory waits for the whole device).
-// Finished solves are retired and their memory freed.  A solve's time to
-// solution ends at a CUDA event recorded right after its last step, mapped onto the host
-// clock through an anchor event recorded when the worker starts.  Built on the library's
-// own C-ABI.
+// as many as fit in about 20 ms (one to eight) so that new arrivals join quickly; every other
+// solve runs on a stream of its own, one chunk of steps at a time, and is only polled between
+// iterations, so that a slow solve (FP64, Navier-Stokes, curvilinear, split form, two
+// interfaces) never holds the batch back (except at a retirement: freeing device memory waits
+// for the whole device).  Finished solves are retired and their memory freed.  A solve's time
+// to solution ends at a CUDA event recorded right after its last step, mapped onto the host
+// clock through an anchor event recorded when the worker starts.  Built on the library's own
+// C-ABI.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -87,6 +87,10 @@ struct sm_server {
   bool batch_dirty = true;
   cudaEvent_t anchor = nullptr;    // recorded (and waited for) when the worker starts
   double anchor_host = 0.0;        // host-clock time of the anchor event
+  // seconds per batched step of the current batch (the last iteration's), which sets the
+  // steps per iteration: new arrivals wait at most about kIterTarget for the next admission
+  double step_s = 0.0;
+  static constexpr double kIterTarget = 0.02;
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -223,8 +227,9 @@ void sm_server::run() {
       }
       batch_dirty = false;
     }
-    // batched solves: one chunk of k steps through the batch, waited for
-    int k = 8;
+    // batched solves: one chunk of k steps through the batch, waited for; k keeps an
+    // iteration near kIterTarget (at most 8 steps, at least one)
+    int k = step_s > 0.0 ? std::max(1, std::min(8, (int)(kIterTarget / step_s))) : 1;
     bool any_batched = false;
     for (Job* j : active)
       if (batchable(j->req.desc) && j->remaining > 0) {
@@ -233,6 +238,7 @@ void sm_server::run() {
       }
     if (!any_batched) k = 0;
     int rc = SM_OK;
+    const double t_iter = now();
     if (k > 0) {
       if (batch) rc = sm_batch_step(batch, k, (void*)st);
       // the batched solves that take their last step here end with this launch sequence
@@ -267,6 +273,7 @@ void sm_server::run() {
     }
     if (k > 0) {
       if (rc == SM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SM_ERR_CUDA;
+      step_s = (now() - t_iter) / k;
       std::lock_guard<std::mutex> lk(mu);
       stats.batched_steps += k;
     } else if (solo_waiting) {
